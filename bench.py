@@ -1,0 +1,345 @@
+"""Throughput of coherent dedispersion + detection + fold on GB300.
+
+Workload (one "step"): the full-rate stream -- 60 s of 16 MHz band at 32 MS/s
+(1.92e9 int8 real samples, seeded synthetic noise + DM 26.8 pulsar (P 0.7145 s,
+5 % duty, S/N 20 per period) + 1 % impulsive RFI), dedispersed with nfft 2^24
+overlap-save into 64 detected sub-channels, folded into 1024 bins and
+decimated to 61.44 us.  Every step pushes the whole stream through the C ABI
+and flushes; the stream (1.92 GB) is larger than L2, so no flush is needed.
+
+JSON line fields: value = Msamples/s with the stream resident in HBM
+(device push); e2e = the same through pond_push from pinned host memory (H2D
+inside the timed region) plus the D2H read of the profile and series;
+roofline = the dominant kernel's algorithmic bytes / its CUDA-event time
+against measured HBM bandwidth; cpu_baseline = the FP64 oracle on a bounded
+slice on the host cores.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference there is:
+the paper publishes no code) on host cores over a bounded slice per step.
+Multi-GPU: replicas only (one independent stream per rank, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Msamples/s dedisperse+detect+fold (×real-time) and % HBM roofline vs plain FP32"
+UNIT = "Msamples/s"
+F0, BW, FS = 326.5, 16.0, 32e6
+PLAN = dict(dm=26.8, nfft=1 << 24, nchan=64, nbins=1024, period=0.7145, t_dec=61.44e-6)
+REALTIME_MSPS = FS / 1e6
+
+
+def workload_config(n_samples: int) -> dict:
+    return {"workload": "full-rate 60 s stream: 1.92e9 int8 samples, 326.5 MHz / 16 MHz, DM 26.8, "
+                        "nfft 2^24 overlap-save, 64 sub-channels, 1024-bin fold, 61.44 us series",
+            "samples_per_step": n_samples, "nfft": PLAN["nfft"], "nchan": PLAN["nchan"],
+            "nbins": PLAN["nbins"], "dm": PLAN["dm"], "period_s": PLAN["period"],
+            "t_dec_s": PLAN["t_dec"], "l2": "inputs larger than L2 (1.92 GB stream, 64 MB spectra)",
+            "parallelism": "replicas"}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return rank, ws, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def traffic_from_profiles(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "fft_block.cuh", "pond_internal.h"):
+        with open(os.path.join(ROOT, "paper_1503_01405_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    src = h.hexdigest()[:16]
+    rows = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) >= 3:
+                rows[parts[0]] = (parts[1], float(parts[2]))
+    if kernel in rows and rows[kernel][0] == src:
+        return rows[kernel][1]
+    return None
+
+
+def oracle_rate(x_host, seconds_budget: float = 20.0):
+    """FP64 oracle over whole segments of x_host, up to about seconds_budget."""
+    from oracle import pcd
+    p = pcd.make_plan(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                      PLAN["t_dec"])
+    t0 = time.perf_counter()
+    nseg = 0
+    while True:
+        a = nseg * p.S
+        seg = x_host[a:a + p.nfft]
+        if len(seg) < p.nfft:
+            break
+        pcd.dedisperse_segment(p, seg)
+        nseg += 1
+        if time.perf_counter() - t0 > seconds_budget * 0.5:
+            break
+    # fold + decimate of the same span's outputs (a small share of the oracle's time)
+    dt_seg = time.perf_counter() - t0
+    import numpy as np
+    P = np.ones(nseg * p.S_c)
+    t1 = time.perf_counter()
+    pcd.fold(p, P, p.n_past)
+    pcd.decimate(p, P, p.n_past)
+    dt = dt_seg + (time.perf_counter() - t1)
+    samples = nseg * p.S       # each segment advances the stream by S real samples
+    return samples / dt / 1e6, nseg, samples, dt
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_1503_01405_gb300 import synth
+    spec = synth.replace(synth.FULL_RATE, n=3 * (1 << 24))
+    x = synth.make_stream(spec)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, nseg, samples, dt = oracle_rate(x, seconds_budget=10.0)
+        if i >= args.warmup:
+            vals.append((v, samples, dt))
+    v = sum(s for _, s, _ in vals) / sum(d for _, _, d in vals) / 1e6
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, _, d in vals) / len(vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": workload_config(int(vals[0][1])),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(vals)} steps x whole segments of a {spec.n}-sample slice "
+                                       "of the full-rate workload (FP64 numpy, single thread)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, ws, dist = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1503_01405_gb300 import build as pbuild
+    from paper_1503_01405_gb300 import pond, synth
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pbuild.build()
+    spec = synth.replace(synth.FULL_RATE, seed=synth.FULL_RATE.seed + rank)
+    if args.samples:
+        spec = synth.replace(spec, n=args.samples)
+    n = spec.n
+    x_dev = synth.make_stream_torch(spec, dev)
+    torch.cuda.synchronize()
+    eng = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                      t_dec=PLAN["t_dec"], timing=True, device=local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step_device():
+        eng.reset()
+        eng.push_tensor(x_dev, stream)
+        eng.flush()
+
+    for _ in range(args.warmup):
+        step_device()
+    st0 = eng.stats()
+    torch.cuda.synchronize()
+    barrier(dist)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(dist, ms)
+    st1 = eng.stats()
+    segs = st1["segments"]          # per step (reset clears it); stats accumulate stage times
+    value = ws * n * args.steps / (ms / 1e3) / 1e6
+
+    # dominant kernel from the per-stage CUDA-event times of the timed steps
+    stages = {}
+    for name, d in st1["stages"].items():
+        d0 = st0["stages"].get(name, {"ms": 0.0, "launches": 0})
+        dl = d["launches"] - d0["launches"]
+        if dl > 0:
+            stages[name] = {"ms": d["ms"] - d0["ms"], "launches": dl, "algo_bytes": d["algo_bytes"]}
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    peaks = measured_peaks()
+    avg_s = stages[dom]["ms"] / stages[dom]["launches"] / 1e3
+    achieved = stages[dom]["algo_bytes"] / avg_s / 1e9
+    kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
+             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_partial", "decimate": "k_decimate"}[dom]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profiles(kname),
+            "kernel": kname, "peak_src": peaks["src"],
+            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in stages.items()}}
+
+    # end to end through pond_push from pinned host memory, results read back
+    x_host = torch.empty(n, dtype=torch.int8, pin_memory=True)
+    x_host.copy_(x_dev)
+    xh = x_host.numpy()
+    torch.cuda.synchronize()
+    eng_h = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                        t_dec=PLAN["t_dec"], device=local)
+    prof = {}
+
+    def step_host():
+        eng_h.reset()
+        eng_h.push(xh)
+        eng_h.flush()
+        s, h, _ = eng_h.profile()
+        T, C, _ = eng_h.timeseries()
+        prof["bytes"] = s.nbytes + h.nbytes + T.nbytes + C.nbytes
+
+    for _ in range(max(1, args.warmup)):
+        step_host()
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    t1 = time.perf_counter()
+    e2e_s = max_over_ranks(dist, t1 - t0)
+    e2e = {"value": ws * n * args.steps / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n,
+           "d2h_bytes_per_step": prof["bytes"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, nseg, samples, dt = oracle_rate(xh[:8 * (1 << 24)], seconds_budget=20.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nseg} whole nfft-2^24 segments ({samples} samples advanced) of the same stream, "
+                         f"{dt:.1f} s of FP64 numpy on 1 host thread"}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(n), "realtime_factor": value / REALTIME_MSPS,
+                "e2e": e2e, "gpu_launches": int(st1["kernel_launches"] * segs * args.steps),
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    eng_h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

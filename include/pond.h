@@ -1,0 +1,221 @@
+/*
+ * pond.h -- C ABI of the GB300 phase-coherent dedispersion engine.
+ *
+ * The engine implements the phase-coherent dedispersion (PCD) mode of PONDER
+ * (Naidu, Joshi, Manoharan & Krishnakumar, "PONDER - A real time software
+ * backend for pulsar and IPS observations at the Ooty Radio Telescope",
+ * Sec. 3.7 and Fig. "gpuflow"): a raw real-sampled 8-bit voltage stream is cut
+ * into overlap-save segments, Fourier transformed, multiplied by the inverse of
+ * the interstellar-medium transfer function H of Eq. 4, inverse transformed
+ * into sub-channels, detected (|v|^2, summed over sub-channels), folded at the
+ * pulsar period (the fold of Sec. 3.4) and decimated to a time series.
+ *
+ * Conventions shared by every entry point:
+ *  - Units: frequencies in MHz, the sampling rate fs in real samples per second
+ *    (fs must equal 2 |bw| 1e6: real Nyquist sampling, Sec. 3.2), DM in
+ *    pc cm^-3, times in seconds.
+ *  - Dispersion constant K = 1/2.41e-4 s MHz^2 (Eq. 1's constant); the phase of
+ *    H(f0+f) is 2 pi K 1e6 DM f^2 / (f0^2 (f0+f)) radians, f in MHz.
+ *    bw > 0 is an upper sideband (baseband b <-> sky f0 - |bw|/2 + b); bw < 0 is
+ *    inverted (sky f0 + |bw|/2 - b), where the baseband spectrum is conjugated
+ *    so the inverse filter is H itself rather than conj(H).
+ *  - Channel samples: sub-channel c (c = 0..nchan-1) covers spectrum bins
+ *    c*M .. c*M+M-1 of the N/2 kept bins (M = nfft/(2 nchan)); its complex
+ *    voltage is sampled every dtc = 2 nchan / fs seconds.  The global channel
+ *    sample index g counts from the first stream sample; output g refers to
+ *    arrival at the band centre f0.  The first n_past and the last n_fut
+ *    channel samples of a stream have incomplete support and are never emitted.
+ *  - Return codes: POND_OK (0) or a negative POND_E_* code.  A message for the
+ *    last error of the calling thread is available from pond_last_error().
+ *  - Ownership: the caller owns every pointer it passes; the library keeps no
+ *    caller pointer after a call returns (device pushes: see pond_push_device).
+ *    A handle owns all device memory, streams and events it creates.
+ *  - Threading: a handle may be used by one thread at a time.
+ *  - Determinism: outputs do not depend on how the stream is split into pushes,
+ *    and repeated runs give bit-identical outputs (no floating-point atomics).
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define POND_OK 0
+#define POND_E_ARG (-1)           /* invalid argument (band, DM, period, sizes, null pointer) */
+#define POND_E_NFFT (-2)          /* nfft not a power of two, outside the supported range,
+                                     or not longer than the overlap (no valid output; Sec. 3.7:
+                                     the filter must exceed the dispersion smear) */
+#define POND_E_NCHAN (-3)         /* nchan not a power of two dividing nfft/2, or too many */
+#define POND_E_OOM (-4)           /* device or pinned-host allocation failed */
+#define POND_E_CUDA (-5)          /* a CUDA runtime call failed */
+#define POND_E_STATE (-6)         /* call not allowed in this state (e.g. push after flush) */
+#define POND_E_OVERRUN (-7)       /* an output buffer would overflow */
+#define POND_E_TIMEOUT (-8)       /* a bounded device wait expired */
+#define POND_E_UNIMPLEMENTED (-9) /* option not supported by this build */
+
+/* Arithmetic of the FFT stages. */
+#define POND_FP32 0        /* FP32 butterflies (CUDA cores) */
+#define POND_SPLIT_BF16 1  /* reserved: split-BF16 tensor-core stages */
+
+typedef struct pond_s* pond_t;
+
+/* Full plan description for pond_plan_ex.  Zero-initialise, then set fields. */
+typedef struct {
+  double f0_mhz;        /* band centre (Sec. 3.7: f0 of Eq. 4) */
+  double bw_mhz;        /* bandwidth; negative = inverted sideband */
+  double fs_hz;         /* real samples per second, = 2 |bw| 1e6, a whole number */
+  double dm;            /* dispersion measure, >= 0 */
+  int64_t nfft;         /* real samples per overlap-save segment, power of two */
+  int32_t nchan;        /* detected sub-channels, power of two dividing nfft/2 */
+  int32_t nbins;        /* fold bins, 1..4096 */
+  double period_s;      /* folding period, > 0 */
+  double t_dec_s;       /* time-series resolution; rounded to whole ns; 0 -> 61.44e-6 */
+  int32_t epoch_mjd_day;/* time of the first stream sample: MJD day ... */
+  double epoch_mjd_sec; /* ... and seconds into that day (reported in pond_meta) */
+  int32_t precision;    /* POND_FP32 */
+  int32_t want_voltages;/* nonzero: keep dedispersed voltages for pond_voltages (tests) */
+  int32_t timing;       /* nonzero: time each GPU stage with CUDA events (pond_stats) */
+  int32_t device;       /* CUDA device ordinal */
+  int32_t reserved[8];
+} pond_opts;
+
+/* Fold metadata returned with a profile snapshot. */
+typedef struct {
+  int32_t epoch_mjd_day;  /* epoch of phase 0 = time of the first stream sample */
+  double epoch_mjd_sec;
+  double period_s;
+  double dm;
+  double dtc_s;           /* channel sample time, 2 nchan / fs */
+  int64_t first_g;        /* first emitted channel sample (= n_past) */
+  int64_t nsamples;       /* channel samples folded so far */
+  int32_t nbins;
+} pond_meta;
+
+/* Counters and per-stage GPU time (ms; stage times only with opts.timing). */
+#define POND_NSTAGE 8
+typedef struct {
+  int64_t samples_in;       /* int8 samples accepted */
+  int64_t segments;         /* segments processed */
+  int64_t outputs;          /* channel samples emitted (detected, folded, decimated) */
+  int64_t n_past, n_fut;    /* overlap discarded at each segment edge, channel samples */
+  int64_t seg_step;         /* real samples between segment starts */
+  int32_t nfft, nchan;
+  int32_t kernel_launches;  /* kernels launched per segment */
+  int32_t flushed;
+  double stage_ms[POND_NSTAGE];   /* accumulated GPU time per stage */
+  int64_t stage_launches[POND_NSTAGE];
+  double algo_bytes[POND_NSTAGE]; /* algorithmic DRAM bytes per launch of each stage */
+  const char* stage_name[POND_NSTAGE];
+} pond_stats_t;
+
+/*
+ * pond_plan / pond_plan_ex: create a handle for one stream.
+ *   out     : receives the handle (set to NULL on error).
+ *   The plan derives the overlap-save geometry: n_past = ceil(K DM (f0^-2 -
+ *   f_hi^-2) / dtc), n_fut = ceil(K DM (f_lo^-2 - f0^-2) / dtc) channel
+ *   samples (Sec. 3.7: the impulse response must span the smear), the
+ *   segment step S_c = M - n_past - n_fut channel samples (S = 2 nchan S_c real
+ *   samples), and builds the FFT twiddle and chirp tables on the device in FP64.
+ *   Supported: 2^5 <= nfft <= 2^25; nchan <= 2048 with M = nfft/(2 nchan) >= 16.
+ *   Errors: POND_E_ARG, POND_E_NFFT, POND_E_NCHAN, POND_E_OOM, POND_E_CUDA,
+ *   POND_E_UNIMPLEMENTED (precision other than POND_FP32).
+ * pond_plan uses t_dec = 61.44 us, epoch 0, FP32, device 0.
+ */
+int pond_plan(pond_t* out, double f0_mhz, double bw_mhz, double fs_hz, double dm,
+              int64_t nfft, int32_t nchan, int32_t nbins, double period_s);
+int pond_plan_ex(pond_t* out, const pond_opts* opts);
+
+/*
+ * pond_push: append n int8 samples from HOST memory x (any n >= 0).  The data
+ *   are copied to the device before the call returns (pinned memory copies
+ *   asynchronously, pageable memory through the driver's staging), so x may be
+ *   reused at once; processing of complete segments continues asynchronously.
+ *   Errors: POND_E_ARG (x NULL with n > 0), POND_E_STATE (after pond_flush),
+ *   POND_E_CUDA.
+ */
+int pond_push(pond_t h, const int8_t* x, size_t n);
+
+/*
+ * pond_push_device: append n int8 samples already in DEVICE memory d_x.  All
+ *   work is enqueued on cuda_stream (a cudaStream_t; NULL = the handle's own
+ *   stream, which then waits for the legacy default stream), in stream order,
+ *   and reads d_x directly for segments that lie inside it.  d_x must stay
+ *   valid and unmodified until the work enqueued on cuda_stream has finished;
+ *   the library itself does not touch d_x after that work completes.
+ *   Errors: as pond_push.
+ */
+int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream);
+
+/*
+ * pond_flush: end of stream.  Processes the zero-padded tail and emits every
+ *   output whose support lies inside the stream (g < floor(n_total/(2 nchan))
+ *   - n_fut), then waits for the device.  Further pushes return POND_E_STATE.
+ */
+int pond_flush(pond_t h);
+
+/*
+ * pond_sync: wait until all work enqueued for the handle has finished.
+ */
+int pond_sync(pond_t h);
+
+/*
+ * pond_reset: start a new stream with the same plan.  Waits for the device,
+ *   then clears the profile, the time series, the kept voltages, the carried
+ *   samples and the counters; the plan's tables and buffers are kept.
+ */
+int pond_reset(pond_t h);
+
+/*
+ * pond_profile: snapshot of the folded profile (non-destructive; waits for the
+ *   device).  sum[b] (FP64) is the sum of detected power P[g] over the channel
+ *   samples folded into bin b = min(floor(frac(g dtc / P) nbins), nbins-1)
+ *   (phase in FP64, epoch = first stream sample), hits[b] their count; the
+ *   mean profile is sum/hits.  sum and hits hold nbins entries; either may be
+ *   NULL.  meta may be NULL.  Errors: POND_E_ARG, POND_E_CUDA.
+ */
+int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta);
+
+/*
+ * pond_timeseries: drain completed samples of the decimated time series.
+ *   Sample j sums P[g] over the emitted g with floor(g / D) = j, where
+ *   D = t_dec fs / (2 nchan) channel samples (an exact rational; with 4 us
+ *   channel samples and t_dec = 61.44 us, bins hold 15 or 16 samples).
+ *   counts[j] (nullable) is the number of channel samples summed; the first
+ *   and last samples of a stream may be partial.  Copies at most cap samples
+ *   into out; *n_out receives the number copied and *first_index the j of
+ *   out[0] (both required).  Samples are complete once every g they cover has
+ *   been processed; after pond_flush all remaining samples are complete.
+ */
+int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n_out,
+                    int64_t* first_index);
+
+/*
+ * pond_voltages: drain dedispersed sub-channel voltages v_c[g] (complex, FP32
+ *   re/im pairs) of the emitted channel samples; only with opts.want_voltages.
+ *   out_c is laid out [nchan][cap][2]; at most cap samples per channel are
+ *   copied; *n_out receives the number per channel, *first_g the g of the first.
+ *   Errors: POND_E_STATE when the plan was made without want_voltages.
+ */
+int pond_voltages(pond_t h, float* out_c, size_t cap, size_t* n_out, int64_t* first_g);
+
+/* pond_stats: counters and per-stage GPU times (waits for the device). */
+int pond_stats(pond_t h, pond_stats_t* s);
+
+/* pond_strerror: static text for a return code.  pond_last_error: message of the
+ * calling thread's last failure (empty if none). */
+const char* pond_strerror(int code);
+const char* pond_last_error(void);
+
+/* pond_destroy: wait for the device, release everything the handle owns.
+ * NULL is accepted. */
+int pond_destroy(pond_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POND_H */

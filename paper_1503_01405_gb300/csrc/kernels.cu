@@ -1,0 +1,490 @@
+// Segment kernels of the coherent-dedispersion path (PONDER Sec. 3.7).
+//
+// One overlap-save segment of N real int8 samples goes through four FFT passes
+// over a spectrum of L = N/2 complex bins, then fold and decimation:
+//
+//  F1 k_fwd_cols   : unpack z[n] = x[2n] + i x[2n+1]; length-R2 FFTs down the
+//                    R1 columns n1 of z viewed as [R2][R1]; multiply by
+//                    exp(-2 pi i n1 k2 / L); store in place of the column.
+//  F2 k_fwd_rows   : length-R1 FFTs along the rows k2 (Z[k2 + R2 k1]); rows k2
+//                    and R2-k2 share a CTA so the real-input split
+//                    X[k] = (Z[k] + Z*[L-k])/2 - i e^{-i pi k/L} (Z[k] - Z*[L-k])/2
+//                    is local; multiply by the inverse ISM response (Eq. 4);
+//                    store Y[k] in natural order.
+//  I1 k_inv_cols   : per sub-channel c (bins cM..cM+M-1), inverse length-Q2
+//                    FFTs down the Q1 columns j1, multiply by exp(+2 pi i j1 m2 / M).
+//  I2 k_inv_rows   : inverse length-Q1 FFTs along rows m2 for all sub-channels
+//                    of the same m2 in one CTA: v_c[m2 + Q2 m1] / M, keep the
+//                    valid span n_past <= m < M - n_fut, detect |v|^2 and sum
+//                    over sub-channels into P (and optionally store v).
+//  k_fold_partial / k_fold_merge : deterministic fold of P (FP64 phase).
+//  k_decimate      : deterministic decimation of P into the time series.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_block.cuh"
+#include "pond_internal.h"
+
+namespace pond {
+
+// ---------------------------------------------------------------------------
+// Tables (built once per plan, FP64 on the device)
+// ---------------------------------------------------------------------------
+
+__global__ void k_make_twiddles(float2* tw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < TW_N) {
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)TW_N, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+  }
+}
+
+// Anchor a covers bins k = 256 a + d - 128 ... (d in [0, 256)); it holds the
+// Taylor coefficients of the dedispersion phase phi(k) = sgn * c(f_k) (cycles)
+// about k_a = 256 a + 128: phi(k_a) and phi'(k_a) reduced mod 1 in Q0.32 fixed
+// point, phi''/2 and phi'''/6 in FP32.  c(f) = alpha f^2 / (f0 + f) with
+// alpha = K 1e6 DM / f0^2 (Eq. 4), f = k du - |bw|/2 (upper sideband) or
+// |bw|/2 - k du (inverted).
+__global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, double du, double half,
+                                     double f0, double alpha, int sgn) {
+  const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nanc) return;
+  const double ka = (double)(a * CHIRP_SPAN + CHIRP_SPAN / 2);
+  const double f = sgn > 0 ? __dsub_rn(__dmul_rn(ka, du), half) : __dsub_rn(half, __dmul_rn(ka, du));
+  const double g = f0 + f;
+  const double q = f0 * f0 / (g * g);
+  const double c = alpha * f * f / g;
+  const double d1 = alpha * (1.0 - q);
+  const double d2 = 2.0 * alpha * q / g;
+  const double d3 = -6.0 * alpha * q / (g * g);
+  const double phi0 = sgn * c;
+  const double phi1 = du * d1;
+  const double phi2 = sgn * du * du * d2 * 0.5;
+  const double phi3 = du * du * du * d3 / 6.0;
+  const double fr0 = phi0 - floor(phi0);
+  const double fr1 = phi1 - floor(phi1);
+  ChirpAnchor r;
+  r.p0 = (unsigned)((unsigned long long)llrint(fr0 * 4294967296.0) & 0xffffffffull);
+  r.p1 = (unsigned)((unsigned long long)llrint(fr1 * 4294967296.0) & 0xffffffffull);
+  r.p2 = (float)phi2;
+  r.p3 = (float)phi3;
+  anc[a] = r;
+}
+
+// exp(-2 pi i phi(k)) from the anchor table (phase error < 1e-7 cycles).
+__device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ anc, unsigned k) {
+  const ChirpAnchor a = anc[k >> CHIRP_LOG];
+  const int d = (int)(k & (CHIRP_SPAN - 1)) - CHIRP_SPAN / 2;
+  const unsigned u = a.p0 + a.p1 * (unsigned)d;           // mod 2^32: phase mod 1 cycle
+  const float df = (float)d;
+  float r = (float)(int)u * 2.3283064365386963e-10f;      // 2^-32
+  r += fmaf(a.p3, df, a.p2) * (df * df);
+  float s, c;
+  sincospif(2.0f * r, &s, &c);
+  return make_float2(c, -s);
+}
+
+// ---------------------------------------------------------------------------
+// F1: unpack + column FFTs of the forward transform
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
+  if (r < in.a_len) return (float)in.a[r];
+  r -= in.a_len;
+  if (r < in.b_len) return (float)in.b[r];
+  return 0.f;
+}
+
+template <int R2>
+__global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1,
+                                                 int logL, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  constexpr int LSTR = line_stride(R2);
+  const int R1 = 1 << logR1;
+  const int nl = min(TILE / R2, R1);
+  const int lognl = __ffs(nl) - 1;
+  const int n1_0 = blockIdx.x * nl;
+  for (int idx = threadIdx.x; idx < nl * R2; idx += NT) {
+    const int n2 = idx >> lognl, b = idx & (nl - 1);
+    const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
+    sm[pidx(b, n2, LSTR)] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+  }
+  __syncthreads();
+  block_fft<R2, false>(sm, nl, tw);
+  const unsigned lmask = (1u << logL) - 1;
+  const float escale = exp2f(1.0f - (float)logL);   // 2/L, exact
+  for (int idx = threadIdx.x; idx < nl * R2; idx += NT) {
+    const int k2 = idx >> lognl, b = idx & (nl - 1);
+    const unsigned n1 = (unsigned)(n1_0 + b);
+    const unsigned e = (n1 * (unsigned)k2) & lmask;
+    float s, c;
+    sincospif(-(float)e * escale, &s, &c);
+    out[(size_t)n1 + ((size_t)k2 << logR1)] = cmul(sm[pidx(b, k2, LSTR)], make_float2(c, s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// F2: row FFTs + real-input split + dedispersion chirp
+// ---------------------------------------------------------------------------
+
+template <int R1>
+__global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
+                                                 int logR2, int logL, const ChirpAnchor* __restrict__ anc,
+                                                 int apply_chirp, const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  constexpr int LSTR = line_stride(R1);
+  constexpr int LOGR1 = ilog2c(R1);
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);   // 2 * pairs
+  const int np = nl >> 1;
+  const int lognl = __ffs(nl) - 1;
+  const int q0 = blockIdx.x * np;
+  auto line_of = [&](int slot) -> int {
+    if (slot < np) return q0 + slot;
+    const int t = slot - np;
+    if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
+    return R2 - (q0 + t);
+  };
+  for (int idx = threadIdx.x; idx < nl * R1; idx += NT) {
+    const int slot = idx >> LOGR1, e = idx & (R1 - 1);
+    sm[pidx(slot, e, LSTR)] = in[((size_t)line_of(slot) << LOGR1) + e];
+  }
+  __syncthreads();
+  block_fft<R1, false>(sm, nl, tw);
+  const unsigned lmask = (1u << logL) - 1;
+  const float kscale = exp2f(-(float)logL);        // 1/L, exact
+  for (int idx = threadIdx.x; idx < nl * R1; idx += NT) {
+    const int k1 = idx >> lognl, slot = idx & (nl - 1);
+    const int line = line_of(slot);
+    const unsigned k = (unsigned)line + ((unsigned)k1 << logR2);
+    const unsigned kp = (0u - k) & lmask;
+    const int linep = (int)(kp & (unsigned)(R2 - 1));
+    const int k1p = (int)(kp >> logR2);
+    const int slotp = (linep == line) ? slot : (slot < np ? slot + np : slot - np);
+    const float2 A = sm[pidx(slot, k1, LSTR)];
+    const float2 B = cconj(sm[pidx(slotp, k1p, LSTR)]);
+    const float2 E = cscale(cadd(A, B), 0.5f);
+    const float2 O = cscale(csub(A, B), 0.5f);
+    float s, c;
+    sincospif(-(float)k * kscale, &s, &c);          // exp(-i pi k / L)
+    float2 X = cadd(E, rot90<false>(cmul(make_float2(c, s), O)));
+    if (apply_chirp) X = cmul(X, chirp_factor(anc, k));
+    out[k] = X;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// I1: per-sub-channel inverse column FFTs
+// ---------------------------------------------------------------------------
+
+template <int Q2>
+__global__ void __launch_bounds__(NT) k_inv_cols(float2* __restrict__ buf, int logQ1, int logM, int nchan,
+                                                 const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  constexpr int LSTR = line_stride(Q2);
+  const int Q1 = 1 << logQ1;
+  const int nl = min(TILE / Q2, nchan * Q1);
+  const int lognl = __ffs(nl) - 1;
+  const int l0 = blockIdx.x * nl;
+  for (int idx = threadIdx.x; idx < nl * Q2; idx += NT) {
+    const int j2 = idx >> lognl, b = idx & (nl - 1);
+    const int l = l0 + b;
+    const size_t addr = ((size_t)(l >> logQ1) << logM) + (l & (Q1 - 1)) + ((size_t)j2 << logQ1);
+    sm[pidx(b, j2, LSTR)] = buf[addr];
+  }
+  __syncthreads();
+  block_fft<Q2, true>(sm, nl, tw);
+  const unsigned mmask = (1u << logM) - 1;
+  const float escale = exp2f(1.0f - (float)logM);   // 2/M
+  for (int idx = threadIdx.x; idx < nl * Q2; idx += NT) {
+    const int m2 = idx >> lognl, b = idx & (nl - 1);
+    const int l = l0 + b;
+    const unsigned j1 = (unsigned)(l & (Q1 - 1));
+    const unsigned e = (j1 * (unsigned)m2) & mmask;
+    float s, c;
+    sincospif((float)e * escale, &s, &c);           // exp(+2 pi i j1 m2 / M)
+    const size_t addr = ((size_t)(l >> logQ1) << logM) + j1 + ((size_t)m2 << logQ1);
+    buf[addr] = cmul(sm[pidx(b, m2, LSTR)], make_float2(c, s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// I2: inverse row FFTs, discard, detect, sum over sub-channels
+// ---------------------------------------------------------------------------
+
+template <int Q1>
+__global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf, float* __restrict__ P,
+                                                 float2* __restrict__ vout, long long vstride,
+                                                 long long vofs, int logQ2, int logM, int nchan,
+                                                 int m_lo, int m_hi, float scale,
+                                                 const float2* __restrict__ tw) {
+  extern __shared__ float2 sm[];
+  constexpr int LSTR = line_stride(Q1);
+  constexpr int LOGQ1 = ilog2c(Q1);
+  const int Q2 = 1 << logQ2;
+  const int b2 = min(TILE / (Q1 * nchan), Q2);
+  const int logb2 = __ffs(b2) - 1;
+  const int nl = nchan * b2;
+  const int m2_0 = blockIdx.x * b2;
+  for (int idx = threadIdx.x; idx < nl * Q1; idx += NT) {
+    const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
+    const int c = slot >> logb2, bb = slot & (b2 - 1);
+    sm[pidx(slot, e, LSTR)] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
+  }
+  __syncthreads();
+  block_fft<Q1, true>(sm, nl, tw);
+  for (int idx = threadIdx.x; idx < b2 * Q1; idx += NT) {
+    const int m1 = idx >> logb2, bb = idx & (b2 - 1);
+    const int m = m2_0 + bb + (m1 << logQ2);
+    if (m < m_lo || m >= m_hi) continue;
+    float p = 0.f;
+    for (int c = 0; c < nchan; ++c) {
+      const float2 v = cscale(sm[pidx((c << logb2) + bb, m1, LSTR)], scale);
+      p = fmaf(v.x, v.x, p);
+      p = fmaf(v.y, v.y, p);
+      if (vout) vout[(size_t)c * vstride + vofs + (m - m_lo)] = v;
+    }
+    P[m - m_lo] = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fold (Sec. 3.4 fold thread): deterministic per-warp histograms
+// ---------------------------------------------------------------------------
+
+constexpr int FOLD_WARPS = 4;
+
+// bin(g) = min(floor(frac(g * inc) * nbins), nbins - 1), FP64, correctly rounded.
+__device__ __forceinline__ int fold_bin(long long g, double inc, int nbins) {
+  const double x = __dmul_rn((double)g, inc);
+  const double ph = __dsub_rn(x, floor(x));
+  const int b = (int)__dmul_rn(ph, (double)nbins);
+  return b < nbins - 1 ? b : nbins - 1;
+}
+
+__global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* __restrict__ P, long long n,
+                                                                  long long g0, double inc, int nbins,
+                                                                  long long chunk, double* __restrict__ psum,
+                                                                  int* __restrict__ phits) {
+  extern __shared__ unsigned char fsm[];
+  double* hsum = reinterpret_cast<double*>(fsm);                  // [FOLD_WARPS][nbins]
+  int* hcnt = reinterpret_cast<int*>(hsum + FOLD_WARPS * nbins);  // [FOLD_WARPS][nbins]
+  float* pbuf = reinterpret_cast<float*>(hcnt + FOLD_WARPS * nbins);  // [FOLD_WARPS][32]
+  for (int i = threadIdx.x; i < FOLD_WARPS * nbins; i += blockDim.x) {
+    hsum[i] = 0.0;
+    hcnt[i] = 0;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long c0 = (long long)blockIdx.x * chunk;
+  const long long c1 = min(n, c0 + chunk);
+  double* myh = hsum + w * nbins;
+  int* myc = hcnt + w * nbins;
+  float* mybuf = pbuf + w * 32;
+  for (long long base = c0 + w * 32; base < c1; base += FOLD_WARPS * 32) {
+    const long long i = base + lane;
+    const bool ok = i < c1;
+    int b = -1;
+    float p = 0.f;
+    if (ok) {
+      b = fold_bin(g0 + i, inc, nbins);
+      p = P[i];
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, b);
+    mybuf[lane] = p;
+    __syncwarp();
+    if (ok && lane == __ffs(peers) - 1) {
+      float s = 0.f;
+      unsigned m = peers;
+      while (m) {
+        s += mybuf[__ffs(m) - 1];
+        m &= m - 1;
+      }
+      myh[b] += (double)s;
+      myc[b] += __popc(peers);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double s = 0.0;
+    int h = 0;
+#pragma unroll
+    for (int k = 0; k < FOLD_WARPS; ++k) {
+      s += hsum[k * nbins + b];
+      h += hcnt[k * nbins + b];
+    }
+    psum[(size_t)blockIdx.x * nbins + b] = s;
+    phits[(size_t)blockIdx.x * nbins + b] = h;
+  }
+}
+
+__global__ void k_fold_merge(const double* __restrict__ psum, const int* __restrict__ phits, int nparts,
+                             int nbins, double* __restrict__ prof_sum, long long* __restrict__ prof_hits) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbins) return;
+  double s = 0.0;
+  long long h = 0;
+  for (int k = 0; k < nparts; ++k) {
+    s += psum[(size_t)k * nbins + b];
+    h += phits[(size_t)k * nbins + b];
+  }
+  prof_sum[b] += s;
+  prof_hits[b] += h;
+}
+
+// ---------------------------------------------------------------------------
+// Decimation: T[j] += sum of P[g], floor(g den / num) = j; one warp per j
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+__global__ void k_decimate(const float* __restrict__ P, long long n, long long g0, long long num,
+                           long long den, long long j_lo, long long nj, float* __restrict__ T,
+                           int* __restrict__ C, long long ring) {
+  const long long jj = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (jj >= nj) return;
+  const long long j = j_lo + jj;
+  long long ga = ceil_div_ll(j * num, den), gb = ceil_div_ll((j + 1) * num, den);
+  ga = max(ga, g0);
+  gb = min(gb, g0 + n);
+  float s = 0.f;
+  for (long long g = ga + lane; g < gb; g += 32) s += P[g - g0];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    const long long slot = j % ring;
+    T[slot] += s;
+    C[slot] += (int)(gb - ga);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+template <int R>
+static size_t smem_bytes(int nl) {
+  return (size_t)nl * line_stride(R) * sizeof(float2);
+}
+
+// Largest padded tile over the line lengths 4..4096 (R = 4: 2048 lines of 5).
+static size_t max_tile_smem_bytes() {
+  size_t m = 0;
+  for (int R = 4; R <= 4096; R *= 2) m = std::max(m, (size_t)(TILE / R) * (R + R / 16 + 1) * sizeof(float2));
+  return m;
+}
+
+#define POND_FOR_R(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+cudaError_t set_kernel_attributes() {
+  const int max_smem = (int)max_tile_smem_bytes();
+  cudaError_t e = cudaSuccess;
+#define SET_ATTR(R)                                                                                   \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  POND_FOR_R(SET_ATTR)
+#undef SET_ATTR
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
+  return e;
+}
+
+cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, double du, double half, double f0,
+                          double alpha, int sgn, cudaStream_t st) {
+  k_make_twiddles<<<TW_N / 256, 256, 0, st>>>(tw);
+  k_make_chirp_anchors<<<(unsigned)((nanc + 127) / 128), 128, 0, st>>>(anc, nanc, du, half, f0, alpha, sgn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R2, R1);
+  const unsigned grid = (unsigned)(R1 / nl);
+  switch (R2) {
+#define CASE(R) case R: k_fwd_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR1, g.logL, tw); break;
+    POND_FOR_R(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int apply_chirp,
+                            const float2* tw, cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R1, R2);
+  const unsigned grid = (unsigned)(R2 / nl);
+  switch (R1) {
+#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, anc, apply_chirp, tw); break;
+    POND_FOR_R(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_cols(const Geom& g, float2* buf, const float2* tw, cudaStream_t st) {
+  const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
+  const int lines = g.nchan * Q1;
+  const int nl = std::min(TILE / Q2, lines);
+  const unsigned grid = (unsigned)(lines / nl);
+  switch (Q2) {
+#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, g.logQ1, g.logM, g.nchan, tw); break;
+    POND_FOR_R(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
+                            long long vofs, int m_hi, const float2* tw, cudaStream_t st) {
+  const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
+  const int b2 = std::min(TILE / (Q1 * g.nchan), Q2);
+  const int nl = g.nchan * b2;
+  const unsigned grid = (unsigned)(Q2 / b2);
+  const float scale = 1.0f / (float)(1u << g.logM);
+  switch (Q1) {
+#define CASE(R) case R: k_inv_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, (int)g.n_past, m_hi, scale, tw); break;
+    POND_FOR_R(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+size_t fold_smem_bytes(int nbins) {
+  return (size_t)FOLD_WARPS * nbins * (sizeof(double) + sizeof(int)) + FOLD_WARPS * 32 * sizeof(float);
+}
+
+int fold_parts(long long n, long long* chunk) {
+  long long c = std::max<long long>(2048, (n + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS);
+  c = (c + 127) / 128 * 128;
+  *chunk = c;
+  return (int)((n + c - 1) / c);
+}
+
+cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,
+                        int* phits, double* prof_sum, long long* prof_hits, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long chunk;
+  const int parts = fold_parts(n, &chunk);
+  k_fold_partial<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, chunk, psum, phits);
+  k_fold_merge<<<(nbins + 127) / 128, 128, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(const float* P, long long n, long long g0, long long num, long long den,
+                            long long j_lo, long long nj, float* T, int* C, long long ring, cudaStream_t st) {
+  if (n <= 0 || nj <= 0) return cudaSuccess;
+  const long long threads = nj * 32;
+  k_decimate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, n, g0, num, den, j_lo, nj, T, C, ring);
+  return cudaGetLastError();
+}
+
+}  // namespace pond

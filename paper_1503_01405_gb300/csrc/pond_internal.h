@@ -1,0 +1,58 @@
+// Internal types shared by the kernels and the C-ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+namespace pond {
+
+constexpr int CHIRP_LOG = 8;                 // bins per chirp anchor = 2^CHIRP_LOG
+constexpr int CHIRP_SPAN = 1 << CHIRP_LOG;
+constexpr int MAX_NBINS = 4096;              // fold bins (per-warp FP64 histograms in smem)
+constexpr int MAX_FOLD_PARTS = 304;          // fold CTAs per segment (2 per SM)
+
+// Taylor coefficients of the dedispersion phase about an anchor bin.
+struct __align__(16) ChirpAnchor {
+  unsigned p0;   // phi(k_a) mod 1, Q0.32
+  unsigned p1;   // phi'(k_a) mod 1 (cycles per bin), Q0.32
+  float p2;      // phi''(k_a) / 2
+  float p3;      // phi'''(k_a) / 6
+};
+
+// A segment's int8 input as up to two runs: samples [0, a_len) from a,
+// [a_len, a_len + b_len) from b, zeros beyond.
+struct SegIn {
+  const int8_t* a;
+  long long a_len;
+  const int8_t* b;
+  long long b_len;
+};
+
+// Geometry of a plan: segment and pass decomposition.
+struct Geom {
+  long long N, L, M;     // real samples per segment, spectrum bins kept, samples per sub-channel
+  int nchan;
+  int logL, logM;
+  int logR1, logR2;      // forward: L = R1 * R2 (F2 rows of R1, F1 columns of R2)
+  int logQ1, logQ2;      // inverse: M = Q1 * Q2 (I2 rows of Q1, I1 columns of Q2)
+  long long n_past, n_fut, S_c, S;
+};
+
+cudaError_t set_kernel_attributes();
+cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, double du, double half, double f0,
+                          double alpha, int sgn, cudaStream_t st);
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int apply_chirp,
+                            const float2* tw, cudaStream_t st);
+cudaError_t launch_inv_cols(const Geom& g, float2* buf, const float2* tw, cudaStream_t st);
+cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
+                            long long vofs, int m_hi, const float2* tw, cudaStream_t st);
+size_t fold_smem_bytes(int nbins);
+int fold_parts(long long n, long long* chunk);
+cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,
+                        int* phits, double* prof_sum, long long* prof_hits, cudaStream_t st);
+cudaError_t launch_decimate(const float* P, long long n, long long g0, long long num, long long den,
+                            long long j_lo, long long nj, float* T, int* C, long long ring, cudaStream_t st);
+
+}  // namespace pond

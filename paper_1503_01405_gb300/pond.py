@@ -1,0 +1,241 @@
+"""ctypes binding of libpond.so: the C ABI of include/pond.h, argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts
+Python/numpy/torch arguments to pointers and sizes and raises ``PondError`` on
+a negative return code.  It fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpond.so")
+
+POND_OK = 0
+POND_E_ARG = -1
+POND_E_NFFT = -2
+POND_E_NCHAN = -3
+POND_E_OOM = -4
+POND_E_CUDA = -5
+POND_E_STATE = -6
+POND_E_OVERRUN = -7
+POND_E_TIMEOUT = -8
+POND_E_UNIMPLEMENTED = -9
+POND_FP32 = 0
+POND_SPLIT_BF16 = 1
+POND_NSTAGE = 8
+
+CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", POND_E_OOM: "OOM",
+              POND_E_CUDA: "CUDA", POND_E_STATE: "STATE", POND_E_OVERRUN: "OVERRUN",
+              POND_E_TIMEOUT: "TIMEOUT", POND_E_UNIMPLEMENTED: "UNIMPLEMENTED"}
+
+# Functions declared in include/pond.h.
+EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_flush", "pond_sync",
+           "pond_reset",
+           "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
+           "pond_last_error", "pond_destroy"]
+
+
+class PondError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{CODE_NAMES.get(code, code)}: {msg}")
+        self.code = code
+        self.name = CODE_NAMES.get(code, str(code))
+
+
+class pond_opts(ctypes.Structure):
+    _fields_ = [("f0_mhz", ctypes.c_double), ("bw_mhz", ctypes.c_double), ("fs_hz", ctypes.c_double),
+                ("dm", ctypes.c_double), ("nfft", ctypes.c_int64), ("nchan", ctypes.c_int32),
+                ("nbins", ctypes.c_int32), ("period_s", ctypes.c_double), ("t_dec_s", ctypes.c_double),
+                ("epoch_mjd_day", ctypes.c_int32), ("epoch_mjd_sec", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("want_voltages", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
+class pond_meta(ctypes.Structure):
+    _fields_ = [("epoch_mjd_day", ctypes.c_int32), ("epoch_mjd_sec", ctypes.c_double),
+                ("period_s", ctypes.c_double), ("dm", ctypes.c_double), ("dtc_s", ctypes.c_double),
+                ("first_g", ctypes.c_int64), ("nsamples", ctypes.c_int64), ("nbins", ctypes.c_int32)]
+
+
+class pond_stats_t(ctypes.Structure):
+    _fields_ = [("samples_in", ctypes.c_int64), ("segments", ctypes.c_int64), ("outputs", ctypes.c_int64),
+                ("n_past", ctypes.c_int64), ("n_fut", ctypes.c_int64), ("seg_step", ctypes.c_int64),
+                ("nfft", ctypes.c_int32), ("nchan", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("flushed", ctypes.c_int32), ("stage_ms", ctypes.c_double * POND_NSTAGE),
+                ("stage_launches", ctypes.c_int64 * POND_NSTAGE),
+                ("algo_bytes", ctypes.c_double * POND_NSTAGE),
+                ("stage_name", ctypes.c_char_p * POND_NSTAGE)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpond.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run __graft_entry__.build() first")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    sig = {
+        "pond_plan": [P(vp), ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                      ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double],
+        "pond_plan_ex": [P(vp), P(pond_opts)],
+        "pond_push": [vp, vp, ctypes.c_size_t],
+        "pond_push_device": [vp, vp, ctypes.c_size_t, vp],
+        "pond_flush": [vp],
+        "pond_sync": [vp],
+        "pond_reset": [vp],
+        "pond_profile": [vp, vp, vp, P(pond_meta)],
+        "pond_timeseries": [vp, vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), P(ctypes.c_int64)],
+        "pond_voltages": [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), P(ctypes.c_int64)],
+        "pond_stats": [vp, P(pond_stats_t)],
+        "pond_strerror": [ctypes.c_int],
+        "pond_last_error": [],
+        "pond_destroy": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name in ("pond_strerror", "pond_last_error") else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != POND_OK:
+        msg = lib().pond_last_error().decode(errors="replace")
+        raise PondError(rc, msg or lib().pond_strerror(rc).decode())
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data if a is not None else 0
+
+
+class Engine:
+    """One coherent-dedispersion stream (a ``pond_t`` handle)."""
+
+    def __init__(self, f0: float, bw: float, fs: float, dm: float, nfft: int, nchan: int, nbins: int,
+                 period: float, t_dec: float = 61.44e-6, want_voltages: bool = False,
+                 timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
+                 precision: int = POND_FP32):
+        o = pond_opts()
+        o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
+        o.nfft, o.nchan, o.nbins, o.period_s = nfft, nchan, nbins, period
+        o.t_dec_s = t_dec
+        o.epoch_mjd_day, o.epoch_mjd_sec = int(epoch_mjd[0]), float(epoch_mjd[1])
+        o.precision = precision
+        o.want_voltages = int(bool(want_voltages))
+        o.timing = int(bool(timing))
+        o.device = device
+        self.nbins = nbins
+        self.nchan = nchan
+        h = ctypes.c_void_p()
+        _check(lib().pond_plan_ex(ctypes.byref(h), ctypes.byref(o)))
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def push(self, x: np.ndarray) -> None:
+        """Append host int8 samples (copied before return)."""
+        x = np.ascontiguousarray(x, dtype=np.int8)
+        _check(lib().pond_push(self._h, _ptr(x), x.size))
+
+    def push_device(self, ptr: int, n: int, stream: int = 0) -> None:
+        """Append n int8 samples at device address ptr, ordered on ``stream``."""
+        _check(lib().pond_push_device(self._h, ptr, n, stream))
+
+    def push_tensor(self, t, stream=None) -> None:
+        """Append a CUDA int8 tensor, ordered on ``stream`` (default: torch's current)."""
+        import torch
+        assert t.is_cuda and t.dtype == torch.int8 and t.is_contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(t.device)
+        self.push_device(t.data_ptr(), t.numel(), s.cuda_stream)
+
+    def flush(self) -> None:
+        _check(lib().pond_flush(self._h))
+
+    def sync(self) -> None:
+        _check(lib().pond_sync(self._h))
+
+    def reset(self) -> None:
+        """Start a new stream with the same plan."""
+        _check(lib().pond_reset(self._h))
+
+    def profile(self):
+        s = np.zeros(self.nbins, dtype=np.float64)
+        h = np.zeros(self.nbins, dtype=np.int64)
+        m = pond_meta()
+        _check(lib().pond_profile(self._h, _ptr(s), _ptr(h), ctypes.byref(m)))
+        meta = {f: getattr(m, f) for f, _ in pond_meta._fields_}
+        return s, h, meta
+
+    def timeseries(self, cap: int = 1 << 20):
+        """Drain every completed time-series sample: (T float32, counts int32, first index)."""
+        parts, cparts, first = [], [], None
+        while True:
+            out = np.zeros(cap, dtype=np.float32)
+            cnt = np.zeros(cap, dtype=np.int32)
+            n = ctypes.c_size_t()
+            j0 = ctypes.c_int64()
+            _check(lib().pond_timeseries(self._h, _ptr(out), _ptr(cnt), cap, ctypes.byref(n),
+                                         ctypes.byref(j0)))
+            if first is None:
+                first = j0.value
+            if n.value == 0:
+                break
+            parts.append(out[:n.value])
+            cparts.append(cnt[:n.value])
+            if n.value < cap:
+                break
+        T = np.concatenate(parts) if parts else np.zeros(0, np.float32)
+        C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
+        return T, C, first
+
+    def voltages(self, cap: int = 1 << 24):
+        """Drain dedispersed voltages: (complex64 [nchan, n], first g)."""
+        out = np.zeros((self.nchan, cap, 2), dtype=np.float32)
+        n = ctypes.c_size_t()
+        g0 = ctypes.c_int64()
+        _check(lib().pond_voltages(self._h, _ptr(out), cap, ctypes.byref(n), ctypes.byref(g0)))
+        v = out[:, :n.value, 0] + 1j * out[:, :n.value, 1]
+        return v.astype(np.complex64), g0.value
+
+    def stats(self) -> dict:
+        s = pond_stats_t()
+        _check(lib().pond_stats(self._h, ctypes.byref(s)))
+        d = {f: getattr(s, f) for f, _ in pond_stats_t._fields_ if f not in
+             ("stage_ms", "stage_launches", "algo_bytes", "stage_name")}
+        d["stages"] = {}
+        for i in range(POND_NSTAGE):
+            name = s.stage_name[i]
+            if name:
+                d["stages"][name.decode()] = {"ms": s.stage_ms[i], "launches": s.stage_launches[i],
+                                              "algo_bytes": s.algo_bytes[i]}
+        return d
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pond_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

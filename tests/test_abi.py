@@ -1,0 +1,97 @@
+"""The C ABI on a machine without a GPU: symbols, argument checks, error codes.
+
+No compute call runs here; plan validation happens on the host before any
+CUDA call, so bad plans return their code without a device.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import pcd
+from paper_1503_01405_gb300 import build as pbuild
+from paper_1503_01405_gb300 import pond
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pbuild.build()
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "pond.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pond_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function():
+    names = _header_functions()
+    assert len(names) >= 13
+    L = pond.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(pond.EXPORTS) == names
+
+
+def test_strerror_covers_codes():
+    L = pond.lib()
+    for code in range(0, -10, -1):
+        assert L.pond_strerror(code)
+    assert L.pond_strerror(-999) == b"unknown error"
+
+
+ORT = dict(f0=326.5, bw=16.0, fs=32e6)
+CASES = [
+    dict(nfft=3000),
+    dict(nfft=1 << 10, dm=3.0),
+    dict(nchan=3),
+    dict(nchan=1 << 12, nfft=1 << 12),
+    dict(dm=-1.0),
+    dict(period=0.0),
+    dict(fs=31e6),
+    dict(nbins=0),
+    dict(bw=0.0),
+]
+
+
+@pytest.mark.parametrize("kw", CASES)
+def test_plan_errors_match_oracle_rules(kw):
+    args = dict(**ORT, dm=0.5, nfft=1 << 16, nchan=4, nbins=64, period=0.1)
+    args.update(kw)
+    with pytest.raises(pcd.PlanError) as oe:
+        pcd.make_plan(**args)
+    with pytest.raises(pond.PondError) as ce:
+        pond.Engine(args["f0"], args["bw"], args["fs"], args["dm"], args["nfft"], args["nchan"],
+                    args["nbins"], args["period"])
+    assert ce.value.name == oe.value.code, (ce.value, oe.value)
+
+
+def test_engine_limits():
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 5000, 0.1)
+    assert e.value.name == "ARG"
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1, precision=pond.POND_SPLIT_BF16)
+    assert e.value.name == "UNIMPLEMENTED"
+
+
+def test_null_handle_and_pointers():
+    L = pond.lib()
+    assert L.pond_flush(None) == pond.POND_E_ARG
+    assert L.pond_destroy(None) == pond.POND_OK
+    assert L.pond_plan_ex(None, None) == pond.POND_E_ARG
+    h = ctypes.c_void_p()
+    assert L.pond_plan_ex(ctypes.byref(h), None) == pond.POND_E_ARG
+    assert h.value is None
+
+
+def test_valid_plan_without_gpu_reports_cuda():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1)
+    assert e.value.name == "CUDA"

@@ -1,0 +1,202 @@
+"""CUDA path vs the FP64 oracle, through the C ABI.
+
+Tolerances: relative L2 error <= 1e-5 on dedispersed voltages and <= 1e-4 on
+folded profiles and decimated series (FP32 engine vs FP64 oracle); fold hits,
+series counts and every index are exact (the fold bin is decided in FP64 on
+both sides with the same correctly rounded operations).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import pcd
+from paper_1503_01405_gb300 import pond, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-5
+TOL_P = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_01405_gb300 import build as pbuild
+    pbuild.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6):
+    with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
+                     want_voltages=want_voltages) as e:
+        if device_push:
+            import torch
+            t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+            pos = 0
+            for c in (chunks or [len(x)]):
+                e.push_tensor(t[pos:pos + c])
+                pos += c
+            torch.cuda.synchronize()
+        else:
+            pos = 0
+            for c in (chunks or [len(x)]):
+                e.push(x[pos:pos + c])
+                pos += c
+        e.flush()
+        s, h, meta = e.profile()
+        T, C, j0 = e.timeseries()
+        V, g0 = e.voltages() if want_voltages else (None, None)
+        st = e.stats()
+    return dict(s=s, h=h, meta=meta, T=T, C=C, j0=j0, V=V, g0=g0, stats=st)
+
+
+def check(out, r, voltages=True):
+    assert np.array_equal(out["h"], r.prof_hits)
+    assert np.array_equal(out["C"], r.ts_counts)
+    assert out["j0"] == r.ts_first
+    assert rel(out["s"], r.prof_sum) <= TOL_P
+    assert rel(out["T"], r.ts) <= TOL_P
+    if voltages:
+        assert out["g0"] == r.first_g
+        assert out["V"].shape == r.voltages.shape
+        ev = rel(out["V"], r.voltages)
+        assert ev <= TOL_V, ev
+        return ev
+    return None
+
+
+CONFIGS = [
+    # nfft, nchan, dm, bw, nbins, period
+    (1 << 10, 1, 0.002, 16.0, 16, 1.1e-3),
+    (1 << 14, 4, 0.05, 16.0, 64, 0.0123),
+    (1 << 14, 4, 0.05, -16.0, 64, 0.0123),
+    (1 << 16, 16, 0.3, 16.0, 128, 0.033),
+    (1 << 17, 64, 1.0, 16.0, 256, 0.05),
+    (1 << 18, 1, 0.5, 16.0, 256, 0.0317),
+    (1 << 20, 8, 2.0, -16.0, 512, 0.1),
+    (1 << 12, 2, 0.0, 16.0, 1, 0.01),
+    (1 << 15, 512, 0.0, 16.0, 32, 0.02),
+]
+
+
+def _stream(p, seed, extra):
+    spec = synth.StreamSpec(n=4 * p.S + p.nfft // 3 + extra, seed=seed, dm=p.dm, period=p.period,
+                            snr=60.0, duty=0.05, bw=p.bw, rfi_duty=0.005)
+    return synth.make_stream(spec)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: f"N{c[0]}_c{c[1]}_dm{c[2]}_bw{c[3]}")
+def test_matches_oracle(cfg):
+    nfft, nchan, dm, bw, nbins, period = cfg
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
+    x = _stream(p, seed=nfft + nchan, extra=17)
+    out = run_engine(x, p)
+    r = pcd.run(p, x, want_voltages=True)
+    check(out, r)
+    assert out["stats"]["outputs"] == len(r.power)
+
+
+def test_streaming_invariance_bit_exact():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.3, 1 << 16, 16, 128, 0.033)
+    x = _stream(p, seed=5, extra=999)
+    ref = run_engine(x, p)
+    rng = np.random.default_rng(1)
+    cuts = []
+    left = len(x)
+    while left > 0:
+        c = int(min(left, rng.choice([0, 1, 7, 1000, 65536, 100_000, 300_001])))
+        cuts.append(c)
+        left -= c
+    for dev in (False, True):
+        got = run_engine(x, p, chunks=cuts, device_push=dev)
+        for k in ("s", "h", "T", "C"):
+            assert np.array_equal(got[k], ref[k]), (k, dev)
+        assert np.array_equal(got["V"], ref["V"])
+        assert got["j0"] == ref["j0"] and got["g0"] == ref["g0"]
+
+
+def test_repeatable_bitwise():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 1.0, 1 << 17, 64, 256, 0.05)
+    x = _stream(p, seed=9, extra=3)
+    a = run_engine(x, p)
+    b = run_engine(x, p)
+    for k in ("s", "h", "T", "C", "V"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_small_workload_end_to_end():
+    """2^23 samples, DM 3, P 0.253 s, S/N 50; nfft 2^21, 1 channel, 256 bins."""
+    x = synth.make_stream(synth.SMALL)
+    p = pcd.make_plan(326.5, 16.0, 32e6, 3.0, 1 << 21, 1, 256, 0.253)
+    out = run_engine(x, p)
+    r = pcd.run(p, x, want_voltages=True)
+    ev = check(out, r)
+    assert out["stats"]["segments"] == 5
+    print(f"small workload: voltages rel L2 {ev:.3e}, profile {rel(out['s'], r.prof_sum):.3e}, "
+          f"series {rel(out['T'], r.ts):.3e}")
+
+
+def test_largest_nfft():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 1.0, 1 << 25, 1, 128, 0.2)
+    x = synth.make_stream(synth.StreamSpec(n=p.nfft + p.S // 2, seed=3, dm=1.0, period=0.2, snr=20.0))
+    out = run_engine(x, p)
+    r = pcd.run(p, x, want_voltages=True)
+    check(out, r)
+
+
+def test_tone_closed_form_on_gpu():
+    """The closed form of a pure tone (see the oracle pins) holds for the engine too."""
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.01, 4096, 4, 16, 1e-3)
+    k0 = (3 * p.L) // 7 + 5
+    A, theta = 7.5, 0.3
+    n = 6 * p.S + p.nfft
+    x = np.clip(np.rint(synth.tone(n, k0, p.nfft, A, theta)), -127, 127).astype(np.int8)
+    out = run_engine(x, p)
+    r = pcd.run(p, x, want_voltages=True)
+    check(out, r)
+
+
+def test_edge_streams():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.05, 1 << 14, 4, 64, 0.0123)
+    # empty stream
+    with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period) as e:
+        e.flush()
+        s, h, meta = e.profile()
+        T, C, j0 = e.timeseries()
+        assert h.sum() == 0 and len(T) == 0 and meta["nsamples"] == 0
+    # shorter than one segment, exactly one segment, one segment plus a byte
+    for n in (p.nfft // 2, p.nfft, p.nfft + 1, 2 * p.n_past * 2 * p.nchan + 3):
+        x = _stream(p, seed=n, extra=0)[:n]
+        out = run_engine(x, p)
+        r = pcd.run(p, x, want_voltages=True)
+        if len(r.power) == 0:
+            assert out["h"].sum() == 0 and len(out["T"]) == 0
+        else:
+            check(out, r)
+
+
+def test_state_errors():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.05, 1 << 14, 4, 64, 0.0123)
+    with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period) as e:
+        e.push(np.zeros(100, np.int8))
+        with pytest.raises(pond.PondError) as err:
+            e.voltages()
+        assert err.value.name == "STATE"
+        e.flush()
+        with pytest.raises(pond.PondError) as err:
+            e.push(np.zeros(10, np.int8))
+        assert err.value.name == "STATE"
+
+
+def test_decimation_options():
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.3, 1 << 16, 16, 128, 0.033, t_dec_s=7.3e-6)
+    x = _stream(p, seed=77, extra=5)
+    out = run_engine(x, p, t_dec=7.3e-6, want_voltages=False)
+    r = pcd.run(p, x)
+    check(out, r, voltages=False)
