@@ -96,6 +96,7 @@ struct pond_s {
   float2* tw = nullptr;
   ChirpAnchor* anc = nullptr;
   long long nanc = 0;
+  int clog = 0;
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
   double* psum = nullptr;
@@ -290,7 +291,7 @@ int run_segment(pond_t h, SegIn in, long long s, long long m_hi) {
   if ((rc = record(h, 0))) return rc;
   CK(launch_fwd_cols(g, in, h->bufA, h->tw, h->st));
   if ((rc = record(h, 1 + ST_F1))) return rc;
-  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->anc, 1, h->tw, h->st));
+  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->anc, h->clog, 1, h->tw, h->st));
   if ((rc = record(h, 1 + ST_F2))) return rc;
   CK(launch_inv_cols(g, h->bufB, h->tw, h->st));
   if ((rc = record(h, 1 + ST_I1))) return rc;
@@ -463,7 +464,16 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMalloc(&h->bufB, g.L * sizeof(float2)));
   CKD(cudaMalloc(&h->P, g.M * sizeof(float)));
   CKD(cudaMalloc(&h->tw, TW_N * sizeof(float2)));
-  h->nanc = (g.L + CHIRP_SPAN - 1) / CHIRP_SPAN;
+  const double du = o->fs_hz / (double)o->nfft * 1e-6;
+  const double half = std::fabs(o->bw_mhz) / 2.0;
+  const double alpha = K_DM * 1e6 * o->dm / (o->f0_mhz * o->f0_mhz);
+  {  // anchor span: the quartic Taylor term alpha f0^2/(f0+f)^5 (du span/2)^4 <= 1e-9 cycles
+    const double fmin = o->f0_mhz - half;
+    const double c4 = alpha * o->f0_mhz * o->f0_mhz / std::pow(fmin, 5);
+    h->clog = CHIRP_LOG_MAX;
+    while (h->clog > 0 && c4 * std::pow(du * (double)(1ll << (h->clog - 1)), 4) > 1e-9) --h->clog;
+  }
+  h->nanc = (g.L + (1ll << h->clog) - 1) >> h->clog;
   CKD(cudaMalloc(&h->anc, h->nanc * sizeof(ChirpAnchor)));
   CKD(cudaMalloc(&h->prof_sum, h->nbins * sizeof(double)));
   CKD(cudaMalloc(&h->prof_hits, h->nbins * sizeof(long long)));
@@ -482,10 +492,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
   CKD(cudaMemsetAsync(h->ts, 0, TS_RING * sizeof(float), h->st));
   CKD(cudaMemsetAsync(h->ts_cnt, 0, TS_RING * sizeof(int), h->st));
-  const double du = o->fs_hz / (double)o->nfft * 1e-6;
-  const double half = std::fabs(o->bw_mhz) / 2.0;
-  const double alpha = K_DM * 1e6 * o->dm / (o->f0_mhz * o->f0_mhz);
-  CKD(launch_tables(h->tw, h->anc, h->nanc, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  CKD(launch_tables(h->tw, h->anc, h->nanc, h->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
   CKD(cudaStreamSynchronize(h->st));
 #undef CKD
   *out = h;

@@ -40,17 +40,19 @@ __global__ void k_make_twiddles(float2* tw) {
   }
 }
 
-// Anchor a covers bins k = 256 a + d - 128 ... (d in [0, 256)); it holds the
+// Anchor a covers the 2^clog bins k = 2^clog a + d (d < 2^clog); it holds the
 // Taylor coefficients of the dedispersion phase phi(k) = sgn * c(f_k) (cycles)
-// about k_a = 256 a + 128: phi(k_a) and phi'(k_a) reduced mod 1 in Q0.32 fixed
-// point, phi''/2 and phi'''/6 in FP32.  c(f) = alpha f^2 / (f0 + f) with
-// alpha = K 1e6 DM / f0^2 (Eq. 4), f = k du - |bw|/2 (upper sideband) or
-// |bw|/2 - k du (inverted).
-__global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, double du, double half,
+// about k_a = 2^clog a + 2^(clog-1): phi(k_a) and phi'(k_a) reduced mod 1 in
+// Q0.32 fixed point, phi''/2 and phi'''/6 in FP32.  c(f) = alpha f^2 / (f0 + f)
+// with alpha = K 1e6 DM / f0^2 (Eq. 4), f = k du - |bw|/2 (upper sideband) or
+// |bw|/2 - k du (inverted).  The planner picks clog so that the dropped quartic
+// term stays below 1e-9 cycles.
+__global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                                      double f0, double alpha, int sgn) {
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= nanc) return;
-  const double ka = (double)(a * CHIRP_SPAN + CHIRP_SPAN / 2);
+  const long long span = 1ll << clog;
+  const double ka = (double)(a * span + span / 2);
   const double f = sgn > 0 ? __dsub_rn(__dmul_rn(ka, du), half) : __dsub_rn(half, __dmul_rn(ka, du));
   const double g = f0 + f;
   const double q = f0 * f0 / (g * g);
@@ -73,9 +75,9 @@ __global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, double du
 }
 
 // exp(-2 pi i phi(k)) from the anchor table (phase error < 1e-7 cycles).
-__device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ anc, unsigned k) {
-  const ChirpAnchor a = anc[k >> CHIRP_LOG];
-  const int d = (int)(k & (CHIRP_SPAN - 1)) - CHIRP_SPAN / 2;
+__device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ anc, int clog, unsigned k) {
+  const ChirpAnchor a = anc[k >> clog];
+  const int d = (int)(k & ((1u << clog) - 1)) - (int)((1u << clog) >> 1);
   const unsigned u = a.p0 + a.p1 * (unsigned)d;           // mod 2^32: phase mod 1 cycle
   const float df = (float)d;
   float r = (float)(int)u * 2.3283064365386963e-10f;      // 2^-32
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
 template <int R1>
 __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
                                                  int logR2, int logL, const ChirpAnchor* __restrict__ anc,
-                                                 int apply_chirp, const float2* __restrict__ tw) {
+                                                 int clog, int apply_chirp, const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   constexpr int LSTR = line_stride(R1);
   constexpr int LOGR1 = ilog2c(R1);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
     float s, c;
     sincospif(-(float)k * kscale, &s, &c);          // exp(-i pi k / L)
     float2 X = cadd(E, rot90<false>(cmul(make_float2(c, s), O)));
-    if (apply_chirp) X = cmul(X, chirp_factor(anc, k));
+    if (apply_chirp) X = cmul(X, chirp_factor(anc, clog, k));
     out[k] = X;
   }
 }
@@ -394,10 +396,10 @@ cudaError_t set_kernel_attributes() {
   return e;
 }
 
-cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, double du, double half, double f0,
-                          double alpha, int sgn, cudaStream_t st) {
+cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
+                          double f0, double alpha, int sgn, cudaStream_t st) {
   k_make_twiddles<<<TW_N / 256, 256, 0, st>>>(tw);
-  k_make_chirp_anchors<<<(unsigned)((nanc + 127) / 128), 128, 0, st>>>(anc, nanc, du, half, f0, alpha, sgn);
+  k_make_chirp_anchors<<<(unsigned)((nanc + 127) / 128), 128, 0, st>>>(anc, nanc, clog, du, half, f0, alpha, sgn);
   return cudaGetLastError();
 }
 
@@ -414,13 +416,13 @@ cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int apply_chirp,
-                            const float2* tw, cudaStream_t st) {
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int clog,
+                            int apply_chirp, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   const unsigned grid = (unsigned)(R2 / nl);
   switch (R1) {
-#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, anc, apply_chirp, tw); break;
+#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, anc, clog, apply_chirp, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;

@@ -7,8 +7,7 @@
 
 namespace pond {
 
-constexpr int CHIRP_LOG = 8;                 // bins per chirp anchor = 2^CHIRP_LOG
-constexpr int CHIRP_SPAN = 1 << CHIRP_LOG;
+constexpr int CHIRP_LOG_MAX = 8;             // at most 2^8 bins per chirp anchor
 constexpr int MAX_NBINS = 4096;              // fold bins (per-warp FP64 histograms in smem)
 constexpr int MAX_FOLD_PARTS = 304;          // fold CTAs per segment (2 per SM)
 
@@ -40,11 +39,11 @@ struct Geom {
 };
 
 cudaError_t set_kernel_attributes();
-cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, double du, double half, double f0,
-                          double alpha, int sgn, cudaStream_t st);
+cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
+                          double f0, double alpha, int sgn, cudaStream_t st);
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int apply_chirp,
-                            const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int clog,
+                            int apply_chirp, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_cols(const Geom& g, float2* buf, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
                             long long vofs, int m_hi, const float2* tw, cudaStream_t st);

@@ -201,14 +201,22 @@ class Engine:
         C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
         return T, C, first
 
-    def voltages(self, cap: int = 1 << 24):
-        """Drain dedispersed voltages: (complex64 [nchan, n], first g)."""
-        out = np.zeros((self.nchan, cap, 2), dtype=np.float32)
-        n = ctypes.c_size_t()
-        g0 = ctypes.c_int64()
-        _check(lib().pond_voltages(self._h, _ptr(out), cap, ctypes.byref(n), ctypes.byref(g0)))
-        v = out[:, :n.value, 0] + 1j * out[:, :n.value, 1]
-        return v.astype(np.complex64), g0.value
+    def voltages(self, cap: int = 1 << 22):
+        """Drain every kept dedispersed voltage: (complex64 [nchan, n], first g)."""
+        parts, first = [], None
+        while True:
+            out = np.zeros((self.nchan, cap, 2), dtype=np.float32)
+            n = ctypes.c_size_t()
+            g0 = ctypes.c_int64()
+            _check(lib().pond_voltages(self._h, _ptr(out), cap, ctypes.byref(n), ctypes.byref(g0)))
+            if first is None:
+                first = g0.value
+            if n.value:
+                parts.append((out[:, :n.value, 0] + 1j * out[:, :n.value, 1]).astype(np.complex64))
+            if n.value < cap:
+                break
+        v = np.concatenate(parts, axis=1) if parts else np.zeros((self.nchan, 0), np.complex64)
+        return v, first
 
     def stats(self) -> dict:
         s = pond_stats_t()
