@@ -206,6 +206,32 @@ int pond_voltages(pond_t h, float* out_c, size_t cap, size_t* n_out, int64_t* fi
 /* pond_stats: counters and per-stage GPU times (waits for the device). */
 int pond_stats(pond_t h, pond_stats_t* s);
 
+/*
+ * pond_fold_noalloc: fold n detected power samples d_power[0..n) (device,
+ *   FP32), which are the channel samples g0 .. g0+n-1, into a caller-owned
+ *   profile, ADDING to d_sum[nbins] (device, FP64) and d_hits[nbins] (device,
+ *   int64); zero them before the first call.  The bin of g is the engine's:
+ *   min(floor(frac(g * (dtc_s / period_s)) * nbins), nbins - 1) in FP64, so
+ *   with dtc_s = 2 nchan / fs the result matches pond_profile bin for bin.
+ *   The paper has no counterpart: this entry point exists for callers that
+ *   cannot allocate device memory (a real-time thread that must not stall on
+ *   cudaMalloc/cudaFree, which can synchronise the device, or a host
+ *   application whose memory manager owns all device allocations).  It
+ *   allocates nothing: its scratch (per-CTA partial histograms) is one fixed
+ *   3.6 MiB device array that every GPU loading the library holds until the
+ *   process exits, so nbins is limited to POND_NOALLOC_MAX_NBINS.  The work
+ *   is enqueued on cuda_stream (a cudaStream_t of the current device, NULL =
+ *   legacy default stream).  The first call on a device looks up the array's
+ *   device address; make that first call before any stream capture.  All
+ *   calls share the one array: calls that overlap on the GPU (other streams,
+ *   other threads) race and must be serialised by the caller.
+ *   Errors: POND_E_ARG (nbins > POND_NOALLOC_MAX_NBINS or < 1, n < 0,
+ *   g0 < 0, dtc_s or period_s <= 0, null pointer with n > 0), POND_E_CUDA.
+ */
+#define POND_NOALLOC_MAX_NBINS 1024
+int pond_fold_noalloc(const float* d_power, int64_t n, int64_t g0, double dtc_s, double period_s,
+                      int32_t nbins, double* d_sum, int64_t* d_hits, void* cuda_stream);
+
 /* pond_strerror: static text for a return code.  pond_last_error: message of the
  * calling thread's last failure (empty if none). */
 const char* pond_strerror(int code);

@@ -72,6 +72,8 @@ struct SegEvents {
 
 }  // namespace
 
+int pond::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct pond_s {
   // parameters
   double f0, bw, fs, dm, period;

@@ -39,6 +39,8 @@ struct Geom {
 };
 
 cudaError_t set_kernel_attributes();
+// Record msg as the calling thread's last error (pond_last_error) and return code.
+int set_error(int code, const char* msg);
 cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st);
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);

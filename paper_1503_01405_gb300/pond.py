@@ -26,6 +26,7 @@ POND_E_UNIMPLEMENTED = -9
 POND_FP32 = 0
 POND_SPLIT_BF16 = 1
 POND_NSTAGE = 8
+POND_NOALLOC_MAX_NBINS = 1024
 
 CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", POND_E_OOM: "OOM",
               POND_E_CUDA: "CUDA", POND_E_STATE: "STATE", POND_E_OVERRUN: "OVERRUN",
@@ -35,7 +36,7 @@ CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", PON
 EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_flush", "pond_sync",
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
-           "pond_last_error", "pond_destroy"]
+           "pond_last_error", "pond_destroy", "pond_fold_noalloc"]
 
 
 class PondError(RuntimeError):
@@ -100,6 +101,8 @@ def lib() -> ctypes.CDLL:
         "pond_strerror": [ctypes.c_int],
         "pond_last_error": [],
         "pond_destroy": [vp],
+        "pond_fold_noalloc": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_int32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
