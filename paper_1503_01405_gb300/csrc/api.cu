@@ -96,6 +96,8 @@ struct pond_s {
   float2* bufB = nullptr;
   float* P = nullptr;
   float2* tw = nullptr;
+  float2* tw2buf = nullptr;
+  Tw2 twL, tw2L, twM;   // exp(-2 pi i e/L), exp(-2 pi i e/(2L)), exp(+2 pi i e/M)
   ChirpAnchor* anc = nullptr;
   long long nanc = 0;
   int clog = 0;
@@ -171,15 +173,20 @@ int geometry(const pond_opts* o, Geom* g, double* dtc) {
     return fail(POND_E_NFFT, "nfft %lld does not exceed the overlap (n_past %lld + n_fut %lld >= M %lld)",
                 (long long)o->nfft, g->n_past, g->n_fut, g->M);
   g->S = 2ll * o->nchan * g->S_c;
-  // forward passes: L = R1 * R2, 4 <= R <= 4096
+  // forward passes: L = R1 * R2, 4 <= R <= 4096, with R2 <= M so that every
+  // sub-channel spans whole columns of F2's row layout
   if (g->logL < 4 || g->logL > 24) return fail(POND_E_NFFT, "nfft must be in 2^5 .. 2^25");
-  g->logR1 = std::min(12, (g->logL + 1) / 2);
-  g->logR2 = g->logL - g->logR1;
-  // inverse passes: M = Q1 * Q2 with nchan * Q1 <= TILE
+  g->logR2 = std::min(g->logL / 2, g->logM);
+  g->logR1 = g->logL - g->logR2;
+  if (g->logR1 > 12) {
+    g->logR1 = 12;
+    g->logR2 = g->logL - 12;
+  }
+  // inverse passes: M = Q1 * Q2 with nchan * Q1 <= TILE and Q1 <= R2
   const int lognch = ilog2ll(o->nchan);
-  g->logQ1 = std::min(std::min((g->logM + 1) / 2, 13 - lognch), 12);
+  g->logQ1 = std::min(std::min((g->logM + 1) / 2, 13 - lognch), std::min(12, g->logR2));
   g->logQ2 = g->logM - g->logQ1;
-  if (g->logQ1 < 2 || g->logQ2 < 2 || g->logQ2 > 12)
+  if (g->logR2 < 2 || g->logR2 > g->logM || g->logQ1 < 2 || g->logQ2 < 2 || g->logQ2 > 12)
     return fail(POND_E_NCHAN, "unsupported nchan %d for nfft %lld (need M >= 16 and nchan*4 <= 8192)",
                 o->nchan, (long long)o->nfft);
   return POND_OK;
@@ -291,13 +298,13 @@ int run_segment(pond_t h, SegIn in, long long s, long long m_hi) {
   }
   int rc;
   if ((rc = record(h, 0))) return rc;
-  CK(launch_fwd_cols(g, in, h->bufA, h->tw, h->st));
+  CK(launch_fwd_cols(g, in, h->bufA, h->twL, h->tw, h->st));
   if ((rc = record(h, 1 + ST_F1))) return rc;
-  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->anc, h->clog, 1, h->tw, h->st));
+  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->tw2L, h->anc, h->clog, 1, h->tw, h->st));
   if ((rc = record(h, 1 + ST_F2))) return rc;
-  CK(launch_inv_cols(g, h->bufB, h->tw, h->st));
+  CK(launch_inv_cols(g, h->bufB, h->bufA, h->twM, h->tw, h->st));
   if ((rc = record(h, 1 + ST_I1))) return rc;
-  CK(launch_inv_rows(g, h->bufB, h->P, vout, h->v_cap, h->v_len, (int)m_hi, h->tw, h->st));
+  CK(launch_inv_rows(g, h->bufA, h->P, vout, h->v_cap, h->v_len, (int)m_hi, h->tw, h->st));
   if ((rc = record(h, 1 + ST_I2))) return rc;
   CK(launch_fold(h->P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
   if ((rc = record(h, 1 + ST_FOLD))) return rc;
@@ -362,6 +369,7 @@ void destroy_all(pond_t h) {
   cudaFree(h->bufB);
   cudaFree(h->P);
   cudaFree(h->tw);
+  cudaFree(h->tw2buf);
   cudaFree(h->anc);
   cudaFree(h->prof_sum);
   cudaFree(h->prof_hits);
@@ -466,6 +474,17 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMalloc(&h->bufB, g.L * sizeof(float2)));
   CKD(cudaMalloc(&h->P, g.M * sizeof(float)));
   CKD(cudaMalloc(&h->tw, TW_N * sizeof(float2)));
+  {  // two-level twiddle tables for exponents below L, 2L and M
+    auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
+    const long long total = 3ll * TW2_LO + nhi(g.logL) + nhi(g.logL + 1) + nhi(g.logM);
+    CKD(cudaMalloc(&h->tw2buf, total * sizeof(float2)));
+    float2* p = h->tw2buf;
+    h->twL = {p, p + TW2_LO};
+    p += TW2_LO + nhi(g.logL);
+    h->tw2L = {p, p + TW2_LO};
+    p += TW2_LO + nhi(g.logL + 1);
+    h->twM = {p, p + TW2_LO};
+  }
   const double du = o->fs_hz / (double)o->nfft * 1e-6;
   const double half = std::fabs(o->bw_mhz) / 2.0;
   const double alpha = K_DM * 1e6 * o->dm / (o->f0_mhz * o->f0_mhz);
@@ -495,6 +514,9 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMemsetAsync(h->ts, 0, TS_RING * sizeof(float), h->st));
   CKD(cudaMemsetAsync(h->ts_cnt, 0, TS_RING * sizeof(int), h->st));
   CKD(launch_tables(h->tw, h->anc, h->nanc, h->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  CKD(launch_tw2(const_cast<float2*>(h->twL.lo), const_cast<float2*>(h->twL.hi), g.logL, -1, h->st));
+  CKD(launch_tw2(const_cast<float2*>(h->tw2L.lo), const_cast<float2*>(h->tw2L.hi), g.logL + 1, -1, h->st));
+  CKD(launch_tw2(const_cast<float2*>(h->twM.lo), const_cast<float2*>(h->twM.hi), g.logM, +1, h->st));
   CKD(cudaStreamSynchronize(h->st));
 #undef CKD
   *out = h;

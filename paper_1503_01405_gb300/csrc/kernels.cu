@@ -88,6 +88,31 @@ __device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ a
 }
 
 // ---------------------------------------------------------------------------
+// Two-level twiddle tables: w^e = hi[e >> 12] * lo[e & 4095], w = exp(+-2 pi i / n)
+// ---------------------------------------------------------------------------
+
+__global__ void k_make_tw2(float2* lo, float2* hi, int logn, int sign) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double inv = 2.0 * sign / (double)(1ll << logn);
+  double s, c;
+  if (i < TW2_LO) {
+    sincospi(inv * (double)i, &s, &c);
+    lo[i] = make_float2((float)c, (float)s);
+  }
+  const long long nhi = logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1;
+  if (i < nhi) {
+    sincospi(inv * (double)((long long)i << TW2_LOG), &s, &c);
+    hi[i] = make_float2((float)c, (float)s);
+  }
+}
+
+__device__ __forceinline__ float2 tw2(const Tw2& t, unsigned e) {
+  return cmul(__ldg(t.hi + (e >> TW2_LOG)), __ldg(t.lo + (e & (TW2_LO - 1))));
+}
+
+constexpr int EPT = TILE / NT;   // tile elements per thread
+
+// ---------------------------------------------------------------------------
 // F1: unpack + column FFTs of the forward transform
 // ---------------------------------------------------------------------------
 
@@ -98,31 +123,40 @@ __device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
   return 0.f;
 }
 
+// z viewed as [R2][R1] (z[n1 + R1 n2]); a CTA transforms nl adjacent columns n1
+// and stores them in place, scaled by exp(-2 pi i n1 k2 / L).
 template <int R2>
-__global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1,
-                                                 int logL, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1, Tw2 twL,
+                                                 const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   constexpr int LSTR = line_stride(R2);
   const int R1 = 1 << logR1;
   const int nl = min(TILE / R2, R1);
   const int lognl = __ffs(nl) - 1;
+  const int tot = nl * R2;
   const int n1_0 = blockIdx.x * nl;
-  for (int idx = threadIdx.x; idx < nl * R2; idx += NT) {
-    const int n2 = idx >> lognl, b = idx & (nl - 1);
-    const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
-    sm[pidx(b, n2, LSTR)] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+  float2 r[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) {
+      const int n2 = idx >> lognl, b = idx & (nl - 1);
+      const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
+      r[u] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
   }
   __syncthreads();
   block_fft<R2, false>(sm, nl, tw);
-  const unsigned lmask = (1u << logL) - 1;
-  const float escale = exp2f(1.0f - (float)logL);   // 2/L, exact
-  for (int idx = threadIdx.x; idx < nl * R2; idx += NT) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int k2 = idx >> lognl, b = idx & (nl - 1);
     const unsigned n1 = (unsigned)(n1_0 + b);
-    const unsigned e = (n1 * (unsigned)k2) & lmask;
-    float s, c;
-    sincospif(-(float)e * escale, &s, &c);
-    out[(size_t)n1 + ((size_t)k2 << logR1)] = cmul(sm[pidx(b, k2, LSTR)], make_float2(c, s));
+    out[(size_t)n1 + ((size_t)k2 << logR1)] = cmul(sm[pidx(b, k2, LSTR)], tw2(twL, n1 * (unsigned)k2));
   }
 }
 
@@ -130,17 +164,22 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
 // F2: row FFTs + real-input split + dedispersion chirp
 // ---------------------------------------------------------------------------
 
+// Row k2 of the column-transformed z holds, after a length-R1 FFT, Z[k2 + R2 k1].
+// Rows k2 and R2-k2 share a CTA (row 0 and row R2/2 pair with themselves) so that
+// X[k] can be formed from Z[k] and Z[L-k]; the chirped spectrum Y[k2 + R2 k1] is
+// stored at row k2, column k1 of the output (the same place the row was read).
 template <int R1>
 __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                 int logR2, int logL, const ChirpAnchor* __restrict__ anc,
-                                                 int clog, int apply_chirp, const float2* __restrict__ tw) {
+                                                 int logR2, int logL, Tw2 tw2L,
+                                                 const ChirpAnchor* __restrict__ anc, int clog, int apply_chirp,
+                                                 const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   constexpr int LSTR = line_stride(R1);
   constexpr int LOGR1 = ilog2c(R1);
   const int R2 = 1 << logR2;
   const int nl = min(TILE / R1, R2);   // 2 * pairs
   const int np = nl >> 1;
-  const int lognl = __ffs(nl) - 1;
+  const int tot = nl * R1;
   const int q0 = blockIdx.x * np;
   auto line_of = [&](int slot) -> int {
     if (slot < np) return q0 + slot;
@@ -148,16 +187,23 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
     if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
     return R2 - (q0 + t);
   };
-  for (int idx = threadIdx.x; idx < nl * R1; idx += NT) {
-    const int slot = idx >> LOGR1, e = idx & (R1 - 1);
-    sm[pidx(slot, e, LSTR)] = in[((size_t)line_of(slot) << LOGR1) + e];
+  float2 r[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) r[u] = in[((size_t)line_of(idx >> LOGR1) << LOGR1) + (idx & (R1 - 1))];
+  }
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) sm[pidx(idx >> LOGR1, idx & (R1 - 1), LSTR)] = r[u];
   }
   __syncthreads();
   block_fft<R1, false>(sm, nl, tw);
   const unsigned lmask = (1u << logL) - 1;
-  const float kscale = exp2f(-(float)logL);        // 1/L, exact
-  for (int idx = threadIdx.x; idx < nl * R1; idx += NT) {
-    const int k1 = idx >> lognl, slot = idx & (nl - 1);
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
+    const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
     const int line = line_of(slot);
     const unsigned k = (unsigned)line + ((unsigned)k1 << logR2);
     const unsigned kp = (0u - k) & lmask;
@@ -168,11 +214,9 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
     const float2 B = cconj(sm[pidx(slotp, k1p, LSTR)]);
     const float2 E = cscale(cadd(A, B), 0.5f);
     const float2 O = cscale(csub(A, B), 0.5f);
-    float s, c;
-    sincospif(-(float)k * kscale, &s, &c);          // exp(-i pi k / L)
-    float2 X = cadd(E, rot90<false>(cmul(make_float2(c, s), O)));
+    float2 X = cadd(E, rot90<false>(cmul(tw2(tw2L, k), O)));   // E - i exp(-i pi k/L) O
     if (apply_chirp) X = cmul(X, chirp_factor(anc, clog, k));
-    out[k] = X;
+    out[((size_t)line << LOGR1) + k1] = X;
   }
 }
 
@@ -180,34 +224,59 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
 // I1: per-sub-channel inverse column FFTs
 // ---------------------------------------------------------------------------
 
+// Line (c, j1) holds Y[c M + j1 + Q1 j2], j2 < Q2, read from the row layout
+// written by F2 (bin k at (k >> logR2) + (k mod R2) R1; with Q1 <= R2 the
+// values j2 = j2lo + 2^s j2hi, s = logR2 - logQ1, lie in runs of M/R2
+// consecutive addresses in j2hi).  The inverse column transform, scaled by
+// exp(+2 pi i j1 m2 / M), is stored in natural order c M + j1 + Q1 m2.
 template <int Q2>
-__global__ void __launch_bounds__(NT) k_inv_cols(float2* __restrict__ buf, int logQ1, int logM, int nchan,
+__global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
+                                                 int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
                                                  const float2* __restrict__ tw) {
   extern __shared__ float2 sm[];
   constexpr int LSTR = line_stride(Q2);
+  constexpr int LOGQ2 = ilog2c(Q2);
   const int Q1 = 1 << logQ1;
   const int nl = min(TILE / Q2, nchan * Q1);
   const int lognl = __ffs(nl) - 1;
+  const int tot = nl * Q2;
   const int l0 = blockIdx.x * nl;
-  for (int idx = threadIdx.x; idx < nl * Q2; idx += NT) {
-    const int j2 = idx >> lognl, b = idx & (nl - 1);
-    const int l = l0 + b;
-    const size_t addr = ((size_t)(l >> logQ1) << logM) + (l & (Q1 - 1)) + ((size_t)j2 << logQ1);
-    sm[pidx(b, j2, LSTR)] = buf[addr];
+  const int s = logR2 - logQ1;                 // j2 = j2lo + 2^s j2hi
+  const int logrun = LOGQ2 - s;                // run length M / R2 (>= 1)
+  float2 r[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) {
+      const int j2hi = idx & ((1 << logrun) - 1);
+      const int rest = idx >> logrun;
+      const int j2lo = rest & ((1 << s) - 1);
+      const int l = l0 + (rest >> s);
+      const int c = l >> logQ1, j1 = l & (Q1 - 1);
+      const size_t k1 = ((size_t)c << (logM - logR2)) + j2hi;
+      const size_t k2 = (size_t)j1 + ((size_t)j2lo << logQ1);
+      r[u] = in[k1 + (k2 << logR1)];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) {
+      const int j2hi = idx & ((1 << logrun) - 1);
+      const int rest = idx >> logrun;
+      const int j2lo = rest & ((1 << s) - 1);
+      sm[pidx(rest >> s, j2lo + (j2hi << s), LSTR)] = r[u];
+    }
   }
   __syncthreads();
   block_fft<Q2, true>(sm, nl, tw);
-  const unsigned mmask = (1u << logM) - 1;
-  const float escale = exp2f(1.0f - (float)logM);   // 2/M
-  for (int idx = threadIdx.x; idx < nl * Q2; idx += NT) {
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int m2 = idx >> lognl, b = idx & (nl - 1);
     const int l = l0 + b;
     const unsigned j1 = (unsigned)(l & (Q1 - 1));
-    const unsigned e = (j1 * (unsigned)m2) & mmask;
-    float s, c;
-    sincospif((float)e * escale, &s, &c);           // exp(+2 pi i j1 m2 / M)
     const size_t addr = ((size_t)(l >> logQ1) << logM) + j1 + ((size_t)m2 << logQ1);
-    buf[addr] = cmul(sm[pidx(b, m2, LSTR)], make_float2(c, s));
+    out[addr] = cmul(sm[pidx(b, m2, LSTR)], tw2(twM, j1 * (unsigned)m2));
   }
 }
 
@@ -228,11 +297,22 @@ __global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf,
   const int b2 = min(TILE / (Q1 * nchan), Q2);
   const int logb2 = __ffs(b2) - 1;
   const int nl = nchan * b2;
+  const int tot = nl * Q1;
   const int m2_0 = blockIdx.x * b2;
-  for (int idx = threadIdx.x; idx < nl * Q1; idx += NT) {
-    const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
-    const int c = slot >> logb2, bb = slot & (b2 - 1);
-    sm[pidx(slot, e, LSTR)] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
+  float2 r[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) {
+      const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
+      const int c = slot >> logb2, bb = slot & (b2 - 1);
+      r[u] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    if (idx < tot) sm[pidx(idx >> LOGQ1, idx & (Q1 - 1), LSTR)] = r[u];
   }
   __syncthreads();
   block_fft<Q1, true>(sm, nl, tw);
@@ -294,17 +374,35 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
       p = P[i];
     }
     const unsigned peers = __match_any_sync(0xffffffffu, b);
-    mybuf[lane] = p;
-    __syncwarp();
-    if (ok && lane == __ffs(peers) - 1) {
-      float s = 0.f;
-      unsigned m = peers;
-      while (m) {
-        s += mybuf[__ffs(m) - 1];
-        m &= m - 1;
+    const int first = __ffs(peers) - 1;
+    const int last = 31 - __clz(peers);
+    const unsigned span = (last == 31 ? 0xffffffffu : ((1u << (last + 1)) - 1u)) & ~((1u << first) - 1u);
+    if (__all_sync(0xffffffffu, peers == span)) {
+      // every bin's lanes are contiguous: segmented scan in a fixed tree order
+      float x = p;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane - d >= first) x += y;
       }
-      myh[b] += (double)s;
-      myc[b] += __popc(peers);
+      if (ok && lane == last) {
+        myh[b] += (double)x;
+        myc[b] += last - first + 1;
+      }
+    } else {
+      // a period shorter than a warp: the group leader sums its lanes in order
+      mybuf[lane] = p;
+      __syncwarp();
+      if (ok && lane == first) {
+        float sum = 0.f;
+        unsigned m = peers;
+        while (m) {
+          sum += mybuf[__ffs(m) - 1];
+          m &= m - 1;
+        }
+        myh[b] += (double)sum;
+        myc[b] += __popc(peers);
+      }
     }
     __syncwarp();
   }
@@ -322,18 +420,28 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
   }
 }
 
+// One warp per bin: lanes take every 32nd part, then a fixed xor-tree sum.
 __global__ void k_fold_merge(const double* __restrict__ psum, const int* __restrict__ phits, int nparts,
                              int nbins, double* __restrict__ prof_sum, long long* __restrict__ prof_hits) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (b >= nbins) return;
   double s = 0.0;
   long long h = 0;
-  for (int k = 0; k < nparts; ++k) {
+#pragma unroll 4
+  for (int k = lane; k < nparts; k += 32) {
     s += psum[(size_t)k * nbins + b];
     h += phits[(size_t)k * nbins + b];
   }
-  prof_sum[b] += s;
-  prof_hits[b] += h;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, off);
+    h += __shfl_xor_sync(0xffffffffu, h, off);
+  }
+  if (lane == 0) {
+    prof_sum[b] += s;
+    prof_hits[b] += h;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -396,6 +504,13 @@ cudaError_t set_kernel_attributes() {
   return e;
 }
 
+cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st) {
+  const long long nhi = logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1;
+  const long long n = std::max<long long>(TW2_LO, nhi);
+  k_make_tw2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lo, hi, logn, sign);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st) {
   k_make_twiddles<<<TW_N / 256, 256, 0, st>>>(tw);
@@ -403,12 +518,12 @@ cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R2, R1);
   const unsigned grid = (unsigned)(R1 / nl);
   switch (R2) {
-#define CASE(R) case R: k_fwd_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR1, g.logL, tw); break;
+#define CASE(R) case R: k_fwd_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR1, twL, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -416,13 +531,13 @@ cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int clog,
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
                             int apply_chirp, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   const unsigned grid = (unsigned)(R2 / nl);
   switch (R1) {
-#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, anc, clog, apply_chirp, tw); break;
+#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, tw2L, anc, clog, apply_chirp, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -430,13 +545,14 @@ cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_inv_cols(const Geom& g, float2* buf, const float2* tw, cudaStream_t st) {
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const float2* tw,
+                            cudaStream_t st) {
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int lines = g.nchan * Q1;
   const int nl = std::min(TILE / Q2, lines);
   const unsigned grid = (unsigned)(lines / nl);
   switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, g.logQ1, g.logM, g.nchan, tw); break;
+#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -465,7 +581,7 @@ size_t fold_smem_bytes(int nbins) {
 }
 
 int fold_parts(long long n, long long* chunk) {
-  long long c = std::max<long long>(2048, (n + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS);
+  long long c = std::max<long long>(1024, (n + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS);
   c = (c + 127) / 128 * 128;
   *chunk = c;
   return (int)((n + c - 1) / c);
@@ -477,7 +593,7 @@ cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, i
   long long chunk;
   const int parts = fold_parts(n, &chunk);
   k_fold_partial<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, chunk, psum, phits);
-  k_fold_merge<<<(nbins + 127) / 128, 128, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
+  k_fold_merge<<<(nbins * 32 + 255) / 256, 256, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
   return cudaGetLastError();
 }
 

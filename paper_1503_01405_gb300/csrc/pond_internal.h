@@ -19,6 +19,14 @@ struct __align__(16) ChirpAnchor {
   float p3;      // phi'''(k_a) / 6
 };
 
+// Two-level twiddle table for exponents e < n: w^e = hi[e >> 12] * lo[e & 4095].
+constexpr int TW2_LOG = 12;
+constexpr int TW2_LO = 1 << TW2_LOG;
+struct Tw2 {
+  const float2* lo;
+  const float2* hi;
+};
+
 // A segment's int8 input as up to two runs: samples [0, a_len) from a,
 // [a_len, a_len + b_len) from b, zeros beyond.
 struct SegIn {
@@ -43,10 +51,12 @@ cudaError_t set_kernel_attributes();
 int set_error(int code, const char* msg);
 cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st);
-cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc, int clog,
+cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st);
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
                             int apply_chirp, const float2* tw, cudaStream_t st);
-cudaError_t launch_inv_cols(const Geom& g, float2* buf, const float2* tw, cudaStream_t st);
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const float2* tw,
+                            cudaStream_t st);
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
                             long long vofs, int m_hi, const float2* tw, cudaStream_t st);
 size_t fold_smem_bytes(int nbins);
