@@ -461,6 +461,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     }                               \
   } while (0)
   CKD(cudaSetDevice(o->device));
+  CKD(cudaDeviceGetAttribute(&h->g.sms, cudaDevAttrMultiProcessorCount, o->device));
   CKD(set_kernel_attributes());
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));

@@ -130,15 +130,34 @@ template <bool INV> struct Dft<16, INV> {
   }
 };
 
-// w^e for w = exp(-+2 pi i / n), n = 2^LOGN <= 2^13, from the FP64-built table
-template <bool INV, int LOGN>
-__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) {
-  float2 w = __ldg(tw + (e << (TW_LOG - LOGN)));
+// Shared-memory twiddle table of a line FFT: stw[m] = exp(-2 pi i m / R), m < R,
+// copied from the FP64-built global table once per CTA.
+template <int R>
+__device__ __forceinline__ void load_twiddles(float2* stw, const float2* __restrict__ tw) {
+  constexpr int LOGR = ilog2c(R);
+  constexpr int PER = (R + NT - 1) / NT;
+  float2 w[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int m = threadIdx.x + u * NT;
+    if (m < R) w[u] = __ldg(tw + (m << (TW_LOG - LOGR)));
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int m = threadIdx.x + u * NT;
+    if (m < R) stw[m] = w[u];
+  }
+}
+
+// w^e for w = exp(-+2 pi i / N_s), N_s = 2^LOGN <= R, from the shared table
+template <int R, bool INV, int LOGN>
+__device__ __forceinline__ float2 twiddle(const float2* stw, int e) {
+  const float2 w = stw[e << (ilog2c(R) - LOGN)];
   return INV ? cconj(w) : w;
 }
 
 template <int R, int RAD, int LS, bool INV>
-__device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* stw) {
   constexpr int LSTR = line_stride(R);
   constexpr int NB = R / RAD;        // butterflies per line
   constexpr int BPT = 16 / RAD;      // butterflies per thread for a full tile
@@ -150,8 +169,15 @@ __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* 
     const int bf = threadIdx.x + u * NT;
     if (bf < total) {
       const int line = bf >> LOGNB, t = bf & (NB - 1);
+      if constexpr (NB % 16 == 0) {
+        // (t + j NB) / 16 = t / 16 + j NB / 16: constant offsets per j
+        const float2* p = s + line * LSTR + t + (t >> 4);
 #pragma unroll
-      for (int j = 0; j < RAD; ++j) v[u][j] = s[pidx(line, t + j * NB, LSTR)];
+        for (int j = 0; j < RAD; ++j) v[u][j] = p[j * (NB + NB / 16)];
+      } else {
+#pragma unroll
+        for (int j = 0; j < RAD; ++j) v[u][j] = s[pidx(line, t + j * NB, LSTR)];
+      }
     }
   }
   __syncthreads();
@@ -161,34 +187,44 @@ __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* 
     if (bf < total) {
       const int line = bf >> LOGNB, t = bf & (NB - 1);
       const int k = t & (LS - 1);
-      if (LS > 1) {
+      if constexpr (LS > 1) {
 #pragma unroll
-        for (int j = 1; j < RAD; ++j) v[u][j] = cmul(v[u][j], twiddle<INV, ilog2c(LS * RAD)>(tw, j * k));
+        for (int j = 1; j < RAD; ++j) v[u][j] = cmul(v[u][j], twiddle<R, INV, ilog2c(LS * RAD)>(stw, j * k));
       }
       Dft<RAD, INV>::run(v[u]);
       const int base = (t / LS) * (LS * RAD) + k;
+      if constexpr (LS % 16 == 0) {
+        float2* p = s + line * LSTR + base + (base >> 4);
 #pragma unroll
-      for (int j = 0; j < RAD; ++j) s[pidx(line, base + j * LS, LSTR)] = v[u][j];
+        for (int j = 0; j < RAD; ++j) p[j * (LS + LS / 16)] = v[u][j];
+      } else if constexpr (LS == 1 && RAD == 16) {
+        float2* p = s + line * LSTR + base + (base >> 4);   // base = 16 t: 17 t + j
+#pragma unroll
+        for (int j = 0; j < RAD; ++j) p[j] = v[u][j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < RAD; ++j) s[pidx(line, base + j * LS, LSTR)] = v[u][j];
+      }
     }
   }
   __syncthreads();
 }
 
 template <int R, int LS, bool INV> struct Stages {
-  static __device__ __forceinline__ void run(float2* s, int nl, const float2* __restrict__ tw) {
+  static __device__ __forceinline__ void run(float2* s, int nl, const float2* stw) {
     if constexpr (LS < R) {
       constexpr int REM = ilog2c(R) % 4;
       constexpr int RAD = (LS == 1 && REM != 0) ? (1 << REM) : 16;
-      stockham_stage<R, RAD, LS, INV>(s, nl, tw);
-      Stages<R, LS * RAD, INV>::run(s, nl, tw);
+      stockham_stage<R, RAD, LS, INV>(s, nl, stw);
+      Stages<R, LS * RAD, INV>::run(s, nl, stw);
     }
   }
 };
 
-// Transform the nl lines of length R held in shared memory s.
+// Transform the nl lines of length R held in shared memory s (stw: twiddle table).
 template <int R, bool INV>
-__device__ __forceinline__ void block_fft(float2* s, int nl, const float2* __restrict__ tw) {
-  Stages<R, 1, INV>::run(s, nl, tw);
+__device__ __forceinline__ void block_fft(float2* s, int nl, const float2* stw) {
+  Stages<R, 1, INV>::run(s, nl, stw);
 }
 
 }  // namespace pond

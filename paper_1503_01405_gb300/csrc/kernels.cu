@@ -127,14 +127,18 @@ __device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
 // and stores them in place, scaled by exp(-2 pi i n1 k2 / L).
 template <int R2>
 __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1, Tw2 twL,
-                                                 const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+                                                    const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  float2* stw = smem;
+  float2* sm = smem + R2;
   constexpr int LSTR = line_stride(R2);
   const int R1 = 1 << logR1;
   const int nl = min(TILE / R2, R1);
   const int lognl = __ffs(nl) - 1;
   const int tot = nl * R2;
-  const int n1_0 = blockIdx.x * nl;
+  load_twiddles<R2>(stw, tw);
+  const int tile = blockIdx.x;
+  const int n1_0 = tile * nl;
   float2 r[EPT];
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
     if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
   }
   __syncthreads();
-  block_fft<R2, false>(sm, nl, tw);
+  block_fft<R2, false>(sm, nl, stw);
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int k2 = idx >> lognl, b = idx & (nl - 1);
@@ -170,17 +174,21 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
 // stored at row k2, column k1 of the output (the same place the row was read).
 template <int R1>
 __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                 int logR2, int logL, Tw2 tw2L,
-                                                 const ChirpAnchor* __restrict__ anc, int clog, int apply_chirp,
-                                                 const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+                                                    int logR2, int logL, Tw2 tw2L,
+                                                    const ChirpAnchor* __restrict__ anc, int clog, int apply_chirp,
+                                                    const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  float2* stw = smem;
+  float2* sm = smem + R1;
   constexpr int LSTR = line_stride(R1);
   constexpr int LOGR1 = ilog2c(R1);
   const int R2 = 1 << logR2;
   const int nl = min(TILE / R1, R2);   // 2 * pairs
   const int np = nl >> 1;
   const int tot = nl * R1;
-  const int q0 = blockIdx.x * np;
+  load_twiddles<R1>(stw, tw);
+  const int tile = blockIdx.x;
+  const int q0 = tile * np;
   auto line_of = [&](int slot) -> int {
     if (slot < np) return q0 + slot;
     const int t = slot - np;
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
     if (idx < tot) sm[pidx(idx >> LOGR1, idx & (R1 - 1), LSTR)] = r[u];
   }
   __syncthreads();
-  block_fft<R1, false>(sm, nl, tw);
+  block_fft<R1, false>(sm, nl, stw);
   const unsigned lmask = (1u << logL) - 1;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
@@ -231,16 +239,20 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
 // exp(+2 pi i j1 m2 / M), is stored in natural order c M + j1 + Q1 m2.
 template <int Q2>
 __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
-                                                 int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
-                                                 const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+                                                    int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
+                                                    const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  float2* stw = smem;
+  float2* sm = smem + Q2;
   constexpr int LSTR = line_stride(Q2);
   constexpr int LOGQ2 = ilog2c(Q2);
   const int Q1 = 1 << logQ1;
   const int nl = min(TILE / Q2, nchan * Q1);
   const int lognl = __ffs(nl) - 1;
   const int tot = nl * Q2;
-  const int l0 = blockIdx.x * nl;
+  load_twiddles<Q2>(stw, tw);
+  const int tile = blockIdx.x;
+  const int l0 = tile * nl;
   const int s = logR2 - logQ1;                 // j2 = j2lo + 2^s j2hi
   const int logrun = LOGQ2 - s;                // run length M / R2 (>= 1)
   float2 r[EPT];
@@ -269,7 +281,7 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
     }
   }
   __syncthreads();
-  block_fft<Q2, true>(sm, nl, tw);
+  block_fft<Q2, true>(sm, nl, stw);
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int m2 = idx >> lognl, b = idx & (nl - 1);
@@ -286,11 +298,13 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
 
 template <int Q1>
 __global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf, float* __restrict__ P,
-                                                 float2* __restrict__ vout, long long vstride,
-                                                 long long vofs, int logQ2, int logM, int nchan,
-                                                 int m_lo, int m_hi, float scale,
-                                                 const float2* __restrict__ tw) {
-  extern __shared__ float2 sm[];
+                                                    float2* __restrict__ vout, long long vstride,
+                                                    long long vofs, int logQ2, int logM, int nchan,
+                                                    int m_lo, int m_hi, float scale,
+                                                    const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  float2* stw = smem;
+  float2* sm = smem + Q1;
   constexpr int LSTR = line_stride(Q1);
   constexpr int LOGQ1 = ilog2c(Q1);
   const int Q2 = 1 << logQ2;
@@ -298,7 +312,9 @@ __global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf,
   const int logb2 = __ffs(b2) - 1;
   const int nl = nchan * b2;
   const int tot = nl * Q1;
-  const int m2_0 = blockIdx.x * b2;
+  load_twiddles<Q1>(stw, tw);
+  const int tile = blockIdx.x;
+  const int m2_0 = tile * b2;
   float2 r[EPT];
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
@@ -315,7 +331,7 @@ __global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf,
     if (idx < tot) sm[pidx(idx >> LOGQ1, idx & (Q1 - 1), LSTR)] = r[u];
   }
   __syncthreads();
-  block_fft<Q1, true>(sm, nl, tw);
+  block_fft<Q1, true>(sm, nl, stw);
   for (int idx = threadIdx.x; idx < b2 * Q1; idx += NT) {
     const int m1 = idx >> logb2, bb = idx & (b2 - 1);
     const int m = m2_0 + bb + (m1 << logQ2);
@@ -475,17 +491,22 @@ __global__ void k_decimate(const float* __restrict__ P, long long n, long long g
 // Host launchers
 // ---------------------------------------------------------------------------
 
+// Twiddle table (R) + padded tile (nl lines of line_stride(R)).
 template <int R>
 static size_t smem_bytes(int nl) {
-  return (size_t)nl * line_stride(R) * sizeof(float2);
+  return ((size_t)R + (size_t)nl * line_stride(R)) * sizeof(float2);
 }
 
-// Largest padded tile over the line lengths 4..4096 (R = 4: 2048 lines of 5).
+// Largest twiddle table + padded tile over the line lengths 4..4096.
 static size_t max_tile_smem_bytes() {
   size_t m = 0;
-  for (int R = 4; R <= 4096; R *= 2) m = std::max(m, (size_t)(TILE / R) * (R + R / 16 + 1) * sizeof(float2));
+  for (int R = 4; R <= 4096; R *= 2)
+    m = std::max(m, ((size_t)R + (size_t)(TILE / R) * (R + R / 16 + 1)) * sizeof(float2));
   return m;
 }
+
+// One CTA per tile.
+static unsigned grid_for(int tiles, int) { return (unsigned)tiles; }
 
 #define POND_FOR_R(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
@@ -521,7 +542,7 @@ cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R2, R1);
-  const unsigned grid = (unsigned)(R1 / nl);
+  const unsigned grid = grid_for(R1 / nl, g.sms);
   switch (R2) {
 #define CASE(R) case R: k_fwd_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR1, twL, tw); break;
     POND_FOR_R(CASE)
@@ -535,7 +556,7 @@ cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw
                             int apply_chirp, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
-  const unsigned grid = (unsigned)(R2 / nl);
+  const unsigned grid = grid_for(R2 / nl, g.sms);
   switch (R1) {
 #define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, tw2L, anc, clog, apply_chirp, tw); break;
     POND_FOR_R(CASE)
@@ -550,7 +571,7 @@ cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 tw
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int lines = g.nchan * Q1;
   const int nl = std::min(TILE / Q2, lines);
-  const unsigned grid = (unsigned)(lines / nl);
+  const unsigned grid = grid_for(lines / nl, g.sms);
   switch (Q2) {
 #define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, tw); break;
     POND_FOR_R(CASE)
@@ -565,7 +586,7 @@ cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* 
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int b2 = std::min(TILE / (Q1 * g.nchan), Q2);
   const int nl = g.nchan * b2;
-  const unsigned grid = (unsigned)(Q2 / b2);
+  const unsigned grid = grid_for(Q2 / b2, g.sms);
   const float scale = 1.0f / (float)(1u << g.logM);
   switch (Q1) {
 #define CASE(R) case R: k_inv_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, (int)g.n_past, m_hi, scale, tw); break;

@@ -44,6 +44,7 @@ struct Geom {
   int logR1, logR2;      // forward: L = R1 * R2 (F2 rows of R1, F1 columns of R2)
   int logQ1, logQ2;      // inverse: M = Q1 * Q2 (I2 rows of Q1, I1 columns of Q2)
   long long n_past, n_fut, S_c, S;
+  int sms;               // streaming multiprocessors of the device
 };
 
 cudaError_t set_kernel_attributes();
