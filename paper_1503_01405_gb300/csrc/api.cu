@@ -95,7 +95,8 @@ struct pond_s {
   float2* bufA = nullptr;
   float2* bufB = nullptr;
   float* P = nullptr;
-  float2* tw = nullptr;
+  float2* tw = nullptr;                     // stage twiddle tables of R1, R2, Q1, Q2
+  const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
   float2* tw2buf = nullptr;
   Tw2 twL, tw2L, twM;   // exp(-2 pi i e/L), exp(-2 pi i e/(2L)), exp(+2 pi i e/M)
   ChirpAnchor* anc = nullptr;
@@ -298,13 +299,18 @@ int run_segment(pond_t h, SegIn in, long long s, long long m_hi) {
   }
   int rc;
   if ((rc = record(h, 0))) return rc;
-  CK(launch_fwd_cols(g, in, h->bufA, h->twL, h->tw, h->st));
+  {  // F1 may load 8 bytes (4 columns of a row) at a time when both runs allow it
+    const int nl1 = std::min(TILE >> g.logR2, 1 << g.logR1);
+    in.vec8 = (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
+              (in.b_len == 0 || (uintptr_t)in.b % 8 == 0);
+  }
+  CK(launch_fwd_cols(g, in, h->bufA, h->twL, h->stwR2, h->st));
   if ((rc = record(h, 1 + ST_F1))) return rc;
-  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->tw2L, h->anc, h->clog, 1, h->tw, h->st));
+  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->tw2L, h->anc, h->clog, 1, h->stwR1, h->st));
   if ((rc = record(h, 1 + ST_F2))) return rc;
-  CK(launch_inv_cols(g, h->bufB, h->bufA, h->twM, h->tw, h->st));
+  CK(launch_inv_cols(g, h->bufB, h->bufA, h->twM, h->stwQ2, h->st));
   if ((rc = record(h, 1 + ST_I1))) return rc;
-  CK(launch_inv_rows(g, h->bufA, h->P, vout, h->v_cap, h->v_len, (int)m_hi, h->tw, h->st));
+  CK(launch_inv_rows(g, h->bufA, h->P, vout, h->v_cap, h->v_len, (int)m_hi, h->stwQ1, h->st));
   if ((rc = record(h, 1 + ST_I2))) return rc;
   CK(launch_fold(h->P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
   if ((rc = record(h, 1 + ST_FOLD))) return rc;
@@ -474,7 +480,15 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMalloc(&h->bufA, g.L * sizeof(float2)));
   CKD(cudaMalloc(&h->bufB, g.L * sizeof(float2)));
   CKD(cudaMalloc(&h->P, g.M * sizeof(float)));
-  CKD(cudaMalloc(&h->tw, TW_N * sizeof(float2)));
+  {
+    const int n1 = stage_tw_entries(1 << g.logR1), n2 = stage_tw_entries(1 << g.logR2);
+    const int n3 = stage_tw_entries(1 << g.logQ1), n4 = stage_tw_entries(1 << g.logQ2);
+    CKD(cudaMalloc(&h->tw, (size_t)std::max(1, n1 + n2 + n3 + n4) * sizeof(float2)));
+    h->stwR1 = h->tw;
+    h->stwR2 = h->stwR1 + n1;
+    h->stwQ1 = h->stwR2 + n2;
+    h->stwQ2 = h->stwQ1 + n3;
+  }
   {  // two-level twiddle tables for exponents below L, 2L and M
     auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
     const long long total = 3ll * TW2_LO + nhi(g.logL) + nhi(g.logL + 1) + nhi(g.logM);
@@ -514,7 +528,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
   CKD(cudaMemsetAsync(h->ts, 0, TS_RING * sizeof(float), h->st));
   CKD(cudaMemsetAsync(h->ts_cnt, 0, TS_RING * sizeof(int), h->st));
-  CKD(launch_tables(h->tw, h->anc, h->nanc, h->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  CKD(launch_tables(h->anc, h->nanc, h->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  CKD(launch_stage_tw(const_cast<float2*>(h->stwR1), 1 << g.logR1, h->st));
+  CKD(launch_stage_tw(const_cast<float2*>(h->stwR2), 1 << g.logR2, h->st));
+  CKD(launch_stage_tw(const_cast<float2*>(h->stwQ1), 1 << g.logQ1, h->st));
+  CKD(launch_stage_tw(const_cast<float2*>(h->stwQ2), 1 << g.logQ2, h->st));
   CKD(launch_tw2(const_cast<float2*>(h->twL.lo), const_cast<float2*>(h->twL.hi), g.logL, -1, h->st));
   CKD(launch_tw2(const_cast<float2*>(h->tw2L.lo), const_cast<float2*>(h->tw2L.hi), g.logL + 1, -1, h->st));
   CKD(launch_tw2(const_cast<float2*>(h->twM.lo), const_cast<float2*>(h->twM.hi), g.logM, +1, h->st));

@@ -3,7 +3,7 @@
 // A CTA holds a tile of TILE complex FP32 samples in shared memory: `nl` lines
 // of R samples each (R a power of two, 4..4096).  All lines are transformed
 // at once by radix-16 Stockham stages (one butterfly per thread per stage),
-// preceded by one radix-2/4/8 stage when log2(R) is not a multiple of 4.
+// followed by one radix-2/4/8 stage when log2(R) is not a multiple of 4.
 // Stockham stage with radix r after sub-transforms of length Ls: butterfly t
 // reads x[t + j R/r], j < r, multiplies input j by w^{j (t mod Ls)} with
 // w = exp(-+2 pi i / (Ls r)), takes an r-point DFT and writes output j to
@@ -130,30 +130,42 @@ template <bool INV> struct Dft<16, INV> {
   }
 };
 
-// Shared-memory twiddle table of a line FFT: stw[m] = exp(-2 pi i m / R), m < R,
-// copied from the FP64-built global table once per CTA.
-template <int R>
-__device__ __forceinline__ void load_twiddles(float2* stw, const float2* __restrict__ tw) {
-  constexpr int LOGR = ilog2c(R);
-  constexpr int PER = (R + NT - 1) / NT;
-  float2 w[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int m = threadIdx.x + u * NT;
-    if (m < R) w[u] = __ldg(tw + (m << (TW_LOG - LOGR)));
-  }
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const int m = threadIdx.x + u * NT;
-    if (m < R) stw[m] = w[u];
-  }
+// Radix schedule of a length-R line: radix-16 stages, then one radix-2/4/8
+// stage last when log2(R) is not a multiple of 4.  Stage s has radix RAD_s and
+// follows sub-transforms of length LS_s = product of the earlier radices.
+// Twiddles of a stage with LS > 1 live in a table laid out [j-1][k]
+// (j = 1..RAD-1, k < LS): entry w^{j k}, w = exp(-2 pi i / (LS RAD)); threads
+// with consecutive k read consecutive words.  The tables of all stages of R
+// are concatenated in stage order; stage_table_size<R>() counts the entries.
+__host__ __device__ constexpr int stage_radix(int R, int LS) {
+  return (R / LS >= 16) ? 16 : R / LS;
 }
+__host__ __device__ constexpr int stage_table_offset(int R, int LS_target) {
+  int off = 0;
+  for (int ls = 1; ls < LS_target; ls *= stage_radix(R, ls))
+    if (ls > 1) off += (stage_radix(R, ls) - 1) * ls;
+  return off;
+}
+__host__ __device__ constexpr int stage_table_size(int R) { return stage_table_offset(R, R); }
 
-// w^e for w = exp(-+2 pi i / N_s), N_s = 2^LOGN <= R, from the shared table
-template <int R, bool INV, int LOGN>
-__device__ __forceinline__ float2 twiddle(const float2* stw, int e) {
-  const float2 w = stw[e << (ilog2c(R) - LOGN)];
-  return INV ? cconj(w) : w;
+// Copy the concatenated stage tables of R (global, FP64-built) into shared memory.
+template <int R>
+__device__ __forceinline__ void load_twiddles(float2* stw, const float2* __restrict__ gtw) {
+  constexpr int NTW = stage_table_size(R);
+  constexpr int PER = (NTW + NT - 1) / NT;
+  if constexpr (NTW > 0) {
+    float2 w[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int m = threadIdx.x + u * NT;
+      if (m < NTW) w[u] = __ldg(gtw + m);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int m = threadIdx.x + u * NT;
+      if (m < NTW) stw[m] = w[u];
+    }
+  }
 }
 
 template <int R, int RAD, int LS, bool INV>
@@ -188,8 +200,12 @@ __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* 
       const int line = bf >> LOGNB, t = bf & (NB - 1);
       const int k = t & (LS - 1);
       if constexpr (LS > 1) {
+        const float2* tws = stw + stage_table_offset(R, LS) + k;
 #pragma unroll
-        for (int j = 1; j < RAD; ++j) v[u][j] = cmul(v[u][j], twiddle<R, INV, ilog2c(LS * RAD)>(stw, j * k));
+        for (int j = 1; j < RAD; ++j) {
+          const float2 w = tws[(j - 1) * LS];
+          v[u][j] = cmul(v[u][j], INV ? cconj(w) : w);
+        }
       }
       Dft<RAD, INV>::run(v[u]);
       const int base = (t / LS) * (LS * RAD) + k;
@@ -213,15 +229,14 @@ __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* 
 template <int R, int LS, bool INV> struct Stages {
   static __device__ __forceinline__ void run(float2* s, int nl, const float2* stw) {
     if constexpr (LS < R) {
-      constexpr int REM = ilog2c(R) % 4;
-      constexpr int RAD = (LS == 1 && REM != 0) ? (1 << REM) : 16;
+      constexpr int RAD = stage_radix(R, LS);
       stockham_stage<R, RAD, LS, INV>(s, nl, stw);
       Stages<R, LS * RAD, INV>::run(s, nl, stw);
     }
   }
 };
 
-// Transform the nl lines of length R held in shared memory s (stw: twiddle table).
+// Transform the nl lines of length R held in shared memory s (stw: stage tables).
 template <int R, bool INV>
 __device__ __forceinline__ void block_fft(float2* s, int nl, const float2* stw) {
   Stages<R, 1, INV>::run(s, nl, stw);

@@ -31,12 +31,23 @@ namespace pond {
 // Tables (built once per plan, FP64 on the device)
 // ---------------------------------------------------------------------------
 
-__global__ void k_make_twiddles(float2* tw) {
+// Concatenated stage twiddle tables of a length-R line FFT (see fft_block.cuh):
+// entry (j-1) LS + k of the stage after sub-transforms of length LS holds
+// exp(-2 pi i j k / (LS RAD)).
+__global__ void k_make_stage_tw(float2* out, int R) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < TW_N) {
-    double s, c;
-    sincospi(-2.0 * (double)m / (double)TW_N, &s, &c);
-    tw[m] = make_float2((float)c, (float)s);
+  int off = 0;
+  for (int ls = 1; ls < R; ls *= stage_radix(R, ls)) {
+    const int rad = stage_radix(R, ls);
+    if (ls == 1) continue;
+    const int n = (rad - 1) * ls;
+    if (m >= off && m < off + n) {
+      const int j = (m - off) / ls + 1, k = (m - off) % ls;
+      double sn, cs;
+      sincospi(-2.0 * (double)(j * k) / (double)(ls * rad), &sn, &cs);
+      out[m] = make_float2((float)cs, (float)sn);
+    }
+    off += n;
   }
 }
 
@@ -130,7 +141,7 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
-  float2* sm = smem + R2;
+  float2* sm = smem + stage_table_size(R2);
   constexpr int LSTR = line_stride(R2);
   const int R1 = 1 << logR1;
   const int nl = min(TILE / R2, R1);
@@ -139,20 +150,50 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
   load_twiddles<R2>(stw, tw);
   const int tile = blockIdx.x;
   const int n1_0 = tile * nl;
-  float2 r[EPT];
+  if (in.vec8) {
+    // 8-byte loads: 4 consecutive columns of one row per load (runs 8-aligned)
+    constexpr int CPT = EPT / 4;
+    const int logq = lognl - 2;            // chunks per row = nl / 4
+    uint2 w[CPT];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int n2 = idx >> lognl, b = idx & (nl - 1);
-      const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
-      r[u] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+    for (int u = 0; u < CPT; ++u) {
+      const int c = threadIdx.x + u * NT;
+      if (c < tot / 4) {
+        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
+        const long long r = 2 * ((long long)(n1_0 + b0) + ((long long)n2 << logR1));
+        if (r < in.a_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.a + r));
+        else if (r - in.a_len < in.b_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.b + (r - in.a_len)));
+        else w[u] = make_uint2(0u, 0u);
+      }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
+    for (int u = 0; u < CPT; ++u) {
+      const int c = threadIdx.x + u * NT;
+      if (c < tot / 4) {
+        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
+        const unsigned lo = w[u].x, hi = w[u].y;
+        sm[pidx(b0 + 0, n2, LSTR)] = make_float2((float)(signed char)(lo & 0xff), (float)(signed char)((lo >> 8) & 0xff));
+        sm[pidx(b0 + 1, n2, LSTR)] = make_float2((float)(signed char)((lo >> 16) & 0xff), (float)(signed char)(lo >> 24));
+        sm[pidx(b0 + 2, n2, LSTR)] = make_float2((float)(signed char)(hi & 0xff), (float)(signed char)((hi >> 8) & 0xff));
+        sm[pidx(b0 + 3, n2, LSTR)] = make_float2((float)(signed char)((hi >> 16) & 0xff), (float)(signed char)(hi >> 24));
+      }
+    }
+  } else {
+    float2 r[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int idx = threadIdx.x + u * NT;
+      if (idx < tot) {
+        const int n2 = idx >> lognl, b = idx & (nl - 1);
+        const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
+        r[u] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      const int idx = threadIdx.x + u * NT;
+      if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
+    }
   }
   __syncthreads();
   block_fft<R2, false>(sm, nl, stw);
@@ -179,7 +220,7 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
-  float2* sm = smem + R1;
+  float2* sm = smem + stage_table_size(R1);
   constexpr int LSTR = line_stride(R1);
   constexpr int LOGR1 = ilog2c(R1);
   const int R2 = 1 << logR2;
@@ -243,7 +284,7 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
-  float2* sm = smem + Q2;
+  float2* sm = smem + stage_table_size(Q2);
   constexpr int LSTR = line_stride(Q2);
   constexpr int LOGQ2 = ilog2c(Q2);
   const int Q1 = 1 << logQ1;
@@ -304,7 +345,7 @@ __global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf,
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
-  float2* sm = smem + Q1;
+  float2* sm = smem + stage_table_size(Q1);
   constexpr int LSTR = line_stride(Q1);
   constexpr int LOGQ1 = ilog2c(Q1);
   const int Q2 = 1 << logQ2;
@@ -491,19 +532,27 @@ __global__ void k_decimate(const float* __restrict__ P, long long n, long long g
 // Host launchers
 // ---------------------------------------------------------------------------
 
-// Twiddle table (R) + padded tile (nl lines of line_stride(R)).
+// Stage twiddle tables + padded tile (nl lines of line_stride(R)).
 template <int R>
 static size_t smem_bytes(int nl) {
-  return ((size_t)R + (size_t)nl * line_stride(R)) * sizeof(float2);
+  return ((size_t)stage_table_size(R) + (size_t)nl * line_stride(R)) * sizeof(float2);
 }
 
-// Largest twiddle table + padded tile over the line lengths 4..4096.
+// Largest stage tables + padded tile over the line lengths 4..4096.
 static size_t max_tile_smem_bytes() {
   size_t m = 0;
   for (int R = 4; R <= 4096; R *= 2)
-    m = std::max(m, ((size_t)R + (size_t)(TILE / R) * (R + R / 16 + 1)) * sizeof(float2));
+    m = std::max(m, ((size_t)stage_table_size(R) + (size_t)(TILE / R) * (R + R / 16 + 1)) * sizeof(float2));
   return m;
 }
+
+cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st) {
+  const int n = stage_table_size(R);
+  if (n > 0) k_make_stage_tw<<<(n + 255) / 256, 256, 0, st>>>(out, R);
+  return cudaGetLastError();
+}
+
+int stage_tw_entries(int R) { return stage_table_size(R); }
 
 // One CTA per tile.
 static unsigned grid_for(int tiles, int) { return (unsigned)tiles; }
@@ -532,9 +581,8 @@ cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
+cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st) {
-  k_make_twiddles<<<TW_N / 256, 256, 0, st>>>(tw);
   k_make_chirp_anchors<<<(unsigned)((nanc + 127) / 128), 128, 0, st>>>(anc, nanc, clog, du, half, f0, alpha, sgn);
   return cudaGetLastError();
 }

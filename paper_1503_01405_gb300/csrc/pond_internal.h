@@ -34,6 +34,7 @@ struct SegIn {
   long long a_len;
   const int8_t* b;
   long long b_len;
+  int vec8;   // both runs 8-byte aligned with a_len % 8 == 0: F1 may load 8 bytes at a time
 };
 
 // Geometry of a plan: segment and pass decomposition.
@@ -50,9 +51,11 @@ struct Geom {
 cudaError_t set_kernel_attributes();
 // Record msg as the calling thread's last error (pond_last_error) and return code.
 int set_error(int code, const char* msg);
-cudaError_t launch_tables(float2* tw, ChirpAnchor* anc, long long nanc, int clog, double du, double half,
+cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st);
 cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st);
+cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st);
+int stage_tw_entries(int R);
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st);
 cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
                             int apply_chirp, const float2* tw, cudaStream_t st);
