@@ -81,7 +81,20 @@ typedef struct {
   int32_t want_voltages;/* nonzero: keep dedispersed voltages for pond_voltages (tests) */
   int32_t timing;       /* nonzero: time each GPU stage with CUDA events (pond_stats) */
   int32_t device;       /* CUDA device ordinal */
-  int32_t reserved[8];
+  /* Batched DM trials: ndm > 0 makes a batched plan over dm_list[0..ndm) (dm,
+   * period and nbins are then ignored and nothing is folded).  Trials that use
+   * the same FFT length share one overlap-save segmentation, set by their largest
+   * DM, and one forward transform per segment; each trial applies its own chirp
+   * and is detected, summed over sub-channels and decimated to its own series.
+   * All trials emit the channel samples of the largest DM in the list. */
+  int32_t ndm;
+  const double* dm_list;
+  int64_t nfft_choices[4]; /* FFT lengths the autotuner may use (0 = unused slot) */
+  int32_t autotune;     /* nonzero (batched plans): group the DM-sorted trials and give
+                           each group one of nfft_choices, minimising the device time per
+                           input sample predicted from timed launches of each length
+                           (cached per nfft, nchan and device); zero: every trial uses nfft */
+  int32_t reserved[7];
 } pond_opts;
 
 /* Fold metadata returned with a profile snapshot. */
@@ -172,6 +185,7 @@ int pond_reset(pond_t h);
 
 /*
  * pond_profile: snapshot of the folded profile (non-destructive; waits for the
+ *   device; POND_E_STATE for a batched plan, which does not fold).
  *   device).  sum[b] (FP64) is the sum of detected power P[g] over the channel
  *   samples folded into bin b = min(floor(frac(g dtc / P) nbins), nbins-1)
  *   (phase in FP64, epoch = first stream sample), hits[b] their count; the
@@ -181,6 +195,13 @@ int pond_reset(pond_t h);
 int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta);
 
 /*
+ * pond_trials: the DM and the FFT length of each trial (in the order of
+ *   dm_list; a single-DM plan has one trial).  dm and nfft (nullable) hold cap
+ *   entries; *ntrials receives the number of trials.
+ */
+int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntrials);
+
+/*
  * pond_timeseries: drain completed samples of the decimated time series.
  *   Sample j sums P[g] over the emitted g with floor(g / D) = j, where
  *   D = t_dec fs / (2 nchan) channel samples (an exact rational; with 4 us
@@ -188,7 +209,8 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta);
  *   counts[j] (nullable) is the number of channel samples summed; the first
  *   and last samples of a stream may be partial.  Copies at most cap samples
  *   into out; *n_out receives the number copied and *first_index the j of
- *   out[0] (both required).  Samples are complete once every g they cover has
+ *   out[0] (both required).  A batched plan writes trial d's samples at
+ *   out[d * cap + i] (out holds ndm * cap floats); counts are common to all trials.  Samples are complete once every g they cover has
  *   been processed; after pond_flush all remaining samples are complete.
  */
 int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n_out,

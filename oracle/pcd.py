@@ -35,7 +35,7 @@ primitive used as the DFT step, pinned against brute-force sums in the tests.
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 from fractions import Fraction
 
 import numpy as np
@@ -213,21 +213,31 @@ def decimate(p: Plan, power: np.ndarray, g0: int) -> tuple[np.ndarray, np.ndarra
     return T, C, j0
 
 
-def run(p: Plan, x: np.ndarray, want_voltages: bool = False) -> Result:
-    """The whole path on a finite stream x (int8 or float), FP64."""
+def run(p: Plan, x: np.ndarray, want_voltages: bool = False, g_range=None) -> Result:
+    """The whole path on a finite stream x (int8 or float), FP64.
+
+    ``g_range`` = (g_first, g_end) narrows the emitted channel samples (the
+    batched form emits one common range for all DM trials).
+    """
     x = np.asarray(x)
     n_total = len(x)
     g_first, g_end = emitted_range(p, n_total)
+    if g_range is not None:
+        g_first, g_end = max(g_first, g_range[0]), min(g_end, g_range[1])
+        g_end = max(g_end, g_first)
     P_parts, V_parts = [], []
     s = 0
     while s * p.S_c + p.n_past < g_end:
+        m_lo = max(p.n_past, g_first - s * p.S_c)
+        m_hi = min(p.M - p.n_fut, g_end - s * p.S_c)
+        if m_hi <= m_lo:
+            s += 1
+            continue
         a = s * p.S
         seg = np.zeros(p.nfft, dtype=np.float64)
         take = x[a:a + p.nfft].astype(np.float64)
         seg[:len(take)] = take                    # zeros past the end of the stream
         v = dedisperse_segment(p, seg)
-        m_lo = p.n_past
-        m_hi = min(p.M - p.n_fut, g_end - s * p.S_c)
         vv = v[:, m_lo:m_hi]
         P_parts.append(np.sum(vv.real ** 2 + vv.imag ** 2, axis=0))
         if want_voltages:
@@ -262,13 +272,32 @@ def dedisperse_at(p: Plan, x: np.ndarray, g_list) -> tuple[np.ndarray, np.ndarra
     return V, np.sum(V.real ** 2 + V.imag ** 2, axis=0)
 
 
-def run_multi_dm(p: Plan, dms, x: np.ndarray) -> list[Result]:
-    """The same path at each DM of ``dms`` (one plan per trial, same geometry)."""
+def trial_plan(p: Plan, dm: float, dm_group_max: float) -> Plan:
+    """One DM trial of the batched form: the chirp at ``dm`` on the segmentation
+    (n_past, n_fut, segment step) that the trial's group takes from its largest
+    DM ``dm_group_max``; all trials of a group share the group's segments."""
+    q = make_plan(p.f0, p.bw, p.fs, float(dm_group_max), p.nfft, p.nchan, p.nbins, p.period,
+                  p.t_dec_ns * 1e-9)
+    return replace(q, dm=float(dm))
+
+
+def batched_range(p: Plan, dm_max: float, n_total: int) -> tuple[int, int]:
+    """[g_first, g_end): the channel samples every trial of a batch up to dm_max emits."""
+    n_past, n_fut = overlap(p.f0, p.bw, dm_max, p.dtc)
+    return n_past, max(n_past, n_total // (2 * p.nchan) - n_fut)
+
+
+def run_batched(p: Plan, trials, x: np.ndarray, want_voltages: bool = False) -> list[Result]:
+    """The batched form: ``trials`` is a list of (dm, nfft, dm_group_max); each
+    trial runs the single-DM path at its DM on its group's segmentation, over
+    the common emitted range of the largest DM of the batch."""
+    dm_max = max(t[0] for t in trials)
+    rng = batched_range(p, dm_max, len(x))
     out = []
-    for dm in dms:
-        q = make_plan(p.f0, p.bw, p.fs, float(dm), p.nfft, p.nchan, p.nbins, p.period,
-                      p.t_dec_ns * 1e-9)
-        out.append(run(q, x))
+    for dm, nfft, gmax in trials:
+        q = trial_plan(make_plan(p.f0, p.bw, p.fs, 0.0, int(nfft), p.nchan, p.nbins, p.period,
+                                 p.t_dec_ns * 1e-9), dm, gmax)
+        out.append(run(q, x, want_voltages=want_voltages, g_range=rng))
     return out
 
 

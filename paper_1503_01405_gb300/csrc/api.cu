@@ -1,17 +1,30 @@
 // C ABI of the engine: planning, stream ingest, segment scheduling, outputs.
 //
 // The host side holds the overlap-save bookkeeping (PONDER Sec. 3.7): segment s
-// starts at real sample s*S (S = 2 nchan S_c) and yields the channel samples
-// g = s*S_c + m, n_past <= m < M - n_fut.  The last n_ov = N - S real samples
-// of the stream seen so far are kept in a device carry buffer for the next
-// segment.  Every arithmetic step on the data runs in the kernels of kernels.cu.
+// of a lane starts at real sample s*S (S = 2 nchan S_c) and yields the channel
+// samples g = s*S_c + m, n_past <= m < M - n_fut.  The last N - S real samples
+// seen so far are kept in the lane's device carry buffer for its next segment.
+//
+// A plan holds one lane per FFT length.  A single-DM plan has one lane with one
+// trial and also folds.  A batched plan holds many DM trials: trials with the
+// same FFT length share a lane, whose segmentation takes the overlap of its
+// largest DM; the lane's forward transform runs once per segment and each trial
+// applies its own chirp in the first inverse pass.  All trials emit the common
+// range of channel samples set by the largest DM of the plan.
+//
+// Every arithmetic step on the data runs in the kernels of kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pond.h"
@@ -42,9 +55,17 @@ int fail(int code, const char* fmt, ...) {
                   cudaGetErrorString(e_), __FILE__, __LINE__);                            \
   } while (0)
 
-constexpr double K_DM = 1.0 / 2.41e-4;        // s MHz^2 (Eq. 1 constant)
-constexpr long long STAGE_BYTES = 64ll << 20; // host-push staging chunk
-constexpr long long TS_RING = 1ll << 22;      // time-series samples held on the device
+#define RC(call)           \
+  do {                     \
+    int rc_ = (call);      \
+    if (rc_) return rc_;   \
+  } while (0)
+
+constexpr double K_DM = 1.0 / 2.41e-4;          // s MHz^2 (Eq. 1 constant)
+constexpr long long STAGE_BYTES = 64ll << 20;   // host-push staging chunk
+constexpr long long TS_RING_SINGLE = 1ll << 22; // time-series samples held on the device (one trial)
+constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched plan
+constexpr int MAX_TRIALS = 4096;
 
 enum Stage { ST_F1 = 0, ST_F2, ST_I1, ST_I2, ST_FOLD, ST_DEC, ST_COUNT };
 const char* kStageName[POND_NSTAGE] = {"fwd_cols_unpack", "fwd_rows_split_chirp", "inv_cols",
@@ -65,9 +86,35 @@ long long gcd_ll(long long a, long long b) {
   return a;
 }
 
-// Events bracketing the stages of one segment (timing mode).
+// Events bracketing the stages of one segment (timing mode); unused slots stay null.
 struct SegEvents {
   cudaEvent_t e[ST_COUNT + 1];
+};
+
+// One DM trial: its chirp anchors and its lane.
+struct Trial {
+  double dm = 0;
+  int lane = 0;
+  ChirpAnchor* anc = nullptr;
+  int clog = 0;
+  long long nanc = 0;
+};
+
+// One FFT length: segmentation, buffers, stream state.
+struct Lane {
+  Geom g;
+  double dm_max = 0;                        // largest DM of the lane (sets the overlap)
+  std::vector<int> trials;
+  float2* bufA = nullptr;
+  float2* bufB = nullptr;
+  float* P = nullptr;
+  float2* stw = nullptr;                    // stage twiddle tables of R1, R2, Q1, Q2
+  const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
+  float2* tw2buf = nullptr;
+  Tw2 twL, tw2L, twM;                       // exp(-2 pi i e/L), exp(-2 pi i e/(2L)), exp(+2 pi i e/M)
+  int8_t* carry[2] = {nullptr, nullptr};
+  int carry_cur = 0;
+  long long seg_start = 0, carry_pos = 0, segments = 0;
 };
 
 }  // namespace
@@ -76,52 +123,46 @@ int pond::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 struct pond_s {
   // parameters
-  double f0, bw, fs, dm, period;
-  int nbins;
+  double f0, bw, fs, period;
+  int nchan, nbins;
   long long t_dec_ns;
   int epoch_day;
   double epoch_sec;
   int want_voltages, timing, device;
-  // geometry
-  Geom g;
-  double dtc, inc;
-  long long dec_num, dec_den;
-  int sgn;
+  bool multi = false;
+  double dtc = 0, inc = 0;
+  long long dec_num = 1, dec_den = 1;
+  int sgn = 1;
+  // lanes and trials (trials in the caller's order)
+  std::vector<Lane> lanes;
+  std::vector<Trial> trials;
+  long long g_first = 0, n_fut_max = 0;     // common emitted range: [g_first, total_c - n_fut_max)
   // streams
   cudaStream_t st = nullptr, cst = nullptr;
   cudaEvent_t ev_done = nullptr, ev_caller = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
-  // device buffers
-  float2* bufA = nullptr;
-  float2* bufB = nullptr;
-  float* P = nullptr;
-  float2* tw = nullptr;                     // stage twiddle tables of R1, R2, Q1, Q2
-  const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
-  float2* tw2buf = nullptr;
-  Tw2 twL, tw2L, twM;   // exp(-2 pi i e/L), exp(-2 pi i e/(2L)), exp(+2 pi i e/M)
-  ChirpAnchor* anc = nullptr;
-  long long nanc = 0;
-  int clog = 0;
+  // fold (single-DM plans)
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
   double* psum = nullptr;
   int* phits = nullptr;
+  // time series rings: [ntrial][ring] sums and counts
+  long long ring = 0;
   float* ts = nullptr;
   int* ts_cnt = nullptr;
-  int8_t* carry[2] = {nullptr, nullptr};
-  int carry_cur = 0;
+  // host-push staging
   int8_t* stage[2] = {nullptr, nullptr};
   int stage_next = 0;
+  // voltages (single-DM plans, tests)
   float2* vbuf = nullptr;
   long long v_cap = 0;
-  // stream state (real-sample indices)
-  long long total_in = 0, seg_start = 0, carry_pos = 0, seg_index = 0;
+  // stream state
+  long long total_in = 0;
   bool flushed = false;
   long long outputs = 0;
-  // time series: samples [ts_drained, ts_written_hi) live in the device ring;
-  // [ts_drained, ts_complete) are complete
+  // time series: [ts_drained, ts_complete) complete on the device; ts_hi = one past the last touched
   long long ts_first = -1, ts_drained = 0, ts_hi = 0, ts_complete = 0;
-  std::vector<float> ts_host;
+  std::vector<std::vector<float>> ts_host;  // per trial
   std::vector<int32_t> ts_host_cnt;
   long long ts_host_first = 0;
   // voltages: device [v_base, v_base + v_len), host spill before that
@@ -134,6 +175,7 @@ struct pond_s {
   SegEvents ev_cur;
   double stage_ms[POND_NSTAGE] = {0};
   long long stage_launches[POND_NSTAGE] = {0};
+  long long launches = 0;
 };
 
 namespace {
@@ -145,34 +187,48 @@ int validate(const pond_opts* o) {
   if (std::fabs(o->fs_hz - 2.0 * std::fabs(o->bw_mhz) * 1e6) > 1e-6 * o->fs_hz)
     return fail(POND_E_ARG, "fs must equal 2|bw| (real Nyquist sampling)");
   if (o->fs_hz != std::floor(o->fs_hz) || o->fs_hz > 9e15) return fail(POND_E_ARG, "fs must be a whole number of Hz");
-  if (!(o->dm >= 0) || !std::isfinite(o->dm)) return fail(POND_E_ARG, "DM must be >= 0");
-  if (!(o->period_s > 0) || !std::isfinite(o->period_s)) return fail(POND_E_ARG, "period must be > 0");
-  if (o->nbins < 1 || o->nbins > MAX_NBINS) return fail(POND_E_ARG, "nbins must be 1..%d", MAX_NBINS);
+  if (o->ndm < 0 || o->ndm > MAX_TRIALS) return fail(POND_E_ARG, "ndm must be 0..%d", MAX_TRIALS);
+  if (o->ndm > 0) {
+    if (!o->dm_list) return fail(POND_E_ARG, "null dm_list");
+    for (int i = 0; i < o->ndm; ++i)
+      if (!(o->dm_list[i] >= 0) || !std::isfinite(o->dm_list[i])) return fail(POND_E_ARG, "DM must be >= 0");
+    if (o->want_voltages) return fail(POND_E_ARG, "want_voltages needs a single-DM plan");
+  } else {
+    if (!(o->dm >= 0) || !std::isfinite(o->dm)) return fail(POND_E_ARG, "DM must be >= 0");
+    if (!(o->period_s > 0) || !std::isfinite(o->period_s)) return fail(POND_E_ARG, "period must be > 0");
+    if (o->nbins < 1 || o->nbins > MAX_NBINS) return fail(POND_E_ARG, "nbins must be 1..%d", MAX_NBINS);
+  }
   if (o->nfft < 4 || (o->nfft & (o->nfft - 1))) return fail(POND_E_NFFT, "nfft must be a power of two");
   if (o->nchan < 1 || (o->nchan & (o->nchan - 1)) || (o->nfft / 2) % o->nchan)
     return fail(POND_E_NCHAN, "nchan must be a power of two dividing nfft/2");
+  for (int i = 0; i < 4; ++i) {
+    const long long n = o->nfft_choices[i];
+    if (n != 0 && (n < 4 || (n & (n - 1)) || (n / 2) % o->nchan))
+      return fail(POND_E_NFFT, "nfft_choices[%d] = %lld is not a usable power of two", i, n);
+  }
   if (o->precision != POND_FP32) return fail(POND_E_UNIMPLEMENTED, "only POND_FP32 is built");
   return POND_OK;
 }
 
-int geometry(const pond_opts* o, Geom* g, double* dtc) {
-  g->N = o->nfft;
-  g->L = o->nfft / 2;
+// Overlap-save geometry of an FFT length at the largest DM it must carry.
+int geometry(const pond_opts* o, long long nfft, double dm, Geom* g) {
+  g->N = nfft;
+  g->L = nfft / 2;
   g->nchan = o->nchan;
   g->M = g->L / o->nchan;
   g->logL = ilog2ll(g->L);
   g->logM = ilog2ll(g->M);
-  *dtc = 2.0 * o->nchan / o->fs_hz;
+  const double dtc = 2.0 * o->nchan / o->fs_hz;
   const double half = std::fabs(o->bw_mhz) / 2.0;
   const double f_lo = o->f0_mhz - half, f_hi = o->f0_mhz + half;
-  const double past = K_DM * o->dm * (std::pow(o->f0_mhz, -2) - std::pow(f_hi, -2));
-  const double fut = K_DM * o->dm * (std::pow(f_lo, -2) - std::pow(o->f0_mhz, -2));
-  g->n_past = (long long)std::ceil(past / *dtc);
-  g->n_fut = (long long)std::ceil(fut / *dtc);
+  const double past = K_DM * dm * (std::pow(o->f0_mhz, -2) - std::pow(f_hi, -2));
+  const double fut = K_DM * dm * (std::pow(f_lo, -2) - std::pow(o->f0_mhz, -2));
+  g->n_past = (long long)std::ceil(past / dtc);
+  g->n_fut = (long long)std::ceil(fut / dtc);
   g->S_c = g->M - g->n_past - g->n_fut;
   if (g->S_c <= 0)
-    return fail(POND_E_NFFT, "nfft %lld does not exceed the overlap (n_past %lld + n_fut %lld >= M %lld)",
-                (long long)o->nfft, g->n_past, g->n_fut, g->M);
+    return fail(POND_E_NFFT, "nfft %lld does not exceed the overlap at DM %g (n_past %lld + n_fut %lld >= M %lld)",
+                nfft, dm, g->n_past, g->n_fut, g->M);
   g->S = 2ll * o->nchan * g->S_c;
   // forward passes: L = R1 * R2, 4 <= R <= 4096, with R2 <= M so that every
   // sub-channel spans whole columns of F2's row layout
@@ -189,12 +245,81 @@ int geometry(const pond_opts* o, Geom* g, double* dtc) {
   g->logQ2 = g->logM - g->logQ1;
   if (g->logR2 < 2 || g->logR2 > g->logM || g->logQ1 < 2 || g->logQ2 < 2 || g->logQ2 > 12)
     return fail(POND_E_NCHAN, "unsupported nchan %d for nfft %lld (need M >= 16 and nchan*4 <= 8192)",
-                o->nchan, (long long)o->nfft);
+                o->nchan, nfft);
   return POND_OK;
 }
 
-// Record boundary event `i` (0 = before F1, i = after stage i-1) of the current segment.
-int record(pond_t h, int i) {
+// Bins per chirp anchor (log2): the dropped quartic Taylor term
+// alpha f0^2/(f0+f)^5 (du span/2)^4 stays below 1e-9 cycles.
+int anchor_log(const pond_opts* o, long long nfft, double dm) {
+  const double du = o->fs_hz / (double)nfft * 1e-6;
+  const double half = std::fabs(o->bw_mhz) / 2.0;
+  const double alpha = K_DM * 1e6 * dm / (o->f0_mhz * o->f0_mhz);
+  const double c4 = alpha * o->f0_mhz * o->f0_mhz / std::pow(o->f0_mhz - half, 5);
+  int clog = CHIRP_LOG_MAX;
+  while (clog > 0 && c4 * std::pow(du * (double)(1ll << (clog - 1)), 4) > 1e-9) --clog;
+  return clog;
+}
+
+int build_trial(pond_t h, const pond_opts* o, Trial* t) {
+  const Lane& ln = h->lanes[t->lane];
+  const long long nfft = ln.g.N;
+  t->clog = anchor_log(o, nfft, t->dm);
+  t->nanc = (ln.g.L + (1ll << t->clog) - 1) >> t->clog;
+  CK(cudaMalloc(&t->anc, t->nanc * sizeof(ChirpAnchor)));
+  const double du = o->fs_hz / (double)nfft * 1e-6;
+  const double half = std::fabs(o->bw_mhz) / 2.0;
+  const double alpha = K_DM * 1e6 * t->dm / (o->f0_mhz * o->f0_mhz);
+  CK(launch_tables(t->anc, t->nanc, t->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  return POND_OK;
+}
+
+int build_lane(pond_t h, Lane* ln) {
+  const Geom& g = ln->g;
+  CK(cudaMalloc(&ln->bufA, g.L * sizeof(float2)));
+  CK(cudaMalloc(&ln->bufB, g.L * sizeof(float2)));
+  CK(cudaMalloc(&ln->P, g.M * sizeof(float)));
+  const int n1 = stage_tw_entries(1 << g.logR1), n2 = stage_tw_entries(1 << g.logR2);
+  const int n3 = stage_tw_entries(1 << g.logQ1), n4 = stage_tw_entries(1 << g.logQ2);
+  CK(cudaMalloc(&ln->stw, (size_t)std::max(1, n1 + n2 + n3 + n4) * sizeof(float2)));
+  ln->stwR1 = ln->stw;
+  ln->stwR2 = ln->stwR1 + n1;
+  ln->stwQ1 = ln->stwR2 + n2;
+  ln->stwQ2 = ln->stwQ1 + n3;
+  auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
+  const long long total = 3ll * TW2_LO + nhi(g.logL) + nhi(g.logL + 1) + nhi(g.logM);
+  CK(cudaMalloc(&ln->tw2buf, total * sizeof(float2)));
+  float2* p = ln->tw2buf;
+  ln->twL = {p, p + TW2_LO};
+  p += TW2_LO + nhi(g.logL);
+  ln->tw2L = {p, p + TW2_LO};
+  p += TW2_LO + nhi(g.logL + 1);
+  ln->twM = {p, p + TW2_LO};
+  CK(cudaMalloc(&ln->carry[0], g.N));
+  CK(cudaMalloc(&ln->carry[1], g.N));
+  CK(launch_stage_tw(const_cast<float2*>(ln->stwR1), 1 << g.logR1, h->st));
+  CK(launch_stage_tw(const_cast<float2*>(ln->stwR2), 1 << g.logR2, h->st));
+  CK(launch_stage_tw(const_cast<float2*>(ln->stwQ1), 1 << g.logQ1, h->st));
+  CK(launch_stage_tw(const_cast<float2*>(ln->stwQ2), 1 << g.logQ2, h->st));
+  CK(launch_tw2(const_cast<float2*>(ln->twL.lo), const_cast<float2*>(ln->twL.hi), g.logL, -1, h->st));
+  CK(launch_tw2(const_cast<float2*>(ln->tw2L.lo), const_cast<float2*>(ln->tw2L.hi), g.logL + 1, -1, h->st));
+  CK(launch_tw2(const_cast<float2*>(ln->twM.lo), const_cast<float2*>(ln->twM.hi), g.logM, +1, h->st));
+  return POND_OK;
+}
+
+void free_lane(Lane* ln) {
+  cudaFree(ln->bufA);
+  cudaFree(ln->bufB);
+  cudaFree(ln->P);
+  cudaFree(ln->stw);
+  cudaFree(ln->tw2buf);
+  cudaFree(ln->carry[0]);
+  cudaFree(ln->carry[1]);
+  *ln = Lane();
+}
+
+// Record boundary event i of the current segment (0 = before F1, i = after stage i-1).
+int record(pond_t h, int i, bool last = false) {
   if (!h->timing) return POND_OK;
   cudaEvent_t e;
   if (!h->ev_pool.empty()) {
@@ -205,7 +330,7 @@ int record(pond_t h, int i) {
   }
   CK(cudaEventRecord(e, h->st));
   h->ev_cur.e[i] = e;
-  if (i == ST_COUNT) h->ev_pending.push_back(h->ev_cur);
+  if (last) h->ev_pending.push_back(h->ev_cur);
   return POND_OK;
 }
 
@@ -214,37 +339,45 @@ int collect_timing(pond_t h) {
   CK(cudaStreamSynchronize(h->st));
   for (auto& se : h->ev_pending) {
     for (int i = 0; i < ST_COUNT; ++i) {
+      if (!se.e[i + 1]) continue;
+      int k = i;
+      while (k >= 0 && !se.e[k]) --k;     // a skipped stage: time from the last boundary
+      if (k < 0) continue;
       float ms = 0;
-      CK(cudaEventElapsedTime(&ms, se.e[i], se.e[i + 1]));
+      CK(cudaEventElapsedTime(&ms, se.e[k], se.e[i + 1]));
       h->stage_ms[i] += ms;
       h->stage_launches[i] += 1;
     }
-    for (int i = 0; i <= ST_COUNT; ++i) h->ev_pool.push_back(se.e[i]);
+    for (int i = 0; i <= ST_COUNT; ++i)
+      if (se.e[i]) h->ev_pool.push_back(se.e[i]);
   }
   h->ev_pending.clear();
   return POND_OK;
 }
 
-// Move completed time-series samples from the device ring to the host vector.
+// Move completed time-series samples of every trial from the device rings to the host.
 int spill_ts(pond_t h) {
   if (h->ts_first < 0 || h->ts_complete <= h->ts_drained) return POND_OK;
   CK(cudaStreamSynchronize(h->st));
   const long long n = h->ts_complete - h->ts_drained;
-  if (h->ts_host.empty()) h->ts_host_first = h->ts_drained;
-  const size_t off = h->ts_host.size();
-  h->ts_host.resize(off + n);
+  const int ntr = (int)h->trials.size();
+  if (h->ts_host[0].empty()) h->ts_host_first = h->ts_drained;
+  const size_t off = h->ts_host[0].size();
+  for (int d = 0; d < ntr; ++d) h->ts_host[d].resize(off + n);
   h->ts_host_cnt.resize(off + n);
-  long long j = h->ts_drained;
-  long long done = 0;
+  long long j = h->ts_drained, done = 0;
   while (done < n) {
-    const long long slot = j % TS_RING;
-    const long long run = std::min(n - done, TS_RING - slot);
-    CK(cudaMemcpyAsync(h->ts_host.data() + off + done, h->ts + slot, run * sizeof(float),
-                       cudaMemcpyDeviceToHost, h->st));
+    const long long slot = j % h->ring;
+    const long long run = std::min(n - done, h->ring - slot);
+    for (int d = 0; d < ntr; ++d) {
+      CK(cudaMemcpyAsync(h->ts_host[d].data() + off + done, h->ts + (size_t)d * h->ring + slot, run * sizeof(float),
+                         cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemsetAsync(h->ts + (size_t)d * h->ring + slot, 0, run * sizeof(float), h->st));
+    }
     CK(cudaMemcpyAsync(h->ts_host_cnt.data() + off + done, h->ts_cnt + slot, run * sizeof(int),
                        cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemsetAsync(h->ts + slot, 0, run * sizeof(float), h->st));
-    CK(cudaMemsetAsync(h->ts_cnt + slot, 0, run * sizeof(int), h->st));
+    for (int d = 0; d < ntr; ++d)
+      CK(cudaMemsetAsync(h->ts_cnt + (size_t)d * h->ring + slot, 0, run * sizeof(int), h->st));
     done += run;
     j += run;
   }
@@ -257,7 +390,7 @@ int spill_voltages(pond_t h) {
   if (!h->want_voltages || h->v_len == 0) return POND_OK;
   CK(cudaStreamSynchronize(h->st));
   if (h->v_host_first < 0) h->v_host_first = h->v_base;
-  for (int c = 0; c < h->g.nchan; ++c) {
+  for (int c = 0; c < h->nchan; ++c) {
     auto& vec = h->v_host[c];
     const size_t off = vec.size();
     vec.resize(off + 2 * h->v_len);
@@ -270,13 +403,31 @@ int spill_voltages(pond_t h) {
   return POND_OK;
 }
 
-// Process one segment (index s) whose input is `in`; m_hi bounds the valid span.
-int run_segment(pond_t h, SegIn in, long long s, long long m_hi) {
-  const Geom& g = h->g;
-  const long long g0 = s * g.S_c + g.n_past;     // first output of this segment
-  const long long nv = m_hi - g.n_past;
-  if (nv <= 0) return POND_OK;
-  // time-series samples touched by this segment
+// The lane's next channel sample still to be produced (its next segment's first output).
+long long lane_next_g(pond_t h, const Lane& ln) {
+  return std::max(h->g_first, (ln.seg_start / ln.g.S) * ln.g.S_c + ln.g.n_past);
+}
+
+void update_complete(pond_t h) {
+  if (h->ts_first < 0) return;
+  long long gn = -1;
+  for (const Lane& ln : h->lanes) {
+    const long long x = lane_next_g(h, ln);
+    gn = gn < 0 ? x : std::min(gn, x);
+  }
+  h->ts_complete = std::max(h->ts_complete, (gn * h->dec_den) / h->dec_num);
+}
+
+// Process segment s of lane li; g_end bounds the emitted channel samples.
+int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
+  Lane& ln = h->lanes[li];
+  const Geom& g = ln.g;
+  const long long m_lo = std::max(g.n_past, h->g_first - s * g.S_c);
+  const long long m_hi = std::min(g.M - g.n_fut, g_end - s * g.S_c);
+  ln.segments = s + 1;
+  if (m_hi <= m_lo) return POND_OK;
+  const long long g0 = s * g.S_c + m_lo;         // first output of this segment
+  const long long nv = m_hi - m_lo;
   const long long j_lo = (g0 * h->dec_den) / h->dec_num;
   const long long j_hi = ((g0 + nv - 1) * h->dec_den) / h->dec_num;
   if (h->ts_first < 0) {
@@ -284,112 +435,108 @@ int run_segment(pond_t h, SegIn in, long long s, long long m_hi) {
     h->ts_drained = j_lo;
     h->ts_complete = j_lo;
   }
-  if (j_hi - h->ts_drained >= TS_RING) {
-    int rc = spill_ts(h);
-    if (rc) return rc;
-  }
+  if (j_hi - h->ts_drained >= h->ring) RC(spill_ts(h));
   float2* vout = nullptr;
   if (h->want_voltages) {
     if (h->v_base < 0) h->v_base = g0;
-    if (h->v_len + nv > h->v_cap) {
-      int rc = spill_voltages(h);
-      if (rc) return rc;
-    }
+    if (h->v_len + nv > h->v_cap) RC(spill_voltages(h));
     vout = h->vbuf;
   }
-  int rc;
-  if ((rc = record(h, 0))) return rc;
   {  // F1 may load 8 bytes (4 columns of a row) at a time when both runs allow it
     const int nl1 = std::min(TILE >> g.logR2, 1 << g.logR1);
     in.vec8 = (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
               (in.b_len == 0 || (uintptr_t)in.b % 8 == 0);
   }
-  CK(launch_fwd_cols(g, in, h->bufA, h->twL, h->stwR2, h->st));
-  if ((rc = record(h, 1 + ST_F1))) return rc;
-  CK(launch_fwd_rows(g, h->bufA, h->bufB, h->tw2L, h->anc, h->clog, 1, h->stwR1, h->st));
-  if ((rc = record(h, 1 + ST_F2))) return rc;
-  CK(launch_inv_cols(g, h->bufB, h->bufA, h->twM, h->stwQ2, h->st));
-  if ((rc = record(h, 1 + ST_I1))) return rc;
-  CK(launch_inv_rows(g, h->bufA, h->P, vout, h->v_cap, h->v_len, (int)m_hi, h->stwQ1, h->st));
-  if ((rc = record(h, 1 + ST_I2))) return rc;
-  CK(launch_fold(h->P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
-  if ((rc = record(h, 1 + ST_FOLD))) return rc;
-  CK(launch_decimate(h->P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts, h->ts_cnt, TS_RING,
-                     h->st));
-  if ((rc = record(h, 1 + ST_DEC))) return rc;
+  h->ev_cur = SegEvents{};
+  RC(record(h, 0));
+  CK(launch_fwd_cols(g, in, ln.bufA, ln.twL, ln.stwR2, h->st));
+  RC(record(h, 1 + ST_F1));
+  const Trial* t0 = &h->trials[ln.trials[0]];
+  // a single-DM lane chirps in F2; a batched lane chirps per trial in I1
+  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw2L, t0->anc, t0->clog, h->multi ? 0 : 1, ln.stwR1, h->st));
+  RC(record(h, 1 + ST_F2));
+  h->launches += 2;
+  for (size_t q = 0; q < ln.trials.size(); ++q) {
+    const int d = ln.trials[q];
+    const Trial& t = h->trials[d];
+    CK(launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, h->multi ? t.anc : nullptr, t.clog, ln.stwQ2, h->st));
+    if (q == 0) RC(record(h, 1 + ST_I1));
+    CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.stwQ1, h->st));
+    if (q == 0) RC(record(h, 1 + ST_I2));
+    if (!h->multi) {
+      CK(launch_fold(ln.P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
+      RC(record(h, 1 + ST_FOLD));
+      h->launches += 2;
+    }
+    CK(launch_decimate(ln.P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
+                       h->ts_cnt + (size_t)d * h->ring, h->ring, h->st));
+    if (q == 0) RC(record(h, 1 + ST_DEC, true));
+    h->launches += 3;
+  }
   if (h->want_voltages) h->v_len += nv;
   h->ts_hi = std::max(h->ts_hi, j_hi + 1);
-  // samples before the next segment's first output are complete
-  const long long g_next = g0 + nv;
-  h->ts_complete = std::max(h->ts_complete, (g_next * h->dec_den) / h->dec_num);
-  h->outputs += nv;
-  h->seg_index = s + 1;
+  if (li == 0) h->outputs += nv;
   return POND_OK;
 }
 
-// Ingest n samples at device pointer d (already ordered on h->st).
+// Ingest n samples at device pointer d into every lane (work ordered on h->st).
 int ingest_device(pond_t h, const int8_t* d, long long n) {
-  const Geom& g = h->g;
   const long long end = h->total_in + n;
-  while (h->seg_start + g.N <= end) {
-    SegIn in;
-    if (h->seg_start < h->total_in) {
-      in.a = h->carry[h->carry_cur] + (h->seg_start - h->carry_pos);
-      in.a_len = h->total_in - h->seg_start;
-      in.b = d;
-      in.b_len = g.N - in.a_len;
-    } else {
-      in.a = d + (h->seg_start - h->total_in);
-      in.a_len = g.N;
-      in.b = nullptr;
-      in.b_len = 0;
+  for (size_t li = 0; li < h->lanes.size(); ++li) {
+    Lane& ln = h->lanes[li];
+    const Geom& g = ln.g;
+    while (ln.seg_start + g.N <= end) {
+      SegIn in;
+      if (ln.seg_start < h->total_in) {
+        in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos);
+        in.a_len = h->total_in - ln.seg_start;
+        in.b = d;
+        in.b_len = g.N - in.a_len;
+      } else {
+        in.a = d + (ln.seg_start - h->total_in);
+        in.a_len = g.N;
+        in.b = nullptr;
+        in.b_len = 0;
+      }
+      RC(run_segment(h, (int)li, in, ln.seg_start / g.S, 1ll << 62));
+      ln.seg_start += g.S;
     }
-    const long long s = h->seg_start / g.S;
-    int rc = run_segment(h, in, s, g.M - g.n_fut);
-    if (rc) return rc;
-    h->seg_start += g.S;
+    // keep [seg_start, end) for the lane's next segment
+    int8_t* dst = ln.carry[1 - ln.carry_cur];
+    if (ln.seg_start < h->total_in) {
+      const long long old = h->total_in - ln.seg_start;
+      CK(cudaMemcpyAsync(dst, ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos), old,
+                         cudaMemcpyDeviceToDevice, h->st));
+      if (n > 0) CK(cudaMemcpyAsync(dst + old, d, n, cudaMemcpyDeviceToDevice, h->st));
+    } else if (end > ln.seg_start) {
+      CK(cudaMemcpyAsync(dst, d + (ln.seg_start - h->total_in), end - ln.seg_start, cudaMemcpyDeviceToDevice,
+                         h->st));
+    }
+    ln.carry_cur = 1 - ln.carry_cur;
+    ln.carry_pos = ln.seg_start;
   }
-  // keep [seg_start, end) for the next segment
-  int8_t* dst = h->carry[1 - h->carry_cur];
-  long long w = 0;
-  if (h->seg_start < h->total_in) {
-    const long long old = h->total_in - h->seg_start;
-    CK(cudaMemcpyAsync(dst, h->carry[h->carry_cur] + (h->seg_start - h->carry_pos), old,
-                       cudaMemcpyDeviceToDevice, h->st));
-    w = old;
-    if (n > 0) CK(cudaMemcpyAsync(dst + w, d, n, cudaMemcpyDeviceToDevice, h->st));
-  } else if (end > h->seg_start) {
-    CK(cudaMemcpyAsync(dst, d + (h->seg_start - h->total_in), end - h->seg_start, cudaMemcpyDeviceToDevice,
-                       h->st));
-  }
-  h->carry_cur = 1 - h->carry_cur;
-  h->carry_pos = h->seg_start;
   h->total_in = end;
+  update_complete(h);
   return POND_OK;
 }
 
 void destroy_all(pond_t h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
-  cudaFree(h->bufA);
-  cudaFree(h->bufB);
-  cudaFree(h->P);
-  cudaFree(h->tw);
-  cudaFree(h->tw2buf);
-  cudaFree(h->anc);
+  for (auto& ln : h->lanes) free_lane(&ln);
+  for (auto& t : h->trials) cudaFree(t.anc);
   cudaFree(h->prof_sum);
   cudaFree(h->prof_hits);
   cudaFree(h->psum);
   cudaFree(h->phits);
   cudaFree(h->ts);
   cudaFree(h->ts_cnt);
-  cudaFree(h->carry[0]);
-  cudaFree(h->carry[1]);
   cudaFree(h->stage[0]);
   cudaFree(h->stage[1]);
   cudaFree(h->vbuf);
   for (auto& se : h->ev_pending)
-    for (int i = 0; i <= ST_COUNT; ++i) cudaEventDestroy(se.e[i]);
+    for (int i = 0; i <= ST_COUNT; ++i)
+      if (se.e[i]) cudaEventDestroy(se.e[i]);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -402,34 +549,172 @@ void destroy_all(pond_t h) {
   delete h;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: per FFT length, the device time of the shared forward passes
+// (F1 + F2) and of one trial's inverse passes (I1 + I2 + decimation), measured
+// with CUDA events over timed launches and cached per (nfft, nchan, device).
+// ---------------------------------------------------------------------------
+
+std::mutex g_tune_mu;
+std::map<std::tuple<long long, int, int>, std::pair<double, double>> g_tune_cache;
+
+int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, double* t_inv) {
+  const auto key = std::make_tuple(nfft, o->nchan, o->device);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *t_fwd = it->second.first;
+      *t_inv = it->second.second;
+      return POND_OK;
+    }
+  }
+  Lane ln;
+  RC(geometry(o, nfft, 0.0, &ln.g));
+  ChirpAnchor* anc = nullptr;
+  float* T = nullptr;
+  int* C = nullptr;
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(h->st);
+    free_lane(&ln);
+    cudaFree(anc);
+    cudaFree(T);
+    cudaFree(C);
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  };
+  int rc = build_lane(h, &ln);
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  const Geom& g = ln.g;
+  const int clog = anchor_log(o, nfft, 0.0);
+  const long long nanc = (g.L + (1ll << clog) - 1) >> clog;
+  const long long nv = std::min<long long>(g.S_c, 1 << 16);
+  cudaError_t ce = cudaMalloc(&anc, nanc * sizeof(ChirpAnchor));
+  if (ce == cudaSuccess) ce = cudaMalloc(&T, (size_t)(nv / 8 + 1) * sizeof(float));
+  if (ce == cudaSuccess) ce = cudaMalloc(&C, (size_t)(nv / 8 + 1) * sizeof(int));
+  for (auto& x : e)
+    if (ce == cudaSuccess) ce = cudaEventCreate(&x);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(ln.carry[0], 0, g.N, h->st);
+  if (ce == cudaSuccess)
+    ce = launch_tables(anc, nanc, clog, o->fs_hz / (double)nfft * 1e-6, std::fabs(o->bw_mhz) / 2, o->f0_mhz, 0.0,
+                       h->sgn, h->st);
+  const int reps = 3;
+  SegIn in{ln.carry[0], g.N, nullptr, 0, 0};
+  for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {      // first pass warms up
+    if (it == 1) ce = cudaEventRecord(e[0], h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA, ln.twL, ln.stwR2, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw2L, anc, clog, 0, ln.stwR1, h->st);
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e[1], h->st);
+  for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
+    if (it == 1) ce = cudaEventRecord(e[2], h->st);
+    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, anc, clog, ln.stwQ2, h->st);
+    if (ce == cudaSuccess)
+      ce = launch_inv_rows(g, ln.bufA, ln.P, nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.stwQ1, h->st);
+    if (ce == cudaSuccess) ce = launch_decimate(ln.P, nv, 0, 8, 1, 0, nv / 8, T, C, nv / 8 + 1, h->st);
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e[3], h->st);
+  float ms_f = 0, ms_i = 0;
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e[3]);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms_f, e[0], e[1]);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms_i, e[2], e[3]);
+  cleanup();
+  if (ce != cudaSuccess) return fail(POND_E_CUDA, "autotune: %s", cudaGetErrorString(ce));
+  *t_fwd = ms_f / reps;
+  *t_inv = ms_i / reps;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = {*t_fwd, *t_inv};
+  return POND_OK;
+}
+
+// Split the DM-sorted trials into contiguous groups, each with one FFT length,
+// minimising the predicted device time per real input sample:
+//   cost(group) = (t_fwd(N) + n_trials t_inv(N)) / S(N, largest DM of the group).
+int choose_groups(pond_t h, const pond_opts* o, const std::vector<double>& dms, const std::vector<int>& order,
+                  const std::vector<long long>& cands, std::vector<long long>* nfft_of_trial) {
+  const int n = (int)order.size();
+  std::vector<double> tf(cands.size(), 0), ti(cands.size(), 0);
+  std::vector<char> usable(cands.size(), 0);
+  for (size_t c = 0; c < cands.size(); ++c) {
+    Geom g0;
+    const std::string keep = g_last_error;
+    if (geometry(o, cands[c], 0.0, &g0)) {
+      g_last_error = keep;
+      continue;
+    }
+    RC(measure_lane(h, o, cands[c], &tf[c], &ti[c]));
+    usable[c] = 1;
+  }
+  std::vector<double> best(n + 1, 1e300);
+  std::vector<int> from(n + 1, -1), with(n + 1, -1);
+  best[0] = 0;
+  for (int j = 1; j <= n; ++j) {
+    const double dmax = dms[order[j - 1]];
+    for (size_t c = 0; c < cands.size(); ++c) {
+      if (!usable[c]) continue;
+      Geom g;
+      const std::string keep = g_last_error;
+      const int rc = geometry(o, cands[c], dmax, &g);
+      g_last_error = keep;
+      if (rc) continue;
+      for (int i = 0; i < j; ++i) {
+        if (best[i] >= 1e299) continue;
+        const double cost = (tf[c] + (j - i) * ti[c]) / (double)g.S;
+        if (best[i] + cost < best[j]) {
+          best[j] = best[i] + cost;
+          from[j] = i;
+          with[j] = (int)c;
+        }
+      }
+    }
+  }
+  if (best[n] >= 1e299) return fail(POND_E_NFFT, "no candidate nfft carries DM %g", dms[order[n - 1]]);
+  nfft_of_trial->assign(dms.size(), 0);
+  for (int j = n; j > 0; j = from[j])
+    for (int k = from[j]; k < j; ++k) (*nfft_of_trial)[order[k]] = cands[with[j]];
+  return POND_OK;
+}
+
 int plan_impl(pond_t* out, const pond_opts* o) {
-  int rc = validate(o);
-  if (rc) return rc;
+  RC(validate(o));
+  // trials (caller's order) and their DMs
+  const bool multi = o->ndm > 0;
+  std::vector<double> dms;
+  if (multi) dms.assign(o->dm_list, o->dm_list + o->ndm);
+  else dms.push_back(o->dm);
+  const double dm_max = *std::max_element(dms.begin(), dms.end());
+  {  // host-side geometry checks before touching the device
+    Geom g;
+    RC(geometry(o, o->nfft, multi ? 0.0 : o->dm, &g));
+    if (multi && !o->autotune) RC(geometry(o, o->nfft, dm_max, &g));
+  }
   pond_t h = new pond_s();
   h->f0 = o->f0_mhz;
   h->bw = o->bw_mhz;
   h->fs = o->fs_hz;
-  h->dm = o->dm;
   h->period = o->period_s;
-  h->nbins = o->nbins;
+  h->nbins = multi ? 0 : o->nbins;
+  h->nchan = o->nchan;
   h->epoch_day = o->epoch_mjd_day;
   h->epoch_sec = o->epoch_mjd_sec;
   h->want_voltages = o->want_voltages;
   h->timing = o->timing;
   h->device = o->device;
   h->sgn = o->bw_mhz > 0 ? 1 : -1;
-  rc = geometry(o, &h->g, &h->dtc);
-  if (rc) {
-    delete h;
-    return rc;
-  }
-  h->inc = h->dtc / o->period_s;
+  h->multi = multi;
+  h->dtc = 2.0 * o->nchan / o->fs_hz;
+  h->inc = multi ? 0.0 : h->dtc / o->period_s;
   const double tdec = o->t_dec_s > 0 ? o->t_dec_s : 61.44e-6;
   h->t_dec_ns = (long long)std::llround(tdec * 1e9);
-  if (h->t_dec_ns <= 0) {
-    delete h;
-    return fail(POND_E_ARG, "t_dec must be >= 1 ns");
-  }
+  auto bail = [&](int rc) {
+    destroy_all(h);
+    return rc;
+  };
+  if (h->t_dec_ns <= 0) return bail(fail(POND_E_ARG, "t_dec must be >= 1 ns"));
   {  // D = t_dec fs / (2 nchan) channel samples, exact rational num/den
     long long num = h->t_dec_ns, den = 1000000000ll * 2 * o->nchan;
     long long fsi = (long long)o->fs_hz;
@@ -439,35 +724,35 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     long long g2 = gcd_ll(num, den);
     num /= g2;
     den /= g2;
-    if (num > (1ll << 40) / std::max(1ll, fsi)) {
-      delete h;
-      return fail(POND_E_ARG, "t_dec too long");
-    }
-    num *= fsi;
-    h->dec_num = num;
+    if (num > (1ll << 40) / std::max(1ll, fsi)) return bail(fail(POND_E_ARG, "t_dec too long"));
+    h->dec_num = num * fsi;
     h->dec_den = den;
   }
-  const Geom& g = h->g;
+  {  // the common emitted range is set by the largest DM
+    const double half = std::fabs(o->bw_mhz) / 2.0;
+    const double fut = K_DM * dm_max * (std::pow(o->f0_mhz - half, -2) - std::pow(o->f0_mhz, -2));
+    const double past = K_DM * dm_max * (std::pow(o->f0_mhz, -2) - std::pow(o->f0_mhz + half, -2));
+    h->g_first = (long long)std::ceil(past / h->dtc);
+    h->n_fut_max = (long long)std::ceil(fut / h->dtc);
+  }
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
-    delete h;
-    return fail(POND_E_CUDA, "no CUDA device");
-  }
-  if (o->device < 0 || o->device >= ndev) {
-    delete h;
-    return fail(POND_E_ARG, "device %d out of range", o->device);
-  }
-#define CKD(call)                   \
-  do {                              \
-    cudaError_t e_ = (call);        \
-    if (e_ != cudaSuccess) {        \
-      int c_ = fail(e_ == cudaErrorMemoryAllocation ? POND_E_OOM : POND_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-      destroy_all(h);               \
-      return c_;                    \
-    }                               \
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return bail(fail(POND_E_CUDA, "no CUDA device"));
+  if (o->device < 0 || o->device >= ndev) return bail(fail(POND_E_ARG, "device %d out of range", o->device));
+#define CKD(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return bail(fail(e_ == cudaErrorMemoryAllocation ? POND_E_OOM : POND_E_CUDA, "%s: %s", #call, \
+                       cudaGetErrorString(e_)));                                                    \
+  } while (0)
+#define RCD(call)              \
+  do {                         \
+    int rc_ = (call);          \
+    if (rc_) return bail(rc_); \
   } while (0)
   CKD(cudaSetDevice(o->device));
-  CKD(cudaDeviceGetAttribute(&h->g.sms, cudaDevAttrMultiProcessorCount, o->device));
+  int sms = 0;
+  CKD(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o->device));
   CKD(set_kernel_attributes());
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
@@ -477,67 +762,64 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     CKD(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
     CKD(cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming));
   }
-  CKD(cudaMalloc(&h->bufA, g.L * sizeof(float2)));
-  CKD(cudaMalloc(&h->bufB, g.L * sizeof(float2)));
-  CKD(cudaMalloc(&h->P, g.M * sizeof(float)));
-  {
-    const int n1 = stage_tw_entries(1 << g.logR1), n2 = stage_tw_entries(1 << g.logR2);
-    const int n3 = stage_tw_entries(1 << g.logQ1), n4 = stage_tw_entries(1 << g.logQ2);
-    CKD(cudaMalloc(&h->tw, (size_t)std::max(1, n1 + n2 + n3 + n4) * sizeof(float2)));
-    h->stwR1 = h->tw;
-    h->stwR2 = h->stwR1 + n1;
-    h->stwQ1 = h->stwR2 + n2;
-    h->stwQ2 = h->stwQ1 + n3;
+  // FFT length of every trial
+  std::vector<long long> nfft_of(dms.size(), o->nfft);
+  if (multi && o->autotune) {
+    std::vector<long long> cands;
+    for (int i = 0; i < 4; ++i)
+      if (o->nfft_choices[i] > 0) cands.push_back(o->nfft_choices[i]);
+    if (cands.empty()) cands.push_back(o->nfft);
+    std::vector<int> order(dms.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dms[a] < dms[b]; });
+    RCD(choose_groups(h, o, dms, order, cands, &nfft_of));
   }
-  {  // two-level twiddle tables for exponents below L, 2L and M
-    auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
-    const long long total = 3ll * TW2_LO + nhi(g.logL) + nhi(g.logL + 1) + nhi(g.logM);
-    CKD(cudaMalloc(&h->tw2buf, total * sizeof(float2)));
-    float2* p = h->tw2buf;
-    h->twL = {p, p + TW2_LO};
-    p += TW2_LO + nhi(g.logL);
-    h->tw2L = {p, p + TW2_LO};
-    p += TW2_LO + nhi(g.logL + 1);
-    h->twM = {p, p + TW2_LO};
+  // one lane per FFT length, in increasing length; trials keep the caller's order
+  std::vector<long long> lens(nfft_of);
+  std::sort(lens.begin(), lens.end());
+  lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
+  h->trials.resize(dms.size());
+  h->lanes.resize(lens.size());
+  for (size_t li = 0; li < lens.size(); ++li) {
+    double lmax = 0;
+    for (size_t d = 0; d < dms.size(); ++d)
+      if (nfft_of[d] == lens[li]) lmax = std::max(lmax, dms[d]);
+    h->lanes[li].dm_max = lmax;
+    RCD(geometry(o, lens[li], lmax, &h->lanes[li].g));
+    h->lanes[li].g.sms = sms;
+    RCD(build_lane(h, &h->lanes[li]));
   }
-  const double du = o->fs_hz / (double)o->nfft * 1e-6;
-  const double half = std::fabs(o->bw_mhz) / 2.0;
-  const double alpha = K_DM * 1e6 * o->dm / (o->f0_mhz * o->f0_mhz);
-  {  // anchor span: the quartic Taylor term alpha f0^2/(f0+f)^5 (du span/2)^4 <= 1e-9 cycles
-    const double fmin = o->f0_mhz - half;
-    const double c4 = alpha * o->f0_mhz * o->f0_mhz / std::pow(fmin, 5);
-    h->clog = CHIRP_LOG_MAX;
-    while (h->clog > 0 && c4 * std::pow(du * (double)(1ll << (h->clog - 1)), 4) > 1e-9) --h->clog;
+  for (size_t d = 0; d < dms.size(); ++d) {
+    Trial& t = h->trials[d];
+    t.dm = dms[d];
+    t.lane = (int)(std::lower_bound(lens.begin(), lens.end(), nfft_of[d]) - lens.begin());
+    h->lanes[t.lane].trials.push_back((int)d);
+    RCD(build_trial(h, o, &t));
   }
-  h->nanc = (g.L + (1ll << h->clog) - 1) >> h->clog;
-  CKD(cudaMalloc(&h->anc, h->nanc * sizeof(ChirpAnchor)));
-  CKD(cudaMalloc(&h->prof_sum, h->nbins * sizeof(double)));
-  CKD(cudaMalloc(&h->prof_hits, h->nbins * sizeof(long long)));
-  CKD(cudaMalloc(&h->psum, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(double)));
-  CKD(cudaMalloc(&h->phits, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(int)));
-  CKD(cudaMalloc(&h->ts, TS_RING * sizeof(float)));
-  CKD(cudaMalloc(&h->ts_cnt, TS_RING * sizeof(int)));
-  CKD(cudaMalloc(&h->carry[0], g.N));
-  CKD(cudaMalloc(&h->carry[1], g.N));
+  // outputs
+  const int ntr = (int)dms.size();
+  h->ring = multi ? TS_RING_MULTI : TS_RING_SINGLE;
+  CKD(cudaMalloc(&h->ts, (size_t)ntr * h->ring * sizeof(float)));
+  CKD(cudaMalloc(&h->ts_cnt, (size_t)ntr * h->ring * sizeof(int)));
+  CKD(cudaMemsetAsync(h->ts, 0, (size_t)ntr * h->ring * sizeof(float), h->st));
+  CKD(cudaMemsetAsync(h->ts_cnt, 0, (size_t)ntr * h->ring * sizeof(int), h->st));
+  h->ts_host.assign(ntr, {});
+  if (!multi) {
+    CKD(cudaMalloc(&h->prof_sum, h->nbins * sizeof(double)));
+    CKD(cudaMalloc(&h->prof_hits, h->nbins * sizeof(long long)));
+    CKD(cudaMalloc(&h->psum, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(double)));
+    CKD(cudaMalloc(&h->phits, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(int)));
+    CKD(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
+    CKD(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
+  }
   if (h->want_voltages) {
-    h->v_cap = std::max<long long>(4 * g.S_c, 1 << 16);
-    CKD(cudaMalloc(&h->vbuf, (size_t)g.nchan * h->v_cap * sizeof(float2)));
-    h->v_host.resize(g.nchan);
+    h->v_cap = std::max<long long>(4 * h->lanes[0].g.S_c, 1 << 16);
+    CKD(cudaMalloc(&h->vbuf, (size_t)h->nchan * h->v_cap * sizeof(float2)));
+    h->v_host.resize(h->nchan);
   }
-  CKD(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
-  CKD(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
-  CKD(cudaMemsetAsync(h->ts, 0, TS_RING * sizeof(float), h->st));
-  CKD(cudaMemsetAsync(h->ts_cnt, 0, TS_RING * sizeof(int), h->st));
-  CKD(launch_tables(h->anc, h->nanc, h->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
-  CKD(launch_stage_tw(const_cast<float2*>(h->stwR1), 1 << g.logR1, h->st));
-  CKD(launch_stage_tw(const_cast<float2*>(h->stwR2), 1 << g.logR2, h->st));
-  CKD(launch_stage_tw(const_cast<float2*>(h->stwQ1), 1 << g.logQ1, h->st));
-  CKD(launch_stage_tw(const_cast<float2*>(h->stwQ2), 1 << g.logQ2, h->st));
-  CKD(launch_tw2(const_cast<float2*>(h->twL.lo), const_cast<float2*>(h->twL.hi), g.logL, -1, h->st));
-  CKD(launch_tw2(const_cast<float2*>(h->tw2L.lo), const_cast<float2*>(h->tw2L.hi), g.logL + 1, -1, h->st));
-  CKD(launch_tw2(const_cast<float2*>(h->twM.lo), const_cast<float2*>(h->twM.hi), g.logM, +1, h->st));
   CKD(cudaStreamSynchronize(h->st));
 #undef CKD
+#undef RCD
   *out = h;
   return POND_OK;
 }
@@ -589,10 +871,8 @@ int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream) {
   if (!d_x) return fail(POND_E_ARG, "null data");
   CK(cudaSetDevice(h->device));
   cudaStream_t cs = (cudaStream_t)cuda_stream;
-  int rc = caller_wait(h, cs);
-  if (rc) return rc;
-  rc = ingest_device(h, d_x, (long long)n);
-  if (rc) return rc;
+  RC(caller_wait(h, cs));
+  RC(ingest_device(h, d_x, (long long)n));
   return caller_release(h, cs);
 }
 
@@ -617,8 +897,7 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
     CK(cudaEventRecord(h->ev_copied[i], h->cst));
     CK(cudaStreamWaitEvent(h->st, h->ev_copied[i], 0));
-    int rc = ingest_device(h, h->stage[i], len);
-    if (rc) return rc;
+    RC(ingest_device(h, h->stage[i], len));
     CK(cudaEventRecord(h->ev_used[i], h->st));
     last = h->ev_copied[i];
   }
@@ -631,20 +910,20 @@ int pond_flush(pond_t h) {
   if (!h) return fail(POND_E_ARG, "null handle");
   if (h->flushed) return POND_OK;
   CK(cudaSetDevice(h->device));
-  const Geom& g = h->g;
-  const long long total_c = h->total_in / (2ll * g.nchan);
-  const long long g_end = total_c - g.n_fut;
-  while (h->seg_start / (2ll * g.nchan) + g.n_past < g_end) {
-    SegIn in;
-    in.a = h->carry[h->carry_cur] + (h->seg_start - h->carry_pos);
-    in.a_len = std::max(0ll, h->total_in - h->seg_start);
-    in.b = nullptr;
-    in.b_len = 0;
-    const long long s = h->seg_start / g.S;
-    const long long m_hi = std::min(g.M - g.n_fut, g_end - s * g.S_c);
-    int rc = run_segment(h, in, s, m_hi);
-    if (rc) return rc;
-    h->seg_start += g.S;
+  const long long total_c = h->total_in / (2ll * h->nchan);
+  const long long g_end = total_c - h->n_fut_max;
+  for (size_t li = 0; li < h->lanes.size(); ++li) {
+    Lane& ln = h->lanes[li];
+    const Geom& g = ln.g;
+    while ((ln.seg_start / g.S) * g.S_c + g.n_past < g_end) {
+      SegIn in;
+      in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos);
+      in.a_len = std::max(0ll, h->total_in - ln.seg_start);
+      in.b = nullptr;
+      in.b_len = 0;
+      RC(run_segment(h, (int)li, in, ln.seg_start / g.S, g_end));
+      ln.seg_start += g.S;
+    }
   }
   h->flushed = true;
   if (h->ts_first >= 0) h->ts_complete = h->ts_hi;
@@ -662,21 +941,27 @@ int pond_sync(pond_t h) {
 int pond_reset(pond_t h) {
   if (!h) return fail(POND_E_ARG, "null handle");
   CK(cudaSetDevice(h->device));
-  int rc = collect_timing(h);
-  if (rc) return rc;
+  RC(collect_timing(h));
   CK(cudaStreamSynchronize(h->st));
-  CK(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
-  CK(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
-  CK(cudaMemsetAsync(h->ts, 0, TS_RING * sizeof(float), h->st));
-  CK(cudaMemsetAsync(h->ts_cnt, 0, TS_RING * sizeof(int), h->st));
+  const int ntr = (int)h->trials.size();
+  if (!h->multi) {
+    CK(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
+    CK(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
+  }
+  CK(cudaMemsetAsync(h->ts, 0, (size_t)ntr * h->ring * sizeof(float), h->st));
+  CK(cudaMemsetAsync(h->ts_cnt, 0, (size_t)ntr * h->ring * sizeof(int), h->st));
   CK(cudaStreamSynchronize(h->st));
-  h->total_in = h->seg_start = h->carry_pos = h->seg_index = 0;
-  h->carry_cur = 0;
+  for (auto& ln : h->lanes) {
+    ln.seg_start = ln.carry_pos = ln.segments = 0;
+    ln.carry_cur = 0;
+  }
+  h->total_in = 0;
   h->flushed = false;
   h->outputs = 0;
+  h->launches = 0;
   h->ts_first = -1;
   h->ts_drained = h->ts_hi = h->ts_complete = 0;
-  h->ts_host.clear();
+  for (auto& v : h->ts_host) v.clear();
   h->ts_host_cnt.clear();
   h->ts_host_first = 0;
   h->v_len = 0;
@@ -688,8 +973,8 @@ int pond_reset(pond_t h) {
 
 int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta) {
   if (!h) return fail(POND_E_ARG, "null handle");
+  if (h->multi) return fail(POND_E_STATE, "a batched plan does not fold");
   CK(cudaSetDevice(h->device));
-  CK(cudaStreamSynchronize(h->st));
   if (sum) CK(cudaMemcpyAsync(sum, h->prof_sum, h->nbins * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (hits) CK(cudaMemcpyAsync(hits, h->prof_hits, h->nbins * sizeof(long long), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
@@ -697,9 +982,9 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta) {
     meta->epoch_mjd_day = h->epoch_day;
     meta->epoch_mjd_sec = h->epoch_sec;
     meta->period_s = h->period;
-    meta->dm = h->dm;
+    meta->dm = h->trials[0].dm;
     meta->dtc_s = h->dtc;
-    meta->first_g = h->g.n_past;
+    meta->first_g = h->g_first;
     meta->nsamples = h->outputs;
     meta->nbins = h->nbins;
   }
@@ -710,16 +995,17 @@ int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n
   if (!h || !n_out || !first_index || (cap > 0 && !out)) return fail(POND_E_ARG, "null argument");
   CK(cudaSetDevice(h->device));
   *n_out = 0;
-  *first_index = h->ts_host.empty() ? std::max(h->ts_drained, 0ll) : h->ts_host_first;
+  *first_index = h->ts_host[0].empty() ? std::max(h->ts_drained, 0ll) : h->ts_host_first;
   if (h->ts_first < 0) return POND_OK;
-  int rc = spill_ts(h);
-  if (rc) return rc;
-  const size_t n = std::min(cap, h->ts_host.size());
+  RC(spill_ts(h));
+  const size_t n = std::min(cap, h->ts_host[0].size());
   if (n) {
-    memcpy(out, h->ts_host.data(), n * sizeof(float));
+    for (size_t d = 0; d < h->trials.size(); ++d) {
+      memcpy(out + d * cap, h->ts_host[d].data(), n * sizeof(float));
+      h->ts_host[d].erase(h->ts_host[d].begin(), h->ts_host[d].begin() + n);
+    }
     if (counts) memcpy(counts, h->ts_host_cnt.data(), n * sizeof(int32_t));
     *first_index = h->ts_host_first;
-    h->ts_host.erase(h->ts_host.begin(), h->ts_host.begin() + n);
     h->ts_host_cnt.erase(h->ts_host_cnt.begin(), h->ts_host_cnt.begin() + n);
     h->ts_host_first += (long long)n;
   }
@@ -731,14 +1017,13 @@ int pond_voltages(pond_t h, float* out_c, size_t cap, size_t* n_out, int64_t* fi
   if (!h || !n_out || !first_g || (cap > 0 && !out_c)) return fail(POND_E_ARG, "null argument");
   if (!h->want_voltages) return fail(POND_E_STATE, "plan made without want_voltages");
   CK(cudaSetDevice(h->device));
-  int rc = spill_voltages(h);
-  if (rc) return rc;
+  RC(spill_voltages(h));
   *n_out = 0;
-  *first_g = h->v_host_first < 0 ? h->g.n_past : h->v_host_first;
+  *first_g = h->v_host_first < 0 ? h->g_first : h->v_host_first;
   if (h->v_host_first < 0) return POND_OK;
   const size_t avail = h->v_host[0].size() / 2;
   const size_t n = std::min(cap, avail);
-  for (int c = 0; c < h->g.nchan; ++c) {
+  for (int c = 0; c < h->nchan; ++c) {
     auto& vec = h->v_host[c];
     memcpy(out_c + (size_t)c * cap * 2, vec.data(), n * 2 * sizeof(float));
     vec.erase(vec.begin(), vec.begin() + 2 * n);
@@ -748,23 +1033,33 @@ int pond_voltages(pond_t h, float* out_c, size_t cap, size_t* n_out, int64_t* fi
   return POND_OK;
 }
 
+int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntrials) {
+  if (!h || !ntrials || cap < 0) return fail(POND_E_ARG, "null argument");
+  *ntrials = (int32_t)h->trials.size();
+  for (int32_t d = 0; d < std::min(cap, *ntrials); ++d) {
+    if (dm) dm[d] = h->trials[d].dm;
+    if (nfft) nfft[d] = h->lanes[h->trials[d].lane].g.N;
+  }
+  return POND_OK;
+}
+
 int pond_stats(pond_t h, pond_stats_t* s) {
   if (!h || !s) return fail(POND_E_ARG, "null argument");
   CK(cudaSetDevice(h->device));
-  int rc = collect_timing(h);
-  if (rc) return rc;
+  RC(collect_timing(h));
   CK(cudaStreamSynchronize(h->st));
   memset(s, 0, sizeof *s);
-  const Geom& g = h->g;
+  const Geom& g = h->lanes[0].g;
   s->samples_in = h->total_in;
-  s->segments = h->seg_index;
+  s->segments = 0;
+  for (auto& ln : h->lanes) s->segments += ln.segments;
   s->outputs = h->outputs;
   s->n_past = g.n_past;
   s->n_fut = g.n_fut;
   s->seg_step = g.S;
   s->nfft = (int32_t)g.N;
   s->nchan = g.nchan;
-  s->kernel_launches = 7;   // F1, F2, I1, I2, fold partial, fold merge, decimate
+  s->kernel_launches = (int32_t)std::min<long long>(h->launches, 0x7fffffff);
   s->flushed = h->flushed;
   const double spec = (double)g.L * sizeof(float2);
   const double nv = (double)g.S_c;

@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
 template <int Q2>
 __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
                                                     int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
+                                                    const ChirpAnchor* __restrict__ anc, int clog,
                                                     const float2* __restrict__ tw) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
       const size_t k1 = ((size_t)c << (logM - logR2)) + j2hi;
       const size_t k2 = (size_t)j1 + ((size_t)j2lo << logQ1);
       r[u] = in[k1 + (k2 << logR1)];
+      if (anc) r[u] = cmul(r[u], chirp_factor(anc, clog, (unsigned)(k2 + (k1 << logR2))));
     }
   }
 #pragma unroll
@@ -614,14 +616,14 @@ cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw
   return cudaGetLastError();
 }
 
-cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const float2* tw,
-                            cudaStream_t st) {
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+                            int clog, const float2* tw, cudaStream_t st) {
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int lines = g.nchan * Q1;
   const int nl = std::min(TILE / Q2, lines);
   const unsigned grid = grid_for(lines / nl, g.sms);
   switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, tw); break;
+#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, anc, clog, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -630,14 +632,14 @@ cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 tw
 }
 
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                            long long vofs, int m_hi, const float2* tw, cudaStream_t st) {
+                            long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st) {
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int b2 = std::min(TILE / (Q1 * g.nchan), Q2);
   const int nl = g.nchan * b2;
   const unsigned grid = grid_for(Q2 / b2, g.sms);
   const float scale = 1.0f / (float)(1u << g.logM);
   switch (Q1) {
-#define CASE(R) case R: k_inv_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, (int)g.n_past, m_hi, scale, tw); break;
+#define CASE(R) case R: k_inv_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, m_lo, m_hi, scale, tw); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;

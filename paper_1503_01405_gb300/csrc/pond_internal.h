@@ -59,10 +59,10 @@ int stage_tw_entries(int R);
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st);
 cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
                             int apply_chirp, const float2* tw, cudaStream_t st);
-cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const float2* tw,
-                            cudaStream_t st);
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+                            int clog, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                            long long vofs, int m_hi, const float2* tw, cudaStream_t st);
+                            long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st);
 size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,

@@ -36,7 +36,7 @@ CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", PON
 EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_flush", "pond_sync",
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
-           "pond_last_error", "pond_destroy", "pond_fold_noalloc"]
+           "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials"]
 
 
 class PondError(RuntimeError):
@@ -53,7 +53,9 @@ class pond_opts(ctypes.Structure):
                 ("epoch_mjd_day", ctypes.c_int32), ("epoch_mjd_sec", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("want_voltages", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("ndm", ctypes.c_int32), ("dm_list", ctypes.POINTER(ctypes.c_double)),
+                ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class pond_meta(ctypes.Structure):
@@ -103,6 +105,7 @@ def lib() -> ctypes.CDLL:
         "pond_destroy": [vp],
         "pond_fold_noalloc": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                               ctypes.c_int32, vp, vp, vp],
+        "pond_trials": [vp, vp, vp, ctypes.c_int32, P(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -128,7 +131,8 @@ class Engine:
     def __init__(self, f0: float, bw: float, fs: float, dm: float, nfft: int, nchan: int, nbins: int,
                  period: float, t_dec: float = 61.44e-6, want_voltages: bool = False,
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
-                 precision: int = POND_FP32):
+                 precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False):
+        """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
         o.nfft, o.nchan, o.nbins, o.period_s = nfft, nchan, nbins, period
@@ -138,6 +142,15 @@ class Engine:
         o.want_voltages = int(bool(want_voltages))
         o.timing = int(bool(timing))
         o.device = device
+        self._dms = None
+        if dms is not None:
+            self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])
+            o.ndm = len(dms)
+            o.dm_list = ctypes.cast(self._dms, ctypes.POINTER(ctypes.c_double))
+            o.autotune = int(bool(autotune))
+            for i, n in enumerate(list(nfft_choices)[:4]):
+                o.nfft_choices[i] = int(n)
+        self.ndm = len(dms) if dms is not None else 0
         self.nbins = nbins
         self.nchan = nchan
         h = ctypes.c_void_p()
@@ -183,10 +196,13 @@ class Engine:
         return s, h, meta
 
     def timeseries(self, cap: int = 1 << 20):
-        """Drain every completed time-series sample: (T float32, counts int32, first index)."""
+        """Drain every completed time-series sample: (T float32, counts int32, first index).
+
+        T is 1-D for a single-DM plan and [ndm, n] for a batched plan."""
+        rows = max(1, self.ndm)
         parts, cparts, first = [], [], None
         while True:
-            out = np.zeros(cap, dtype=np.float32)
+            out = np.zeros((rows, cap), dtype=np.float32)
             cnt = np.zeros(cap, dtype=np.int32)
             n = ctypes.c_size_t()
             j0 = ctypes.c_int64()
@@ -196,13 +212,22 @@ class Engine:
                 first = j0.value
             if n.value == 0:
                 break
-            parts.append(out[:n.value])
+            parts.append(out[:, :n.value])
             cparts.append(cnt[:n.value])
             if n.value < cap:
                 break
-        T = np.concatenate(parts) if parts else np.zeros(0, np.float32)
+        T = np.concatenate(parts, axis=1) if parts else np.zeros((rows, 0), np.float32)
         C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
-        return T, C, first
+        return (T if self.ndm else T[0]), C, first
+
+    def trials(self):
+        """(DM, FFT length) of every trial, in the order the plan was given."""
+        n = ctypes.c_int32()
+        _check(lib().pond_trials(self._h, None, None, 0, ctypes.byref(n)))
+        dm = np.zeros(n.value, np.float64)
+        nf = np.zeros(n.value, np.int64)
+        _check(lib().pond_trials(self._h, _ptr(dm), _ptr(nf), n.value, ctypes.byref(n)))
+        return dm, nf
 
     def voltages(self, cap: int = 1 << 22):
         """Drain every kept dedispersed voltage: (complex64 [nchan, n], first g)."""

@@ -95,3 +95,19 @@ def test_valid_plan_without_gpu_reports_cuda():
     with pytest.raises(pond.PondError) as e:
         pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1)
     assert e.value.name == "CUDA"
+
+
+def test_batched_plan_validation():
+    base = dict(f0=326.5, bw=16.0, fs=32e6, dm=0.0, nfft=1 << 16, nchan=4, nbins=1, period=1.0)
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(**base, dms=[0.1, -1.0])
+    assert e.value.name == "ARG"
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(**base, dms=[0.1], want_voltages=True)
+    assert e.value.name == "ARG"
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(**base, dms=[0.1], nfft_choices=(3000,), autotune=True)
+    assert e.value.name == "NFFT"
+    with pytest.raises(pond.PondError) as e:        # the fixed nfft cannot carry DM 30
+        pond.Engine(**base, dms=[0.1, 30.0])
+    assert e.value.name == "NFFT"

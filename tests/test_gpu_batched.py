@@ -1,0 +1,111 @@
+"""Batched DM trials on the GPU vs the oracle's batched form, through the C ABI.
+
+Trial d of a batched plan is the single-DM path at DM_d on its group's
+segmentation (the group's FFT length, with the overlap of the group's largest
+DM) over the common output range of the plan's largest DM; the oracle computes
+exactly that (oracle.pcd.run_batched).  Tolerance as for single-DM series:
+relative L2 <= 1e-4 per trial, counts and indices exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import pcd
+from paper_1503_01405_gb300 import pond, synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+F0, BW, FS = 326.5, 16.0, 32e6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1503_01405_gb300 import build as pbuild
+    pbuild.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def run_engine(x, dms, nfft, nchan, t_dec, chunks=None, **kw):
+    with pond.Engine(F0, BW, FS, 0.0, nfft, nchan, 1, 1.0, t_dec=t_dec, dms=dms, **kw) as e:
+        pos = 0
+        for c in (chunks or [len(x)]):
+            e.push(x[pos:pos + c])
+            pos += c
+        e.flush()
+        T, C, j0 = e.timeseries()
+        dm_out, nf = e.trials()
+    return T, C, j0, nf
+
+
+def oracle_batched(x, dms, nfft_of, nchan, t_dec):
+    base = pcd.make_plan(F0, BW, FS, 0.0, int(min(nfft_of)), nchan, 1, 1.0, t_dec)
+    gmax = {}
+    for dm, nf in zip(dms, nfft_of):
+        gmax[nf] = max(gmax.get(nf, 0.0), dm)
+    return pcd.run_batched(base, [(dm, nf, gmax[nf]) for dm, nf in zip(dms, nfft_of)], x)
+
+
+def stream(n, seed, dm=0.2):
+    return synth.make_stream(synth.StreamSpec(n=n, seed=seed, dm=dm, period=0.011, snr=80.0, duty=0.05))
+
+
+def test_batched_fixed_nfft_matches_oracle():
+    dms = [0.0, 0.05, 0.3, 0.15, 0.25]
+    nfft, nchan, t_dec = 1 << 16, 16, 8e-6
+    x = stream(7 * (1 << 16) + 12345, seed=31)
+    T, C, j0, nf = run_engine(x, dms, nfft, nchan, t_dec)
+    assert np.all(nf == nfft)
+    res = oracle_batched(x, dms, nf, nchan, t_dec)
+    assert T.shape[0] == len(dms)
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first
+        assert np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
+
+
+def test_batched_autotune_groups_match_oracle():
+    dms = list(np.linspace(0.0, 0.6, 9))
+    nchan, t_dec = 16, 8e-6
+    x = stream(6 * (1 << 17) + 999, seed=32, dm=0.4)
+    T, C, j0, nf = run_engine(x, dms, 1 << 17, nchan, t_dec,
+                              nfft_choices=(1 << 15, 1 << 16, 1 << 17), autotune=True)
+    # every group's FFT length carries its largest DM; lengths grow with DM
+    for nfft in set(nf.tolist()):
+        gm = max(dm for dm, n in zip(dms, nf) if n == nfft)
+        pcd.make_plan(F0, BW, FS, gm, int(nfft), nchan, 1, 1.0, t_dec)
+    assert all(np.diff(nf[np.argsort(dms)]) >= 0)
+    res = oracle_batched(x, dms, nf, nchan, t_dec)
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (d, nf[d], rel(T[d], r.ts))
+
+
+def test_batched_streaming_invariance_bit_exact():
+    dms = [0.1, 0.0, 0.2]
+    x = stream(5 * (1 << 15) + 4321, seed=33)
+    a = run_engine(x, dms, 1 << 15, 8, 8e-6)
+    rng = np.random.default_rng(3)
+    cuts, left = [], len(x)
+    while left > 0:
+        c = int(min(left, rng.integers(1, 70_000)))
+        cuts.append(c)
+        left -= c
+    b = run_engine(x, dms, 1 << 15, 8, 8e-6, chunks=cuts)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_single_trial_batch_equals_single_dm_plan():
+    dm, nfft, nchan, t_dec = 0.2, 1 << 15, 8, 8e-6
+    x = stream(6 * nfft, seed=34)
+    T, C, j0, _ = run_engine(x, [dm], nfft, nchan, t_dec)
+    with pond.Engine(F0, BW, FS, dm, nfft, nchan, 16, 0.011, t_dec=t_dec) as e:
+        e.push(x)
+        e.flush()
+        Ts, Cs, js = e.timeseries()
+    assert js == j0 and np.array_equal(Cs, C)
+    assert rel(T[0], Ts) <= 1e-5

@@ -341,3 +341,43 @@ def test_pulsar_recovered_small_workload():
     snr = np.sum(t * d / sig ** 2) / np.sqrt(np.sum(t ** 2 / sig ** 2))
     assert int(np.argmax(prof)) in range(124, 132)
     assert 40 < snr < 60, snr
+
+
+# --- the batched form (many DM trials on shared segments) ---------------------------
+
+def test_batched_trial_with_own_geometry_is_single_dm_run():
+    p = pcd.make_plan(**ORT, dm=0.05, nfft=1 << 14, nchan=4, nbins=16, period=1e-3)
+    x = synth.make_stream(synth.StreamSpec(n=5 * p.S + 777, seed=13, dm=0.05, period=1e-3, snr=40))
+    q = pcd.trial_plan(p, 0.05, 0.05)
+    assert (q.n_past, q.n_fut, q.S_c, q.S) == (p.n_past, p.n_fut, p.S_c, p.S)
+    a = pcd.run(p, x)
+    b = pcd.run_batched(p, [(0.05, p.nfft, 0.05)], x)[0]
+    assert np.array_equal(a.power, b.power) and np.array_equal(a.ts, b.ts)
+    c = pcd.run(p, x, g_range=pcd.emitted_range(p, len(x)))
+    assert np.array_equal(a.power, c.power)
+
+
+@pytest.mark.parametrize("dms", [(0.0, 0.004, 0.01), (0.01, 0.002)])
+def test_batched_trials_tone_closed_form(dms):
+    """Each trial of a batch obeys the tone closed form at its own DM, on the
+    group's (larger-overlap) segments and the batch's common output range."""
+    base = pcd.make_plan(326.5, 16.0, 32e6, 0.0, 4096, 4, 16, 1e-3)
+    gmax = max(dms)
+    k0 = (3 * base.L) // 7 + 5
+    A, theta = 7.5, 0.3
+    g_geo = pcd.make_plan(326.5, 16.0, 32e6, gmax, 4096, 4, 16, 1e-3)
+    n_seg = 6
+    n = n_seg * g_geo.S + 4096
+    x = synth.tone(n, k0, 4096, A, theta)
+    res = pcd.run_batched(base, [(dm, 4096, gmax) for dm in dms], x, want_voltages=True)
+    g_first, g_end = pcd.batched_range(base, gmax, n)
+    c0, j0 = divmod(k0, base.M)
+    f = k0 * base.fs / base.nfft * 1e-6 - 8.0
+    for dm, r in zip(dms, res):
+        assert r.first_g == g_first
+        g = r.first_g + np.arange(r.voltages.shape[1])
+        complete = g < n_seg * g_geo.S_c + g_geo.n_past
+        c = pcd.K_DM * 1e6 * dm * f * f / (326.5 ** 2 * (326.5 + f))
+        want = A * 4 * np.exp(1j * theta) * np.exp(-2j * np.pi * (c - round(c))) \
+            * np.exp(2j * np.pi * ((j0 * g) % base.M) / base.M)
+        assert np.max(np.abs(r.voltages[c0, complete] - want[complete])) < 1e-9 * A * 4
