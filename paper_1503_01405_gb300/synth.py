@@ -375,3 +375,86 @@ def make_stream_torch(spec: StreamSpec, device, block: int = 1 << 26):
 
 def with_n(spec: StreamSpec, n: int) -> StreamSpec:
     return replace(spec, n=n)
+
+
+# --- single dispersed pulses (transient search workloads) ----------------------------
+
+@dataclass(frozen=True)
+class Pulse:
+    t0: float        # emission time referenced to arrival at f0, s from the chunk start
+    dm: float        # pc cm^-3
+    width: float     # FWHM, s
+    snr: float       # matched-filter S/N over the pulse (same definition as the pulsar)
+
+
+def draw_pulses(seed: int, n_pulses: int, duration: float, dm_range=(2.0, 58.0), edge=0.25,
+                width_range=(1e-4, 2e-3), snr_range=(6.0, 30.0)) -> list[Pulse]:
+    """Pulses at uniform times (``edge`` s away from the chunk ends), uniform DM,
+    log-uniform width and uniform S/N, drawn from Philox sub-stream STREAM_EVENTS."""
+    u = uniform(seed, STREAM_EVENTS, 0, 4 * n_pulses).reshape(n_pulses, 4)
+    out = []
+    for a, b, c, d in u:
+        t0 = edge + a * (duration - 2 * edge)
+        dm = dm_range[0] + b * (dm_range[1] - dm_range[0])
+        w = math.exp(math.log(width_range[0]) + c * math.log(width_range[1] / width_range[0]))
+        snr = snr_range[0] + d * (snr_range[1] - snr_range[0])
+        out.append(Pulse(float(t0), float(dm), float(w), float(snr)))
+    return sorted(out, key=lambda p: p.t0)
+
+
+def pulse_window(spec: StreamSpec, p: Pulse, index: int) -> tuple[int, np.ndarray]:
+    """(first sample, dispersed voltage) of one pulse: extra Gaussian noise of
+    variance A g(t) sigma^2 with g a Gaussian of peak 1 and FWHM p.width,
+    A = snr sqrt(2 / sum g^2), passed through the ISM response at p.dm."""
+    fs = spec.fs
+    half_w = int(math.ceil(3 * p.width * fs))
+    sp = replace(spec, dm=p.dm)
+    late, early = margins(sp)
+    c = int(round(p.t0 * fs))
+    e0 = c - half_w - late
+    ne = 2 * half_w + late + early
+    t = (np.arange(e0, e0 + ne) - p.t0 * fs) / fs
+    g = np.exp(-4.0 * math.log(2.0) * (t / p.width) ** 2)
+    amp = p.snr * math.sqrt(2.0 / np.sum(g * g))
+    w = gaussian(spec.seed, STREAM_PULSAR, (1 << 44) + index * (1 << 36), ne)
+    L = _next_fast(ne)
+    em = np.zeros(L)
+    em[:ne] = spec.sigma * np.sqrt(amp * g) * w
+    v = ism_disperse(em, sp) if p.dm > 0 else em
+    return e0, v[:ne]
+
+
+def make_chunk(spec: StreamSpec, pulses: list[Pulse]) -> np.ndarray:
+    """Noise (plus RFI per spec) with the given dispersed pulses, as int8 (CPU)."""
+    n = spec.n
+    v = spec.sigma * gaussian(spec.seed, STREAM_NOISE, 0, n)
+    for i, p in enumerate(pulses):
+        e0, pv = pulse_window(spec, p, i)
+        a, b = max(0, e0), min(n, e0 + len(pv))
+        if b > a:
+            v[a:b] += pv[a - e0:b - e0]
+    for s0, ln in rfi_bursts(spec, n):
+        e = min(n, s0 + ln)
+        v[s0:e] += spec.rfi_sigma * spec.sigma * gaussian(spec.seed, STREAM_RFI_NOISE, s0, e - s0)
+    return quantise(v, spec.clip)
+
+
+def make_chunk_torch(spec: StreamSpec, pulses: list[Pulse], device):
+    """``make_chunk`` on a CUDA device (torch RNG for the noise; pulses from the
+    CPU model, each generated over its own dispersed window)."""
+    import torch
+    n = spec.n
+    gen = torch.Generator(device=device)
+    gen.manual_seed(spec.seed)
+    v = torch.randn(n, generator=gen, device=device, dtype=torch.float32) * spec.sigma
+    for i, p in enumerate(pulses):
+        e0, pv = pulse_window(spec, p, i)
+        a, b = max(0, e0), min(n, e0 + len(pv))
+        if b > a:
+            v[a:b] += torch.from_numpy(pv[a - e0:b - e0].astype(np.float32)).to(device)
+    return torch.clamp(torch.round(v), -spec.clip, spec.clip).to(torch.int8)
+
+
+# The batched workload: 8 s chunks, 10 single pulses, 128 DM trials 0..60.
+BATCH_CHUNK = StreamSpec(n=256_000_000, seed=4, dm=0.0, period=0.0, snr=0.0)
+BATCH_DMS = [60.0 * d / 127.0 for d in range(128)]
