@@ -109,6 +109,17 @@ typedef struct {
   int32_t nbins;
 } pond_meta;
 
+/* A single-pulse candidate of the boxcar detector. */
+typedef struct {
+  int32_t trial;    /* DM trial (row of the series block) */
+  int32_t width;    /* boxcar width w* in series samples (1, 2, 4, ..., 64) */
+  int64_t index;    /* series sample where the boxcar starts */
+  double snr;       /* S/N at (trial, index, width) */
+  double dm;        /* DM of the trial (pond_candidates; 0 from pond_boxcar) */
+  float score;      /* classifier score, -1 when not scored */
+  int32_t reserved;
+} pond_cand;
+
 /* Counters and per-stage GPU time (ms; stage times only with opts.timing). */
 #define POND_NSTAGE 8
 typedef struct {
@@ -224,6 +235,34 @@ int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n
  *   Errors: POND_E_STATE when the plan was made without want_voltages.
  */
 int pond_voltages(pond_t h, float* out_c, size_t cap, size_t* n_out, int64_t* first_g);
+
+/*
+ * pond_boxcar: boxcar S/N single-pulse search over a block of dedispersed
+ *   series (automatic transient detection is the paper's plan in Sec. 5).
+ *   d_series: DEVICE float [ndm][stride], n samples per row (stride >= n).
+ *   Per row d: mu = median, sigma = 1.4826 x median absolute deviation (exact
+ *   order statistics; an even count takes the FP64 mean of the middle two);
+ *   S_w(t) = (sum_{i<w} T[t+i] - w mu) / (sigma sqrt(w)) for w = 1, 2, ..., 64
+ *   with the sum in FP64 in index order; s(t) = max_w S_w(t) with its smallest
+ *   maximising width w*; (d, t) is a candidate when s >= threshold and no
+ *   point within 2 rows and w* samples has a larger s (equal s: the earlier
+ *   point in (row, sample) order wins).  A row with sigma = 0 has none.
+ *   Candidates go to HOST out[cap], sorted by (trial, index); *n_found gets
+ *   their number.  Allocates device scratch (8 + 1 bytes per series sample).
+ *   Work runs on cuda_stream and the call waits for it.
+ *   Errors: POND_E_ARG, POND_E_OVERRUN (more candidates than cap; *n_found is
+ *   the number found), POND_E_OOM, POND_E_CUDA.
+ */
+int pond_boxcar(const float* d_series, int32_t ndm, int64_t n, int64_t stride, double threshold,
+                pond_cand* out, size_t cap, size_t* n_found, void* cuda_stream);
+
+/*
+ * pond_candidates: pond_boxcar over the handle's completed series samples that
+ *   have not been drained yet (all trials of a batched plan), with index = the
+ *   series sample index j and dm = the trial's DM.  Call it before
+ *   pond_timeseries drains the samples.
+ */
+int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found);
 
 /* pond_stats: counters and per-stage GPU times (waits for the device). */
 int pond_stats(pond_t h, pond_stats_t* s);

@@ -1043,6 +1043,42 @@ int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntria
   return POND_OK;
 }
 
+int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found) {
+  if (!h || !n_found || (cap > 0 && !out)) return fail(POND_E_ARG, "null argument");
+  CK(cudaSetDevice(h->device));
+  *n_found = 0;
+  if (h->ts_first < 0) return POND_OK;
+  CK(cudaStreamSynchronize(h->st));
+  const long long j0 = h->ts_drained, n = h->ts_complete - h->ts_drained;
+  if (n <= 0) return POND_OK;
+  if (n > h->ring) return fail(POND_E_OVERRUN, "more undrained series samples than the device ring holds");
+  const int ntr = (int)h->trials.size();
+  float* blk = nullptr;
+  CK(cudaMalloc(&blk, (size_t)ntr * n * sizeof(float)));
+  // gather [j0, j0 + n) of every trial from the rings (at most two runs each)
+  long long done = 0;
+  cudaError_t e = cudaSuccess;
+  while (done < n && e == cudaSuccess) {
+    const long long slot = (j0 + done) % h->ring;
+    const long long run = std::min(n - done, h->ring - slot);
+    e = cudaMemcpy2DAsync(blk + done, n * sizeof(float), h->ts + slot, h->ring * sizeof(float), run * sizeof(float),
+                          ntr, cudaMemcpyDeviceToDevice, h->st);
+    done += run;
+  }
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return fail(POND_E_CUDA, "gather series: %s", cudaGetErrorString(e));
+  }
+  const int rc = run_boxcar(blk, ntr, n, n, threshold, out, cap, n_found, h->st);
+  cudaFree(blk);
+  const size_t m = std::min(*n_found, cap);
+  for (size_t i = 0; i < m; ++i) {
+    out[i].index += j0;
+    out[i].dm = h->trials[out[i].trial].dm;
+  }
+  return rc;
+}
+
 int pond_stats(pond_t h, pond_stats_t* s) {
   if (!h || !s) return fail(POND_E_ARG, "null argument");
   CK(cudaSetDevice(h->device));

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 
+#include "../../include/pond.h"
+
 namespace pond {
 
 constexpr int CHIRP_LOG_MAX = 8;             // at most 2^8 bins per chirp anchor
@@ -49,6 +51,8 @@ struct Geom {
 };
 
 cudaError_t set_kernel_attributes();
+int run_boxcar(const float* d_series, int ndm, long long n, long long stride, double thr, pond_cand* host_out,
+               size_t cap, size_t* n_found, cudaStream_t st);
 // Record msg as the calling thread's last error (pond_last_error) and return code.
 int set_error(int code, const char* msg);
 cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du, double half,

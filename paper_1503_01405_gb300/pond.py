@@ -36,7 +36,8 @@ CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", PON
 EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_flush", "pond_sync",
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
-           "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials"]
+           "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials",
+           "pond_boxcar", "pond_candidates"]
 
 
 class PondError(RuntimeError):
@@ -62,6 +63,12 @@ class pond_meta(ctypes.Structure):
     _fields_ = [("epoch_mjd_day", ctypes.c_int32), ("epoch_mjd_sec", ctypes.c_double),
                 ("period_s", ctypes.c_double), ("dm", ctypes.c_double), ("dtc_s", ctypes.c_double),
                 ("first_g", ctypes.c_int64), ("nsamples", ctypes.c_int64), ("nbins", ctypes.c_int32)]
+
+
+class pond_cand(ctypes.Structure):
+    _fields_ = [("trial", ctypes.c_int32), ("width", ctypes.c_int32), ("index", ctypes.c_int64),
+                ("snr", ctypes.c_double), ("dm", ctypes.c_double), ("score", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 
 class pond_stats_t(ctypes.Structure):
@@ -106,6 +113,9 @@ def lib() -> ctypes.CDLL:
         "pond_fold_noalloc": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                               ctypes.c_int32, vp, vp, vp],
         "pond_trials": [vp, vp, vp, ctypes.c_int32, P(ctypes.c_int32)],
+        "pond_boxcar": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp,
+                        ctypes.c_size_t, P(ctypes.c_size_t), vp],
+        "pond_candidates": [vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -119,6 +129,19 @@ def _check(rc: int) -> None:
     if rc != POND_OK:
         msg = lib().pond_last_error().decode(errors="replace")
         raise PondError(rc, msg or lib().pond_strerror(rc).decode())
+
+
+def cand_dict(c) -> dict:
+    return {"trial": c.trial, "width": c.width, "index": c.index, "snr": c.snr, "dm": c.dm, "score": c.score}
+
+
+def boxcar(d_series_ptr: int, ndm: int, n: int, stride: int, threshold: float = 6.0, cap: int = 1 << 16,
+           stream: int = 0):
+    """pond_boxcar over a device series block [ndm][stride]: list of candidate dicts."""
+    out = (pond_cand * cap)()
+    nf = ctypes.c_size_t()
+    _check(lib().pond_boxcar(d_series_ptr, ndm, n, stride, threshold, out, cap, ctypes.byref(nf), stream))
+    return [cand_dict(out[i]) for i in range(nf.value)]
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -219,6 +242,13 @@ class Engine:
         T = np.concatenate(parts, axis=1) if parts else np.zeros((rows, 0), np.float32)
         C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
         return (T if self.ndm else T[0]), C, first
+
+    def candidates(self, threshold: float = 6.0, cap: int = 1 << 16):
+        """Boxcar candidates over the completed, undrained series: list of dicts."""
+        out = (pond_cand * cap)()
+        n = ctypes.c_size_t()
+        _check(lib().pond_candidates(self._h, threshold, out, cap, ctypes.byref(n)))
+        return [cand_dict(out[i]) for i in range(n.value)]
 
     def trials(self):
         """(DM, FFT length) of every trial, in the order the plan was given."""
