@@ -264,6 +264,50 @@ int pond_boxcar(const float* d_series, int32_t ndm, int64_t n, int64_t stride, d
  */
 int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found);
 
+/*
+ * Single-pulse candidate classifier (automatic transient detection is the
+ * paper's plan in Sec. 5; the network is this library's).  Input: patches of
+ * 32 DM trials x 256 series samples, BF16 [batch][32][256] in device memory
+ * (see pond_patches).  Network: 3 x [Conv1d(32 -> 32, kernel 7, zero padding
+ * 3) + ReLU], 2:1 max-pool after the first two, global average over time,
+ * Linear(32 -> 4), softmax over {dispersed pulse, broadband RFI, narrowband
+ * RFI, noise}.  Parameters (POND_CNN_NPARAM FP32 values, flat): for each conv
+ * layer w[co][ci][k] then b[co]; then fc w[4][32], fc b[4].  BF16 weights and
+ * activations, FP32 accumulation and master weights; training minimises the
+ * batch-mean cross-entropy with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Weight gradients are reduced over the batch in sample order (deterministic).
+ * A network belongs to one device and one thread at a time.
+ */
+#define POND_CNN_NPARAM 21732
+typedef struct pond_cnn_s* pond_cnn_t;
+/* create with host initial parameters; scratch for batches up to max_batch */
+int pond_cnn_create(pond_cnn_t* out, const float* init_params, int32_t max_batch, int32_t device);
+/* replace the parameters (host) and reset the Adam state */
+int pond_cnn_set_params(pond_cnn_t net, const float* params);
+/* copy the FP32 master parameters to host memory */
+int pond_cnn_params(pond_cnn_t net, float* out);
+/* class probabilities of a batch: d_prob (device) [batch][4] */
+int pond_cnn_forward(pond_cnn_t net, const void* d_x, int32_t batch, float* d_prob, void* cuda_stream);
+/* gradient of the batch-mean cross-entropy (host [POND_CNN_NPARAM], nullable) and
+ * the loss (host, nullable), without updating; labels are device int32 [batch] */
+int pond_cnn_gradient(pond_cnn_t net, const void* d_x, const int32_t* d_labels, int32_t batch,
+                      float* grad_out, float* loss_out, void* cuda_stream);
+/* one Adam step on a batch; loss_out (host, nullable) receives the loss before it */
+int pond_cnn_train_step(pond_cnn_t net, const void* d_x, const int32_t* d_labels, int32_t batch,
+                        float lr, float* loss_out, void* cuda_stream);
+int pond_cnn_destroy(pond_cnn_t net);
+
+/*
+ * pond_patches: cut classifier patches from a series block [ndm][stride]
+ *   (DEVICE float, n samples per row).  Patch p covers rows d0..d0+31 and
+ *   samples t0..t0+255 with (d0, t0) = d_corners[2p], d_corners[2p+1] (device
+ *   int32); rows and samples outside the block repeat the nearest edge.  Each
+ *   patch is shifted to zero mean and scaled to unit standard deviation (FP32;
+ *   a constant patch keeps scale 1) and stored as BF16 [npatch][32][256].
+ */
+int pond_patches(const float* d_series, int32_t ndm, int64_t n, int64_t stride, const int32_t* d_corners,
+                 int32_t npatch, void* d_out, void* cuda_stream);
+
 /* pond_stats: counters and per-stage GPU times (waits for the device). */
 int pond_stats(pond_t h, pond_stats_t* s);
 

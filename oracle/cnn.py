@@ -152,3 +152,17 @@ def init_params(rng_uniform: np.ndarray) -> np.ndarray:
     bf = np.sqrt(6.0 / C)
     theta[o:o + NCLS * C] = (2 * u[o:o + NCLS * C] - 1) * bf * 0.5
     return theta
+
+
+def patch(series: np.ndarray, d0: int, t0: int, rows: int = C, cols: int = T) -> np.ndarray:
+    """Rows d0.. and samples t0.. of a series block (indices outside repeat the
+    nearest edge), less the mean, over the standard deviation (population; a
+    constant patch keeps scale 1), in FP64."""
+    series = np.asarray(series, dtype=np.float64)
+    ndm, n = series.shape
+    d = np.clip(np.arange(d0, d0 + rows), 0, ndm - 1)
+    t = np.clip(np.arange(t0, t0 + cols), 0, n - 1)
+    p = series[np.ix_(d, t)]
+    mu = p.mean()
+    sd = np.sqrt(np.mean((p - mu) ** 2))
+    return (p - mu) / (sd if sd > 0 else 1.0)

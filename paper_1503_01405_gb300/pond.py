@@ -37,7 +37,8 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
            "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials",
-           "pond_boxcar", "pond_candidates"]
+           "pond_boxcar", "pond_candidates", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
+           "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches"]
 
 
 class PondError(RuntimeError):
@@ -116,6 +117,14 @@ def lib() -> ctypes.CDLL:
         "pond_boxcar": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp,
                         ctypes.c_size_t, P(ctypes.c_size_t), vp],
         "pond_candidates": [vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
+        "pond_cnn_create": [P(vp), vp, ctypes.c_int32, ctypes.c_int32],
+        "pond_cnn_set_params": [vp, vp],
+        "pond_cnn_params": [vp, vp],
+        "pond_cnn_forward": [vp, vp, ctypes.c_int32, vp, vp],
+        "pond_cnn_gradient": [vp, vp, vp, ctypes.c_int32, vp, vp, vp],
+        "pond_cnn_train_step": [vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp, vp],
+        "pond_cnn_destroy": [vp],
+        "pond_patches": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -305,3 +314,67 @@ class Engine:
             self.close()
         except Exception:
             pass
+
+
+CNN_NPARAM = 21732
+
+
+class Classifier:
+    """The single-pulse candidate classifier (a ``pond_cnn_t``)."""
+
+    def __init__(self, params: np.ndarray, max_batch: int = 512, device: int = 0):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == CNN_NPARAM
+        h = ctypes.c_void_p()
+        _check(lib().pond_cnn_create(ctypes.byref(h), _ptr(p), max_batch, device))
+        self._h = h
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(CNN_NPARAM, np.float32)
+        _check(lib().pond_cnn_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, params: np.ndarray) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().pond_cnn_set_params(self._h, _ptr(p)))
+
+    def forward(self, x, stream: int = 0):
+        """Probabilities [B, 4] (torch CUDA tensor) of BF16 patches x [B, 32, 256]."""
+        import torch
+        prob = torch.empty((x.shape[0], 4), dtype=torch.float32, device=x.device)
+        _check(lib().pond_cnn_forward(self._h, x.data_ptr(), x.shape[0], prob.data_ptr(), stream))
+        return prob
+
+    def gradient(self, x, labels, stream: int = 0):
+        g = np.zeros(CNN_NPARAM, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().pond_cnn_gradient(self._h, x.data_ptr(), labels.data_ptr(), x.shape[0], _ptr(g),
+                                       ctypes.byref(loss), stream))
+        return float(loss.value), g
+
+    def train_step(self, x, labels, lr: float, stream: int = 0, want_loss: bool = False):
+        loss = ctypes.c_float()
+        _check(lib().pond_cnn_train_step(self._h, x.data_ptr(), labels.data_ptr(), x.shape[0], lr,
+                                         ctypes.byref(loss) if want_loss else None, stream))
+        return float(loss.value) if want_loss else None
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pond_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def patches(series, corners, stream: int = 0):
+    """BF16 patches [P, 32, 256] from a device series block [ndm, n] and int32 corners [P, 2]."""
+    import torch
+    assert series.dtype == torch.float32 and series.is_cuda and corners.dtype == torch.int32
+    out = torch.empty((corners.shape[0], 32, 256), dtype=torch.bfloat16, device=series.device)
+    _check(lib().pond_patches(series.data_ptr(), series.shape[0], series.shape[1], series.stride(0),
+                              corners.data_ptr(), corners.shape[0], out.data_ptr(), stream))
+    return out
