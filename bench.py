@@ -282,6 +282,45 @@ def run_batched(args, rank, ws, dist):
     eng.close()
 
 
+def run_learned(args, rank):
+    """Classifier on DM-time patches: training chunks and disjoint held-out
+    chunks (different seeds) through the batched engine; recall and false
+    positive rate of the classifier and of the boxcar detector; inference rate."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    from oracle import cnn as _cnn_init   # parameter initialisation only (uniforms -> He bounds)
+    from paper_1503_01405_gb300 import build as pbuild
+    from paper_1503_01405_gb300 import learn, pond, synth
+
+    pbuild.build()
+    t0 = time.perf_counter()
+    Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000)
+    Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000)
+    gen_s = time.perf_counter() - t0
+    theta = _cnn_init.init_params(synth.uniform(99, 0, 0, _cnn_init.n_params())).astype(np.float32)
+    clf = pond.Classifier(theta, max_batch=512)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = learn.train(clf, Xtr, Ytr, epochs=30, batch=256, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    res = learn.evaluate(learn.predict(clf, Xte), Yte, Fte)
+    rate = learn.inference_rate(clf, Xte)
+    clf.close()
+    line = {"metric": "single-pulse candidates classified per second (CNN inference)", "value": rate,
+            "unit": "candidates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "learned: DM-time patches (32 trials x 256 samples of 32 us) from the batched "
+                                   "engine on labelled 8 s chunks; pulse / DM-0 burst / narrowband / noise",
+                       "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)), "epochs": 30,
+                       "batch": 256, "lr": 2e-3},
+            "evaluation": res, "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
+            "dataset_s": gen_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,8 +329,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched"],
-                    help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks")
+    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned"],
+                    help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks; "
+                         "learned: classifier training and evaluation beside the boxcar detector")
+    ap.add_argument("--chunks", type=int, default=40, help="learned: 8 s training chunks")
     args = ap.parse_args()
     rank, ws, dist = dist_init()
     if args.impl == "reference":
@@ -299,6 +340,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args, rank, ws, dist)
+        return
+    if args.workload == "learned":
+        run_learned(args, rank)
         return
     import numpy as np
     import torch

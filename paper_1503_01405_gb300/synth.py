@@ -458,3 +458,103 @@ def make_chunk_torch(spec: StreamSpec, pulses: list[Pulse], device):
 # The batched workload: 8 s chunks, 10 single pulses, 128 DM trials 0..60.
 BATCH_CHUNK = StreamSpec(n=256_000_000, seed=4, dm=0.0, period=0.0, snr=0.0)
 BATCH_DMS = [60.0 * d / 127.0 for d in range(128)]
+
+
+# --- labelled events for the candidate classifier ------------------------------------
+
+EV_PULSE, EV_BURST, EV_NARROW, EV_NOISE = 0, 1, 2, 3
+
+
+@dataclass(frozen=True)
+class Event:
+    kind: int        # EV_PULSE, EV_BURST (undispersed broadband), EV_NARROW (sinusoid), EV_NOISE
+    t0: float        # s from the chunk start (arrival at f0 for pulses)
+    dm: float        # pulse DM; 0 for a burst; the DM row a patch is centred on otherwise
+    width: float     # FWHM (pulse, burst) or duration (sinusoid), s
+    snr: float       # matched-filter S/N (pulse, burst)
+    freq: float      # baseband frequency of a sinusoid, MHz
+
+
+def draw_events(seed: int, n: int, duration: float, dm_max: float = 60.0, spacing: float = 0.3,
+                first: float = 0.3) -> list[Event]:
+    """n events of uniformly drawn kind at t = first + i spacing (the DM-60 sweep
+    is 0.23 s, so events do not overlap).  Pulses: DM U(2, dm_max - 2), width
+    log-U(0.1, 2) ms, S/N U(6, 30); bursts: DM 0, width log-U(0.05, 2) ms,
+    S/N U(6, 30); sinusoids: amplitude 2 sigma, 1-20 ms, uniform frequency;
+    noise: nothing (centre DM drawn uniformly)."""
+    u = uniform(seed, STREAM_EVENTS, 1 << 20, 6 * n).reshape(n, 6)
+    out = []
+    for i in range(n):
+        k = int(u[i, 0] * 4) % 4
+        t0 = first + i * spacing
+        if t0 > duration - 0.25:
+            break
+        if k == EV_PULSE:
+            dm = 2.0 + u[i, 1] * (dm_max - 4.0)
+            w = math.exp(math.log(1e-4) + u[i, 2] * math.log(20.0))
+        elif k == EV_BURST:
+            dm = 0.0
+            w = math.exp(math.log(5e-5) + u[i, 2] * math.log(40.0))
+        elif k == EV_NARROW:
+            dm = u[i, 1] * dm_max
+            w = 1e-3 + u[i, 2] * 19e-3
+        else:
+            dm = u[i, 1] * dm_max
+            w = 0.0
+        out.append(Event(k, float(t0), float(dm), float(w), float(6.0 + u[i, 3] * 24.0), float(u[i, 4] * 16.0)))
+    return out
+
+
+def _ism_phase_torch(Lb: int, spec: StreamSpec, dm: float, device):
+    import torch
+    k = torch.arange(Lb // 2 + 1, dtype=torch.float64, device=device)
+    step = spec.fs / Lb * 1e-6
+    half = abs(spec.bw) / 2
+    f = k * step - half if spec.bw > 0 else half - k * step
+    c = K_DM * 1e6 * dm * f * f / (spec.f0 * spec.f0 * (spec.f0 + f))
+    c = c - torch.round(c)
+    sign = 1.0 if spec.bw > 0 else -1.0
+    return torch.polar(torch.ones_like(c), sign * 2 * math.pi * c).to(torch.complex64)
+
+
+def make_labelled_chunk_torch(spec: StreamSpec, events: list[Event], device, seed_offset: int = 0):
+    """Noise plus the events of ``events`` on a CUDA device, as int8.  Pulses and
+    bursts follow the pulse model of ``pulse_window`` (dispersed by the ISM
+    response with torch.fft); sinusoids are 2 sigma tones with a Hann envelope."""
+    import torch
+    n = spec.n
+    gen = torch.Generator(device=device)
+    gen.manual_seed(spec.seed + seed_offset)
+    v = torch.randn(n, generator=gen, device=device, dtype=torch.float32) * spec.sigma
+    fs = spec.fs
+    for ev in events:
+        if ev.kind in (EV_PULSE, EV_BURST):
+            sp = replace(spec, dm=ev.dm)
+            late, early = margins(sp)
+            half_w = int(math.ceil(3 * ev.width * fs))
+            c = int(round(ev.t0 * fs))
+            e0 = c - half_w - late
+            ne = 2 * half_w + late + early
+            t = (torch.arange(e0, e0 + ne, device=device, dtype=torch.float64) - ev.t0 * fs) / fs
+            g = torch.exp(-4.0 * math.log(2.0) * (t / ev.width) ** 2)
+            amp = ev.snr * math.sqrt(2.0 / float(torch.sum(g * g)))
+            w = torch.randn(ne, generator=gen, device=device, dtype=torch.float64)
+            em = spec.sigma * torch.sqrt(amp * g) * w
+            if ev.dm > 0:
+                L = 1 << int(math.ceil(math.log2(ne)))
+                buf = torch.zeros(L, dtype=torch.float32, device=device)
+                buf[:ne] = em.to(torch.float32)
+                em = torch.fft.irfft(torch.fft.rfft(buf) * _ism_phase_torch(L, spec, ev.dm, device), n=L)[:ne]
+            a, b = max(0, e0), min(n, e0 + ne)
+            if b > a:
+                v[a:b] += em[a - e0:b - e0].to(torch.float32)
+        elif ev.kind == EV_NARROW:
+            ln = int(ev.width * fs)
+            a = int(round(ev.t0 * fs)) - ln // 2
+            t = torch.arange(ln, device=device, dtype=torch.float64)
+            env = 0.5 - 0.5 * torch.cos(2 * math.pi * t / max(ln - 1, 1))
+            tone = 2.0 * spec.sigma * env * torch.cos(2 * math.pi * ev.freq * 1e6 * t / fs)
+            a0, b0 = max(0, a), min(n, a + ln)
+            if b0 > a0:
+                v[a0:b0] += tone[a0 - a:b0 - a].to(torch.float32)
+    return torch.clamp(torch.round(v), -spec.clip, spec.clip).to(torch.int8)
