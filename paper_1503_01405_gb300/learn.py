@@ -107,6 +107,7 @@ def train(clf: pond.Classifier, X, Y: np.ndarray, epochs: int, batch: int, lr: f
 
 
 def predict(clf: pond.Classifier, X, batch: int = 512) -> np.ndarray:
+    batch = min(batch, clf.max_batch)
     out = []
     for s in range(0, X.shape[0], batch):
         out.append(clf.forward(X[s:s + batch].contiguous()).cpu().numpy())
@@ -136,6 +137,7 @@ def evaluate(prob: np.ndarray, Y: np.ndarray, flags: np.ndarray) -> dict:
 def inference_rate(clf: pond.Classifier, X, batch: int = 512, reps: int = 20) -> float:
     """Patches classified per second (CUDA events around repeated batches)."""
     import torch
+    batch = min(batch, clf.max_batch)
     xb = X[:batch].contiguous()
     if xb.shape[0] < batch:
         xb = xb.repeat((math.ceil(batch / xb.shape[0]), 1, 1))[:batch].contiguous()

@@ -328,6 +328,7 @@ class Classifier:
         h = ctypes.c_void_p()
         _check(lib().pond_cnn_create(ctypes.byref(h), _ptr(p), max_batch, device))
         self._h = h
+        self.max_batch = max_batch
 
     def params(self) -> np.ndarray:
         out = np.zeros(CNN_NPARAM, np.float32)
