@@ -281,6 +281,175 @@ def run_batched(args, rank, ws, dist):
         print(json.dumps(line), flush=True)
     eng.close()
 
+PREC_PLAN = dict(dm=3.0, nfft=1 << 21, nchan=1, nbins=256, period=0.253, t_dec=61.44e-6)
+
+
+def run_precision(args, rank, ws, dist):
+    """Precision form: the 2^23-sample stream (DM 3, P 0.253 s, S/N 50 per fold;
+    nfft 2^21, one channel, 256-bin fold) with every radix-16 FFT stage computed
+    as split-BF16 16-point DFT-matrix products on the tensor cores (three product
+    terms, FP32 accumulation).  The five-term form and the FP32 path run the same
+    stream in the same process: value is the three-term throughput, the line
+    carries the FP32 and five-term throughputs, the measured error of every
+    output against the FP64 oracle, and the same comparison at the full-rate
+    geometry (nfft 2^24, 64 channels) on a 2^28-sample slice of the full-rate
+    stream.  The 8 MB stream fits in L2, so L2 is flushed (a 256 MB write)
+    before every timed step and each step is timed alone with CUDA events."""
+    import numpy as np
+    import torch
+
+    from oracle import pcd
+    from paper_1503_01405_gb300 import build as pbuild
+    from paper_1503_01405_gb300 import pond, synth
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pbuild.build()
+    P = PREC_PLAN
+    spec = synth.replace(synth.SMALL, seed=synth.SMALL.seed + rank)
+    xh = synth.make_stream(spec)
+    n = len(xh)
+    x_dev = torch.from_numpy(xh).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    precs = {"bf16x3": pond.POND_SPLIT_BF16, "bf16x5": pond.POND_SPLIT_BF16_5T, "fp32": pond.POND_FP32}
+
+    def engine(prec, timing=False, want_voltages=False, plan=P):
+        return pond.Engine(F0, BW, FS, plan["dm"], plan["nfft"], plan["nchan"], plan["nbins"], plan["period"],
+                           t_dec=plan["t_dec"], timing=timing, want_voltages=want_voltages, device=local,
+                           precision=prec)
+
+    def timed(eng, x, steps, warmup, flush_l2):
+        def step():
+            eng.reset()
+            eng.push_tensor(x, stream)
+            eng.flush()
+        for _ in range(warmup):
+            step()
+        st0 = eng.stats()
+        torch.cuda.synchronize()
+        barrier(dist)
+        total = 0.0
+        for _ in range(steps):
+            if flush_l2:
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        barrier(dist)
+        return max_over_ranks(dist, total), st0, eng.stats()
+
+    res = {}
+    with Clocks(local) as clk:
+        for name, prec in precs.items():
+            eng = engine(prec, timing=True)
+            ms, st0, st1 = timed(eng, x_dev, args.steps, args.warmup, True)
+            res[name] = {"ms": ms, "st0": st0, "st1": st1, "value": ws * n * args.steps / (ms / 1e3) / 1e6}
+            eng.close()
+    main = res["bf16x3"]
+    stages = {}
+    for name, d in main["st1"]["stages"].items():
+        d0 = main["st0"]["stages"].get(name, {"ms": 0.0, "launches": 0})
+        dl = d["launches"] - d0["launches"]
+        if dl > 0:
+            stages[name] = {"ms": d["ms"] - d0["ms"], "launches": dl, "algo_bytes": d["algo_bytes"]}
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    peaks = measured_peaks()
+    achieved = stages[dom]["algo_bytes"] / (stages[dom]["ms"] / stages[dom]["launches"] / 1e3) / 1e9
+    kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
+             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_partial", "decimate": "k_decimate"}[dom]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname + " (tensor-core form)",
+            "peak_src": peaks["src"],
+            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in stages.items()}}
+
+    # full-rate geometry on a 2^28-sample slice (larger than L2)
+    full = {}
+    fspec = synth.replace(synth.FULL_RATE, n=1 << 28, seed=synth.FULL_RATE.seed + rank)
+    xf = synth.make_stream_torch(fspec, dev)
+    for name, prec in precs.items():
+        eng = engine(prec, plan=PLAN)
+        ms, _, _ = timed(eng, xf, max(2, args.steps // 2), 1, False)
+        full[name] = ws * fspec.n * max(2, args.steps // 2) / (ms / 1e3) / 1e6
+        eng.close()
+    del xf
+
+    # end to end: pond_push from pinned host memory, results read back
+    x_pin = torch.empty(n, dtype=torch.int8, pin_memory=True)
+    x_pin.copy_(x_dev)
+    xp = x_pin.numpy()
+    eng_h = engine(pond.POND_SPLIT_BF16)
+    nbytes = {}
+
+    def step_host():
+        eng_h.reset()
+        eng_h.push(xp)
+        eng_h.flush()
+        s_, h_, _ = eng_h.profile()
+        T_, C_, _ = eng_h.timeseries()
+        nbytes["d2h"] = s_.nbytes + h_.nbytes + T_.nbytes + C_.nbytes
+
+    for _ in range(max(1, args.warmup)):
+        step_host()
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    launches = int(eng_h.stats()["kernel_launches"]) * args.steps
+    eng_h.close()
+    e2e = {"value": ws * n * args.steps / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n,
+           "d2h_bytes_per_step": nbytes["d2h"]}
+
+    line = None
+    if rank == 0:
+        # error of every output against the FP64 oracle (rank 0's stream)
+        p = pcd.make_plan(F0, BW, FS, P["dm"], P["nfft"], P["nchan"], P["nbins"], P["period"], P["t_dec"])
+        t1 = time.perf_counter()
+        r = pcd.run(p, xh, want_voltages=True)
+        oracle_s = time.perf_counter() - t1
+
+        def rel(a, b):
+            return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+        err = {}
+        for name, prec in precs.items():
+            with engine(prec, want_voltages=True) as e:
+                e.push(xh)
+                e.flush()
+                s_, h_, _ = e.profile()
+                T_, C_, _ = e.timeseries()
+                V_, _ = e.voltages()
+            err[name] = {"voltage": rel(V_, r.voltages), "profile": rel(s_, r.prof_sum), "series": rel(T_, r.ts),
+                         "hits_exact": bool(np.array_equal(h_, r.prof_hits)),
+                         "counts_exact": bool(np.array_equal(C_, r.ts_counts))}
+        cpu = None
+        if not args.no_cpu_baseline:
+            cpu = {"value": n / oracle_s / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"the whole {n}-sample stream (5 segments of 2^21), FP64 numpy on 1 host thread, "
+                             f"{oracle_s:.1f} s, voltages kept"}
+        line = {"metric": METRIC + " [precision form]", "value": main["value"], "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms"] / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f32acc",
+                "data": "synthetic", "realtime_factor": main["value"] / REALTIME_MSPS,
+                "config": {"workload": "precision form: 2^23 int8 samples, DM 3, P 0.253 s, nfft 2^21, 1 channel, "
+                                       "256-bin fold; radix-16 stages as split-BF16 DFT-matrix products on tcgen05",
+                           "samples_per_step": n, "l2": "flushed (256 MB write) before every timed step"},
+                "fp32_value": res["fp32"]["value"], "bf16x5_value": res["bf16x5"]["value"],
+                "speedup_vs_fp32": {"bf16x3": main["value"] / res["fp32"]["value"],
+                                    "bf16x5": res["bf16x5"]["value"] / res["fp32"]["value"]},
+                "full_rate_geometry_msps": full,
+                "full_rate_speedup_vs_fp32": {k: full[k] / full["fp32"] for k in ("bf16x3", "bf16x5")},
+                "error_vs_oracle": err, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "cpu_baseline": cpu, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
 
 def run_learned(args, rank):
     """Classifier on DM-time patches: training chunks and disjoint held-out
@@ -329,9 +498,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned"],
+    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned", "precision"],
                     help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks; "
-                         "learned: classifier training and evaluation beside the boxcar detector")
+                         "learned: classifier training and evaluation beside the boxcar detector; "
+                         "precision: split-BF16 tensor-core FFT stages vs the FP32 path and the oracle")
     ap.add_argument("--chunks", type=int, default=40, help="learned: 8 s training chunks")
     args = ap.parse_args()
     rank, ws, dist = dist_init()
@@ -343,6 +513,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned(args, rank)
+        return
+    if args.workload == "precision":
+        run_precision(args, rank, ws, dist)
         return
     import numpy as np
     import torch
@@ -448,7 +621,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(n), "realtime_factor": value / REALTIME_MSPS,
-                "e2e": e2e, "gpu_launches": int(st1["kernel_launches"] * segs * args.steps),
+                "e2e": e2e, "gpu_launches": int(st1["kernel_launches"]) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line), flush=True)
     eng.close()

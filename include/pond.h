@@ -59,8 +59,13 @@ extern "C" {
 #define POND_E_UNIMPLEMENTED (-9) /* option not supported by this build */
 
 /* Arithmetic of the FFT stages. */
-#define POND_FP32 0        /* FP32 butterflies (CUDA cores) */
-#define POND_SPLIT_BF16 1  /* reserved: split-BF16 tensor-core stages */
+#define POND_FP32 0           /* FP32 butterflies (CUDA cores) */
+#define POND_SPLIT_BF16 1     /* radix-16 stages as 16-point DFT-matrix products on the
+                                 tensor cores: data split into hi + lo BF16, W16 into
+                                 hi + mid + lo, three product terms (x_hi w_hi + x_hi w_mid
+                                 + x_lo w_hi) accumulated in FP32 */
+#define POND_SPLIT_BF16_5T 2  /* as POND_SPLIT_BF16 with five terms (adds x_hi w_lo and
+                                 x_lo w_mid): only the data split rounds to BF16 */
 
 typedef struct pond_s* pond_t;
 
@@ -77,7 +82,7 @@ typedef struct {
   double t_dec_s;       /* time-series resolution; rounded to whole ns; 0 -> 61.44e-6 */
   int32_t epoch_mjd_day;/* time of the first stream sample: MJD day ... */
   double epoch_mjd_sec; /* ... and seconds into that day (reported in pond_meta) */
-  int32_t precision;    /* POND_FP32 */
+  int32_t precision;    /* POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T */
   int32_t want_voltages;/* nonzero: keep dedispersed voltages for pond_voltages (tests) */
   int32_t timing;       /* nonzero: time each GPU stage with CUDA events (pond_stats) */
   int32_t device;       /* CUDA device ordinal */
@@ -129,7 +134,7 @@ typedef struct {
   int64_t n_past, n_fut;    /* overlap discarded at each segment edge, channel samples */
   int64_t seg_step;         /* real samples between segment starts */
   int32_t nfft, nchan;
-  int32_t kernel_launches;  /* kernels launched per segment */
+  int32_t kernel_launches;  /* kernels launched since the plan or the last pond_reset */
   int32_t flushed;
   double stage_ms[POND_NSTAGE];   /* accumulated GPU time per stage */
   int64_t stage_launches[POND_NSTAGE];
@@ -146,8 +151,12 @@ typedef struct {
  *   segment step S_c = M - n_past - n_fut channel samples (S = 2 nchan S_c real
  *   samples), and builds the FFT twiddle and chirp tables on the device in FP64.
  *   Supported: 2^5 <= nfft <= 2^25; nchan <= 2048 with M = nfft/(2 nchan) >= 16.
- *   Errors: POND_E_ARG, POND_E_NFFT, POND_E_NCHAN, POND_E_OOM, POND_E_CUDA,
- *   POND_E_UNIMPLEMENTED (precision other than POND_FP32).
+ *   With precision POND_SPLIT_BF16 / POND_SPLIT_BF16_5T every radix-16 stage of
+ *   the four FFT passes multiplies 16-point blocks by the DFT matrix on the
+ *   tensor cores (tcgen05, FP32 accumulators); radix-2/4/8 stages, twiddles, the
+ *   chirp (FP64 phase argument) and detection stay as in POND_FP32.
+ *   Errors: POND_E_ARG (including an unknown precision), POND_E_NFFT,
+ *   POND_E_NCHAN, POND_E_OOM, POND_E_CUDA.
  * pond_plan uses t_dec = 61.44 us, epoch 0, FP32, device 0.
  */
 int pond_plan(pond_t* out, double f0_mhz, double bw_mhz, double fs_hz, double dm,
@@ -179,11 +188,14 @@ int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream);
  * pond_flush: end of stream.  Processes the zero-padded tail and emits every
  *   output whose support lies inside the stream (g < floor(n_total/(2 nchan))
  *   - n_fut), then waits for the device.  Further pushes return POND_E_STATE.
+ *   Errors: POND_E_CUDA; POND_E_TIMEOUT when a tensor-core stage's bounded wait
+ *   for its MMAs expired (the outputs are then invalid).
  */
 int pond_flush(pond_t h);
 
 /*
  * pond_sync: wait until all work enqueued for the handle has finished.
+ *   Errors: as pond_flush.
  */
 int pond_sync(pond_t h);
 

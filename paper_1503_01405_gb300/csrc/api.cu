@@ -176,6 +176,10 @@ struct pond_s {
   double stage_ms[POND_NSTAGE] = {0};
   long long stage_launches[POND_NSTAGE] = {0};
   long long launches = 0;
+  // split-BF16 tensor-core stages: product terms (0 = FP32), W16 parts, MMA wait flag
+  int tc_terms = 0;
+  uint4* wdft = nullptr;
+  int* tc_err = nullptr;
 };
 
 namespace {
@@ -206,7 +210,8 @@ int validate(const pond_opts* o) {
     if (n != 0 && (n < 4 || (n & (n - 1)) || (n / 2) % o->nchan))
       return fail(POND_E_NFFT, "nfft_choices[%d] = %lld is not a usable power of two", i, n);
   }
-  if (o->precision != POND_FP32) return fail(POND_E_UNIMPLEMENTED, "only POND_FP32 is built");
+  if (o->precision != POND_FP32 && o->precision != POND_SPLIT_BF16 && o->precision != POND_SPLIT_BF16_5T)
+    return fail(POND_E_ARG, "precision must be POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T");
   return POND_OK;
 }
 
@@ -275,6 +280,11 @@ int build_trial(pond_t h, const pond_opts* o, Trial* t) {
 }
 
 int build_lane(pond_t h, Lane* ln) {
+  if (h->tc_terms) {
+    ln->g.tc_terms = h->tc_terms;
+    ln->g.tc_fwd = {h->wdft, h->tc_terms, h->tc_err};
+    ln->g.tc_inv = {h->wdft + TC_W_BYTES / 16, h->tc_terms, h->tc_err};
+  }
   const Geom& g = ln->g;
   CK(cudaMalloc(&ln->bufA, g.L * sizeof(float2)));
   CK(cudaMalloc(&ln->bufB, g.L * sizeof(float2)));
@@ -520,6 +530,18 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
   return POND_OK;
 }
 
+// POND_E_TIMEOUT when a bounded tensor-core MMA wait expired since the last check.
+int check_tc(pond_t h) {
+  if (!h->tc_err) return POND_OK;
+  int e = 0;
+  CK(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(cudaMemset(h->tc_err, 0, sizeof(int)));
+    return fail(POND_E_TIMEOUT, "a tensor-core MMA completion wait expired");
+  }
+  return POND_OK;
+}
+
 void destroy_all(pond_t h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
@@ -534,6 +556,8 @@ void destroy_all(pond_t h) {
   cudaFree(h->stage[0]);
   cudaFree(h->stage[1]);
   cudaFree(h->vbuf);
+  cudaFree(h->wdft);
+  cudaFree(h->tc_err);
   for (auto& se : h->ev_pending)
     for (int i = 0; i <= ST_COUNT; ++i)
       if (se.e[i]) cudaEventDestroy(se.e[i]);
@@ -754,6 +778,16 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   int sms = 0;
   CKD(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o->device));
   CKD(set_kernel_attributes());
+  if (o->precision != POND_FP32) {
+    h->tc_terms = o->precision == POND_SPLIT_BF16_5T ? 5 : 3;
+    CKD(set_kernel_attributes_tc());
+    std::vector<uint16_t> w(2 * TC_W_BYTES / 2);
+    build_w16_parts(w.data());
+    CKD(cudaMalloc(&h->wdft, 2 * TC_W_BYTES));
+    CKD(cudaMalloc(&h->tc_err, sizeof(int)));
+    CKD(cudaMemcpy(h->wdft, w.data(), 2 * TC_W_BYTES, cudaMemcpyHostToDevice));
+    CKD(cudaMemset(h->tc_err, 0, sizeof(int)));
+  }
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
@@ -928,14 +962,14 @@ int pond_flush(pond_t h) {
   h->flushed = true;
   if (h->ts_first >= 0) h->ts_complete = h->ts_hi;
   CK(cudaStreamSynchronize(h->st));
-  return POND_OK;
+  return check_tc(h);
 }
 
 int pond_sync(pond_t h) {
   if (!h) return fail(POND_E_ARG, "null handle");
   CK(cudaSetDevice(h->device));
   CK(cudaStreamSynchronize(h->st));
-  return POND_OK;
+  return check_tc(h);
 }
 
 int pond_reset(pond_t h) {

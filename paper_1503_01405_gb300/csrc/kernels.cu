@@ -1,7 +1,8 @@
 // Segment kernels of the coherent-dedispersion path (PONDER Sec. 3.7).
 //
 // One overlap-save segment of N real int8 samples goes through four FFT passes
-// over a spectrum of L = N/2 complex bins, then fold and decimation:
+// over a spectrum of L = N/2 complex bins (passes.cuh; FP32 instantiations
+// here), then fold and decimation:
 //
 //  F1 k_fwd_cols   : unpack z[n] = x[2n] + i x[2n+1]; length-R2 FFTs down the
 //                    R1 columns n1 of z viewed as [R2][R1]; multiply by
@@ -22,8 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fft_block.cuh"
-#include "pond_internal.h"
+#include "passes.cuh"
 
 namespace pond {
 
@@ -85,19 +85,6 @@ __global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, int clog,
   anc[a] = r;
 }
 
-// exp(-2 pi i phi(k)) from the anchor table (phase error < 1e-7 cycles).
-__device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ anc, int clog, unsigned k) {
-  const ChirpAnchor a = anc[k >> clog];
-  const int d = (int)(k & ((1u << clog) - 1)) - (int)((1u << clog) >> 1);
-  const unsigned u = a.p0 + a.p1 * (unsigned)d;           // mod 2^32: phase mod 1 cycle
-  const float df = (float)d;
-  float r = (float)(int)u * 2.3283064365386963e-10f;      // 2^-32
-  r += fmaf(a.p3, df, a.p2) * (df * df);
-  float s, c;
-  sincospif(2.0f * r, &s, &c);
-  return make_float2(c, -s);
-}
-
 // ---------------------------------------------------------------------------
 // Two-level twiddle tables: w^e = hi[e >> 12] * lo[e & 4095], w = exp(+-2 pi i / n)
 // ---------------------------------------------------------------------------
@@ -114,279 +101,6 @@ __global__ void k_make_tw2(float2* lo, float2* hi, int logn, int sign) {
   if (i < nhi) {
     sincospi(inv * (double)((long long)i << TW2_LOG), &s, &c);
     hi[i] = make_float2((float)c, (float)s);
-  }
-}
-
-__device__ __forceinline__ float2 tw2(const Tw2& t, unsigned e) {
-  return cmul(__ldg(t.hi + (e >> TW2_LOG)), __ldg(t.lo + (e & (TW2_LO - 1))));
-}
-
-constexpr int EPT = TILE / NT;   // tile elements per thread
-
-// ---------------------------------------------------------------------------
-// F1: unpack + column FFTs of the forward transform
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
-  if (r < in.a_len) return (float)in.a[r];
-  r -= in.a_len;
-  if (r < in.b_len) return (float)in.b[r];
-  return 0.f;
-}
-
-// z viewed as [R2][R1] (z[n1 + R1 n2]); a CTA transforms nl adjacent columns n1
-// and stores them in place, scaled by exp(-2 pi i n1 k2 / L).
-template <int R2>
-__global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1, Tw2 twL,
-                                                    const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(R2);
-  constexpr int LSTR = line_stride(R2);
-  const int R1 = 1 << logR1;
-  const int nl = min(TILE / R2, R1);
-  const int lognl = __ffs(nl) - 1;
-  const int tot = nl * R2;
-  load_twiddles<R2>(stw, tw);
-  const int tile = blockIdx.x;
-  const int n1_0 = tile * nl;
-  if (in.vec8) {
-    // 8-byte loads: 4 consecutive columns of one row per load (runs 8-aligned)
-    constexpr int CPT = EPT / 4;
-    const int logq = lognl - 2;            // chunks per row = nl / 4
-    uint2 w[CPT];
-#pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-      const int c = threadIdx.x + u * NT;
-      if (c < tot / 4) {
-        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
-        const long long r = 2 * ((long long)(n1_0 + b0) + ((long long)n2 << logR1));
-        if (r < in.a_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.a + r));
-        else if (r - in.a_len < in.b_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.b + (r - in.a_len)));
-        else w[u] = make_uint2(0u, 0u);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < CPT; ++u) {
-      const int c = threadIdx.x + u * NT;
-      if (c < tot / 4) {
-        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
-        const unsigned lo = w[u].x, hi = w[u].y;
-        sm[pidx(b0 + 0, n2, LSTR)] = make_float2((float)(signed char)(lo & 0xff), (float)(signed char)((lo >> 8) & 0xff));
-        sm[pidx(b0 + 1, n2, LSTR)] = make_float2((float)(signed char)((lo >> 16) & 0xff), (float)(signed char)(lo >> 24));
-        sm[pidx(b0 + 2, n2, LSTR)] = make_float2((float)(signed char)(hi & 0xff), (float)(signed char)((hi >> 8) & 0xff));
-        sm[pidx(b0 + 3, n2, LSTR)] = make_float2((float)(signed char)((hi >> 16) & 0xff), (float)(signed char)(hi >> 24));
-      }
-    }
-  } else {
-    float2 r[EPT];
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const int idx = threadIdx.x + u * NT;
-      if (idx < tot) {
-        const int n2 = idx >> lognl, b = idx & (nl - 1);
-        const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
-        r[u] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const int idx = threadIdx.x + u * NT;
-      if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
-    }
-  }
-  __syncthreads();
-  block_fft<R2, false>(sm, nl, stw);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int k2 = idx >> lognl, b = idx & (nl - 1);
-    const unsigned n1 = (unsigned)(n1_0 + b);
-    out[(size_t)n1 + ((size_t)k2 << logR1)] = cmul(sm[pidx(b, k2, LSTR)], tw2(twL, n1 * (unsigned)k2));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// F2: row FFTs + real-input split + dedispersion chirp
-// ---------------------------------------------------------------------------
-
-// Row k2 of the column-transformed z holds, after a length-R1 FFT, Z[k2 + R2 k1].
-// Rows k2 and R2-k2 share a CTA (row 0 and row R2/2 pair with themselves) so that
-// X[k] can be formed from Z[k] and Z[L-k]; the chirped spectrum Y[k2 + R2 k1] is
-// stored at row k2, column k1 of the output (the same place the row was read).
-template <int R1>
-__global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logR2, int logL, Tw2 tw2L,
-                                                    const ChirpAnchor* __restrict__ anc, int clog, int apply_chirp,
-                                                    const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(R1);
-  constexpr int LSTR = line_stride(R1);
-  constexpr int LOGR1 = ilog2c(R1);
-  const int R2 = 1 << logR2;
-  const int nl = min(TILE / R1, R2);   // 2 * pairs
-  const int np = nl >> 1;
-  const int tot = nl * R1;
-  load_twiddles<R1>(stw, tw);
-  const int tile = blockIdx.x;
-  const int q0 = tile * np;
-  auto line_of = [&](int slot) -> int {
-    if (slot < np) return q0 + slot;
-    const int t = slot - np;
-    if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
-    return R2 - (q0 + t);
-  };
-  float2 r[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) r[u] = in[((size_t)line_of(idx >> LOGR1) << LOGR1) + (idx & (R1 - 1))];
-  }
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) sm[pidx(idx >> LOGR1, idx & (R1 - 1), LSTR)] = r[u];
-  }
-  __syncthreads();
-  block_fft<R1, false>(sm, nl, stw);
-  const unsigned lmask = (1u << logL) - 1;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
-    const int line = line_of(slot);
-    const unsigned k = (unsigned)line + ((unsigned)k1 << logR2);
-    const unsigned kp = (0u - k) & lmask;
-    const int linep = (int)(kp & (unsigned)(R2 - 1));
-    const int k1p = (int)(kp >> logR2);
-    const int slotp = (linep == line) ? slot : (slot < np ? slot + np : slot - np);
-    const float2 A = sm[pidx(slot, k1, LSTR)];
-    const float2 B = cconj(sm[pidx(slotp, k1p, LSTR)]);
-    const float2 E = cscale(cadd(A, B), 0.5f);
-    const float2 O = cscale(csub(A, B), 0.5f);
-    float2 X = cadd(E, rot90<false>(cmul(tw2(tw2L, k), O)));   // E - i exp(-i pi k/L) O
-    if (apply_chirp) X = cmul(X, chirp_factor(anc, clog, k));
-    out[((size_t)line << LOGR1) + k1] = X;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// I1: per-sub-channel inverse column FFTs
-// ---------------------------------------------------------------------------
-
-// Line (c, j1) holds Y[c M + j1 + Q1 j2], j2 < Q2, read from the row layout
-// written by F2 (bin k at (k >> logR2) + (k mod R2) R1; with Q1 <= R2 the
-// values j2 = j2lo + 2^s j2hi, s = logR2 - logQ1, lie in runs of M/R2
-// consecutive addresses in j2hi).  The inverse column transform, scaled by
-// exp(+2 pi i j1 m2 / M), is stored in natural order c M + j1 + Q1 m2.
-template <int Q2>
-__global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
-                                                    const ChirpAnchor* __restrict__ anc, int clog,
-                                                    const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(Q2);
-  constexpr int LSTR = line_stride(Q2);
-  constexpr int LOGQ2 = ilog2c(Q2);
-  const int Q1 = 1 << logQ1;
-  const int nl = min(TILE / Q2, nchan * Q1);
-  const int lognl = __ffs(nl) - 1;
-  const int tot = nl * Q2;
-  load_twiddles<Q2>(stw, tw);
-  const int tile = blockIdx.x;
-  const int l0 = tile * nl;
-  const int s = logR2 - logQ1;                 // j2 = j2lo + 2^s j2hi
-  const int logrun = LOGQ2 - s;                // run length M / R2 (>= 1)
-  float2 r[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int j2hi = idx & ((1 << logrun) - 1);
-      const int rest = idx >> logrun;
-      const int j2lo = rest & ((1 << s) - 1);
-      const int l = l0 + (rest >> s);
-      const int c = l >> logQ1, j1 = l & (Q1 - 1);
-      const size_t k1 = ((size_t)c << (logM - logR2)) + j2hi;
-      const size_t k2 = (size_t)j1 + ((size_t)j2lo << logQ1);
-      r[u] = in[k1 + (k2 << logR1)];
-      if (anc) r[u] = cmul(r[u], chirp_factor(anc, clog, (unsigned)(k2 + (k1 << logR2))));
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int j2hi = idx & ((1 << logrun) - 1);
-      const int rest = idx >> logrun;
-      const int j2lo = rest & ((1 << s) - 1);
-      sm[pidx(rest >> s, j2lo + (j2hi << s), LSTR)] = r[u];
-    }
-  }
-  __syncthreads();
-  block_fft<Q2, true>(sm, nl, stw);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int m2 = idx >> lognl, b = idx & (nl - 1);
-    const int l = l0 + b;
-    const unsigned j1 = (unsigned)(l & (Q1 - 1));
-    const size_t addr = ((size_t)(l >> logQ1) << logM) + j1 + ((size_t)m2 << logQ1);
-    out[addr] = cmul(sm[pidx(b, m2, LSTR)], tw2(twM, j1 * (unsigned)m2));
-  }
-}
-
-// ---------------------------------------------------------------------------
-// I2: inverse row FFTs, discard, detect, sum over sub-channels
-// ---------------------------------------------------------------------------
-
-template <int Q1>
-__global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf, float* __restrict__ P,
-                                                    float2* __restrict__ vout, long long vstride,
-                                                    long long vofs, int logQ2, int logM, int nchan,
-                                                    int m_lo, int m_hi, float scale,
-                                                    const float2* __restrict__ tw) {
-  extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(Q1);
-  constexpr int LSTR = line_stride(Q1);
-  constexpr int LOGQ1 = ilog2c(Q1);
-  const int Q2 = 1 << logQ2;
-  const int b2 = min(TILE / (Q1 * nchan), Q2);
-  const int logb2 = __ffs(b2) - 1;
-  const int nl = nchan * b2;
-  const int tot = nl * Q1;
-  load_twiddles<Q1>(stw, tw);
-  const int tile = blockIdx.x;
-  const int m2_0 = tile * b2;
-  float2 r[EPT];
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
-      const int c = slot >> logb2, bb = slot & (b2 - 1);
-      r[u] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) sm[pidx(idx >> LOGQ1, idx & (Q1 - 1), LSTR)] = r[u];
-  }
-  __syncthreads();
-  block_fft<Q1, true>(sm, nl, stw);
-  for (int idx = threadIdx.x; idx < b2 * Q1; idx += NT) {
-    const int m1 = idx >> logb2, bb = idx & (b2 - 1);
-    const int m = m2_0 + bb + (m1 << logQ2);
-    if (m < m_lo || m >= m_hi) continue;
-    float p = 0.f;
-    for (int c = 0; c < nchan; ++c) {
-      const float2 v = cscale(sm[pidx((c << logb2) + bb, m1, LSTR)], scale);
-      p = fmaf(v.x, v.x, p);
-      p = fmaf(v.y, v.y, p);
-      if (vout) vout[(size_t)c * vstride + vofs + (m - m_lo)] = v;
-    }
-    P[m - m_lo] = p;
   }
 }
 
@@ -534,20 +248,6 @@ __global__ void k_decimate(const float* __restrict__ P, long long n, long long g
 // Host launchers
 // ---------------------------------------------------------------------------
 
-// Stage twiddle tables + padded tile (nl lines of line_stride(R)).
-template <int R>
-static size_t smem_bytes(int nl) {
-  return ((size_t)stage_table_size(R) + (size_t)nl * line_stride(R)) * sizeof(float2);
-}
-
-// Largest stage tables + padded tile over the line lengths 4..4096.
-static size_t max_tile_smem_bytes() {
-  size_t m = 0;
-  for (int R = 4; R <= 4096; R *= 2)
-    m = std::max(m, ((size_t)stage_table_size(R) + (size_t)(TILE / R) * (R + R / 16 + 1)) * sizeof(float2));
-  return m;
-}
-
 cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st) {
   const int n = stage_table_size(R);
   if (n > 0) k_make_stage_tw<<<(n + 255) / 256, 256, 0, st>>>(out, R);
@@ -555,26 +255,6 @@ cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st) {
 }
 
 int stage_tw_entries(int R) { return stage_table_size(R); }
-
-// One CTA per tile.
-static unsigned grid_for(int tiles, int) { return (unsigned)tiles; }
-
-#define POND_FOR_R(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
-
-cudaError_t set_kernel_attributes() {
-  const int max_smem = (int)max_tile_smem_bytes();
-  cudaError_t e = cudaSuccess;
-#define SET_ATTR(R)                                                                                   \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  POND_FOR_R(SET_ATTR)
-#undef SET_ATTR
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
-  return e;
-}
 
 cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st) {
   const long long nhi = logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1;
@@ -589,62 +269,34 @@ cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du,
   return cudaGetLastError();
 }
 
+cudaError_t set_kernel_attributes() {
+  cudaError_t e = set_attributes_t<false>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
+  return e;
+}
+
+// The pass launchers pick the FP32 or the tensor-core instantiation.
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
-  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
-  const int nl = std::min(TILE / R2, R1);
-  const unsigned grid = grid_for(R1 / nl, g.sms);
-  switch (R2) {
-#define CASE(R) case R: k_fwd_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR1, twL, tw); break;
-    POND_FOR_R(CASE)
-#undef CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return g.tc_terms ? launch_fwd_cols_tc(g, in, out, twL, tw, st) : launch_fwd_cols_t<false>(g, in, out, twL, tw, st);
 }
 
 cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
                             int apply_chirp, const float2* tw, cudaStream_t st) {
-  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
-  const int nl = std::min(TILE / R1, R2);
-  const unsigned grid = grid_for(R2 / nl, g.sms);
-  switch (R1) {
-#define CASE(R) case R: k_fwd_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logR2, g.logL, tw2L, anc, clog, apply_chirp, tw); break;
-    POND_FOR_R(CASE)
-#undef CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return g.tc_terms ? launch_fwd_rows_tc(g, in, out, tw2L, anc, clog, apply_chirp, tw, st)
+                    : launch_fwd_rows_t<false>(g, in, out, tw2L, anc, clog, apply_chirp, tw, st);
 }
 
 cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
                             int clog, const float2* tw, cudaStream_t st) {
-  const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
-  const int lines = g.nchan * Q1;
-  const int nl = std::min(TILE / Q2, lines);
-  const unsigned grid = grid_for(lines / nl, g.sms);
-  switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R><<<grid, NT, smem_bytes<R>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, anc, clog, tw); break;
-    POND_FOR_R(CASE)
-#undef CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return g.tc_terms ? launch_inv_cols_tc(g, in, out, twM, anc, clog, tw, st)
+                    : launch_inv_cols_t<false>(g, in, out, twM, anc, clog, tw, st);
 }
 
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
                             long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st) {
-  const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
-  const int b2 = std::min(TILE / (Q1 * g.nchan), Q2);
-  const int nl = g.nchan * b2;
-  const unsigned grid = grid_for(Q2 / b2, g.sms);
-  const float scale = 1.0f / (float)(1u << g.logM);
-  switch (Q1) {
-#define CASE(R) case R: k_inv_rows<R><<<grid, NT, smem_bytes<R>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, m_lo, m_hi, scale, tw); break;
-    POND_FOR_R(CASE)
-#undef CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  return g.tc_terms ? launch_inv_rows_tc(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw, st)
+                    : launch_inv_rows_t<false>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw, st);
 }
 
 size_t fold_smem_bytes(int nbins) {

@@ -39,6 +39,17 @@ struct SegIn {
   int vec8;   // both runs 8-byte aligned with a_len % 8 == 0: F1 may load 8 bytes at a time
 };
 
+constexpr int TC_W_BYTES = 3 * 32 * 32 * 2;   // W16 hi, mid, lo parts of one direction
+
+// Tensor-core stage arguments: the W16 parts of one transform direction
+// (hi, mid, lo BF16 in the operand layout, 6 KiB), the product terms (3 or 5)
+// and the plan's error flag (set when a bounded MMA wait expires).
+struct TcArgs {
+  const uint4* w;
+  int terms;
+  int* err;
+};
+
 // Geometry of a plan: segment and pass decomposition.
 struct Geom {
   long long N, L, M;     // real samples per segment, spectrum bins kept, samples per sub-channel
@@ -48,9 +59,15 @@ struct Geom {
   int logQ1, logQ2;      // inverse: M = Q1 * Q2 (I2 rows of Q1, I1 columns of Q2)
   long long n_past, n_fut, S_c, S;
   int sms;               // streaming multiprocessors of the device
+  int tc_terms = 0;      // 0: FP32 stages; 3 or 5: split-BF16 tensor-core radix-16 stages
+  TcArgs tc_fwd{}, tc_inv{};
 };
 
 cudaError_t set_kernel_attributes();
+cudaError_t set_kernel_attributes_tc();
+// W16 parts for the tensor-core stages, host-built: [fwd, inv][hi, mid, lo] in
+// the K-major operand layout (2 x 6 KiB).
+void build_w16_parts(uint16_t* out);
 int run_boxcar(const float* d_series, int ndm, long long n, long long stride, double thr, pond_cand* host_out,
                size_t cap, size_t* n_found, cudaStream_t st);
 // Record msg as the calling thread's last error (pond_last_error) and return code.

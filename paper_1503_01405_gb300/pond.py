@@ -25,6 +25,7 @@ POND_E_TIMEOUT = -8
 POND_E_UNIMPLEMENTED = -9
 POND_FP32 = 0
 POND_SPLIT_BF16 = 1
+POND_SPLIT_BF16_5T = 2
 POND_NSTAGE = 8
 POND_NOALLOC_MAX_NBINS = 1024
 

@@ -74,8 +74,8 @@ def test_engine_limits():
         pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 5000, 0.1)
     assert e.value.name == "ARG"
     with pytest.raises(pond.PondError) as e:
-        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1, precision=pond.POND_SPLIT_BF16)
-    assert e.value.name == "UNIMPLEMENTED"
+        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1, precision=7)
+    assert e.value.name == "ARG"
 
 
 def test_null_handle_and_pointers():
