@@ -260,9 +260,15 @@ int anchor_log(const pond_opts* o, long long nfft, double dm) {
   const double du = o->fs_hz / (double)nfft * 1e-6;
   const double half = std::fabs(o->bw_mhz) / 2.0;
   const double alpha = K_DM * 1e6 * dm / (o->f0_mhz * o->f0_mhz);
+  // |c''''|/24 and |c'''|/6 at their band maximum (f0 + f = f0 - |bw|/2)
   const double c4 = alpha * o->f0_mhz * o->f0_mhz / std::pow(o->f0_mhz - half, 5);
+  const double c3 = alpha * o->f0_mhz * o->f0_mhz / std::pow(o->f0_mhz - half, 4);
   int clog = CHIRP_LOG_MAX;
-  while (clog > 0 && c4 * std::pow(du * (double)(1ll << (clog - 1)), 4) > 1e-9) --clog;
+  // dropped quartic term <= 1e-9 cycles; the FP32 cubic term <= 1e-2 cycles
+  // (so its rounding stays < 1e-9 cycles)
+  while (clog > 0 && (c4 * std::pow(du * (double)(1ll << (clog - 1)), 4) > 1e-9 ||
+                      c3 * std::pow(du * (double)(1ll << (clog - 1)), 3) > 1e-2))
+    --clog;
   return clog;
 }
 
@@ -459,17 +465,16 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   }
   h->ev_cur = SegEvents{};
   RC(record(h, 0));
-  CK(launch_fwd_cols(g, in, ln.bufA, ln.twL, ln.stwR2, h->st));
+  CK(launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st));
   RC(record(h, 1 + ST_F1));
-  const Trial* t0 = &h->trials[ln.trials[0]];
-  // a single-DM lane chirps in F2; a batched lane chirps per trial in I1
-  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw2L, t0->anc, t0->clog, h->multi ? 0 : 1, ln.stwR1, h->st));
+  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.twL, ln.tw2L, ln.stwR1, h->st));
   RC(record(h, 1 + ST_F2));
   h->launches += 2;
   for (size_t q = 0; q < ln.trials.size(); ++q) {
     const int d = ln.trials[q];
     const Trial& t = h->trials[d];
-    CK(launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, h->multi ? t.anc : nullptr, t.clog, ln.stwQ2, h->st));
+    // every trial's chirp is applied as I1 loads the shared forward spectrum
+    CK(launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, t.anc, t.clog, ln.stwQ2, h->st));
     if (q == 0) RC(record(h, 1 + ST_I1));
     CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.stwQ1, h->st));
     if (q == 0) RC(record(h, 1 + ST_I2));
@@ -630,8 +635,8 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
   SegIn in{ln.carry[0], g.N, nullptr, 0, 0};
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {      // first pass warms up
     if (it == 1) ce = cudaEventRecord(e[0], h->st);
-    if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA, ln.twL, ln.stwR2, h->st);
-    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw2L, anc, clog, 0, ln.stwR1, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.twL, ln.tw2L, ln.stwR1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[1], h->st);
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {

@@ -53,11 +53,20 @@ __global__ void k_make_stage_tw(float2* out, int R) {
 
 // Anchor a covers the 2^clog bins k = 2^clog a + d (d < 2^clog); it holds the
 // Taylor coefficients of the dedispersion phase phi(k) = sgn * c(f_k) (cycles)
-// about k_a = 2^clog a + 2^(clog-1): phi(k_a) and phi'(k_a) reduced mod 1 in
-// Q0.32 fixed point, phi''/2 and phi'''/6 in FP32.  c(f) = alpha f^2 / (f0 + f)
+// about k_a = 2^clog a + 2^(clog-1): phi(k_a) mod 1 in Q0.32, phi'(k_a) and
+// phi''(k_a)/2 mod 1 in Q0.64 (so the polynomial up to d^2 is exact mod 1 in
+// integer arithmetic), phi'''(k_a)/6 in FP32.  c(f) = alpha f^2 / (f0 + f)
 // with alpha = K 1e6 DM / f0^2 (Eq. 4), f = k du - |bw|/2 (upper sideband) or
-// |bw|/2 - k du (inverted).  The planner picks clog so that the dropped quartic
-// term stays below 1e-9 cycles.
+// |bw|/2 - k du (inverted).  The planner picks clog so that the dropped
+// quartic term stays below 1e-9 cycles.
+__device__ __forceinline__ unsigned long long frac_q064(double x) {
+  const double fr = x - floor(x);                 // in [0, 1), exact in FP64
+  const double t = fr * 4294967296.0;             // exact scaling
+  const double h = floor(t);
+  const long long l = llrint((t - h) * 4294967296.0);
+  return ((unsigned long long)h << 32) + (unsigned long long)l;   // a carry from l = 2^32 wraps mod 2^64
+}
+
 __global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                                      double f0, double alpha, int sgn) {
   const long long a = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,12 +85,12 @@ __global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, int clog,
   const double phi2 = sgn * du * du * d2 * 0.5;
   const double phi3 = du * du * du * d3 / 6.0;
   const double fr0 = phi0 - floor(phi0);
-  const double fr1 = phi1 - floor(phi1);
   ChirpAnchor r;
   r.p0 = (unsigned)((unsigned long long)llrint(fr0 * 4294967296.0) & 0xffffffffull);
-  r.p1 = (unsigned)((unsigned long long)llrint(fr1 * 4294967296.0) & 0xffffffffull);
-  r.p2 = (float)phi2;
+  r.p1 = frac_q064(phi1);
+  r.p2 = frac_q064(phi2);
   r.p3 = (float)phi3;
+  r.pad[0] = r.pad[1] = 0u;
   anc[a] = r;
 }
 
@@ -109,6 +118,7 @@ __global__ void k_make_tw2(float2* lo, float2* hi, int logn, int sign) {
 // ---------------------------------------------------------------------------
 
 constexpr int FOLD_WARPS = 4;
+constexpr int FOLD_U = 4;        // 32-sample groups in flight per warp
 
 // bin(g) = min(floor(frac(g * inc) * nbins), nbins - 1), FP64, correctly rounded.
 __device__ __forceinline__ int fold_bin(long long g, double inc, int nbins) {
@@ -137,47 +147,59 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
   double* myh = hsum + w * nbins;
   int* myc = hcnt + w * nbins;
   float* mybuf = pbuf + w * 32;
-  for (long long base = c0 + w * 32; base < c1; base += FOLD_WARPS * 32) {
-    const long long i = base + lane;
-    const bool ok = i < c1;
-    int b = -1;
-    float p = 0.f;
-    if (ok) {
-      b = fold_bin(g0 + i, inc, nbins);
-      p = P[i];
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, b);
-    const int first = __ffs(peers) - 1;
-    const int last = 31 - __clz(peers);
-    const unsigned span = (last == 31 ? 0xffffffffu : ((1u << (last + 1)) - 1u)) & ~((1u << first) - 1u);
-    if (__all_sync(0xffffffffu, peers == span)) {
-      // every bin's lanes are contiguous: segmented scan in a fixed tree order
-      float x = p;
+  // FOLD_U groups of 32 samples per warp and iteration: their loads and FP64
+  // bin computations are all in flight before the groups are scanned in order
+  for (long long base = c0 + (long long)w * 32 * FOLD_U; base < c1; base += FOLD_WARPS * 32 * FOLD_U) {
+    float pv[FOLD_U];
+    int bv[FOLD_U];
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane - d >= first) x += y;
-      }
-      if (ok && lane == last) {
-        myh[b] += (double)x;
-        myc[b] += last - first + 1;
-      }
-    } else {
-      // a period shorter than a warp: the group leader sums its lanes in order
-      mybuf[lane] = p;
-      __syncwarp();
-      if (ok && lane == first) {
-        float sum = 0.f;
-        unsigned m = peers;
-        while (m) {
-          sum += mybuf[__ffs(m) - 1];
-          m &= m - 1;
-        }
-        myh[b] += (double)sum;
-        myc[b] += __popc(peers);
+    for (int u = 0; u < FOLD_U; ++u) {
+      const long long i = base + u * 32 + lane;
+      pv[u] = 0.f;
+      bv[u] = -1;
+      if (i < c1) {
+        pv[u] = __ldg(P + i);
+        bv[u] = fold_bin(g0 + i, inc, nbins);
       }
     }
-    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < FOLD_U; ++u) {
+      const int b = bv[u];
+      const bool ok = b >= 0;
+      const float p = pv[u];
+      const unsigned peers = __match_any_sync(0xffffffffu, b);
+      const int first = __ffs(peers) - 1;
+      const int last = 31 - __clz(peers);
+      const unsigned span = (last == 31 ? 0xffffffffu : ((1u << (last + 1)) - 1u)) & ~((1u << first) - 1u);
+      if (__all_sync(0xffffffffu, peers == span)) {
+        // every bin's lanes are contiguous: segmented scan in a fixed tree order
+        float x = p;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const float y = __shfl_up_sync(0xffffffffu, x, d);
+          if (lane - d >= first) x += y;
+        }
+        if (ok && lane == last) {
+          myh[b] += (double)x;
+          myc[b] += last - first + 1;
+        }
+      } else {
+        // a period shorter than a warp: the group leader sums its lanes in order
+        mybuf[lane] = p;
+        __syncwarp();
+        if (ok && lane == first) {
+          float sum = 0.f;
+          unsigned m = peers;
+          while (m) {
+            sum += mybuf[__ffs(m) - 1];
+            m &= m - 1;
+          }
+          myh[b] += (double)sum;
+          myc[b] += __popc(peers);
+        }
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
@@ -193,27 +215,41 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
   }
 }
 
-// One warp per bin: lanes take every 32nd part, then a fixed xor-tree sum.
-__global__ void k_fold_merge(const double* __restrict__ psum, const int* __restrict__ phits, int nparts,
-                             int nbins, double* __restrict__ prof_sum, long long* __restrict__ prof_hits) {
-  const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (b >= nbins) return;
+// A CTA merges 32 consecutive bins: warp y sums parts y, y + 8, y + 16, ... in
+// order (lanes read 32 consecutive bins of a part: coalesced), then lane x of
+// warp 0 adds the eight warp sums of bin x in a fixed order.
+constexpr int MERGE_WARPS = 8;
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) k_fold_merge(const double* __restrict__ psum,
+                                                                 const int* __restrict__ phits, int nparts,
+                                                                 int nbins, double* __restrict__ prof_sum,
+                                                                 long long* __restrict__ prof_hits) {
+  __shared__ double ss[MERGE_WARPS][32];
+  __shared__ long long sh[MERGE_WARPS][32];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int b = blockIdx.x * 32 + x;
   double s = 0.0;
   long long h = 0;
+  if (b < nbins) {
 #pragma unroll 4
-  for (int k = lane; k < nparts; k += 32) {
-    s += psum[(size_t)k * nbins + b];
-    h += phits[(size_t)k * nbins + b];
+    for (int k = y; k < nparts; k += MERGE_WARPS) {
+      s += __ldg(psum + (size_t)k * nbins + b);
+      h += __ldg(phits + (size_t)k * nbins + b);
+    }
   }
+  ss[y][x] = s;
+  sh[y][x] = h;
+  __syncthreads();
+  if (y == 0 && b < nbins) {
+    double t = 0.0;
+    long long c = 0;
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, off);
-    h += __shfl_xor_sync(0xffffffffu, h, off);
-  }
-  if (lane == 0) {
-    prof_sum[b] += s;
-    prof_hits[b] += h;
+    for (int w = 0; w < MERGE_WARPS; ++w) {
+      t += ss[w][x];
+      c += sh[w][x];
+    }
+    prof_sum[b] += t;
+    prof_hits[b] += c;
   }
 }
 
@@ -223,6 +259,9 @@ __global__ void k_fold_merge(const double* __restrict__ psum, const int* __restr
 
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
 
+// One warp per series sample j (spans of 64 or more channel samples): four
+// independent partial sums keep four loads in flight per lane, combined in a
+// fixed order, then a fixed xor-tree over the lanes.
 __global__ void k_decimate(const float* __restrict__ P, long long n, long long g0, long long num,
                            long long den, long long j_lo, long long nj, float* __restrict__ T,
                            int* __restrict__ C, long long ring) {
@@ -233,15 +272,43 @@ __global__ void k_decimate(const float* __restrict__ P, long long n, long long g
   long long ga = ceil_div_ll(j * num, den), gb = ceil_div_ll((j + 1) * num, den);
   ga = max(ga, g0);
   gb = min(gb, g0 + n);
-  float s = 0.f;
-  for (long long g = ga + lane; g < gb; g += 32) s += P[g - g0];
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  long long g = ga + lane;
+  for (; g + 96 < gb; g += 128) {
+    s0 += __ldg(P + (g - g0));
+    s1 += __ldg(P + (g + 32 - g0));
+    s2 += __ldg(P + (g + 64 - g0));
+    s3 += __ldg(P + (g + 96 - g0));
+  }
+  if (g < gb) s0 += __ldg(P + (g - g0));
+  if (g + 32 < gb) s1 += __ldg(P + (g + 32 - g0));
+  if (g + 64 < gb) s2 += __ldg(P + (g + 64 - g0));
+  float s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) {
     const long long slot = j % ring;
     T[slot] += s;
-    C[slot] += (int)(gb - ga);
+    C[slot] += (int)max(gb - ga, 0ll);
   }
+}
+
+// One thread per series sample j (spans shorter than 64 channel samples): the
+// span is summed in index order; neighbouring threads read neighbouring spans.
+__global__ void k_decimate_short(const float* __restrict__ P, long long n, long long g0, long long num,
+                                 long long den, long long j_lo, long long nj, float* __restrict__ T,
+                                 int* __restrict__ C, long long ring) {
+  const long long jj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (jj >= nj) return;
+  const long long j = j_lo + jj;
+  long long ga = ceil_div_ll(j * num, den), gb = ceil_div_ll((j + 1) * num, den);
+  ga = max(ga, g0);
+  gb = min(gb, g0 + n);
+  float s = 0.f;
+  for (long long g = ga; g < gb; ++g) s += __ldg(P + (g - g0));
+  const long long slot = j % ring;
+  T[slot] += s;
+  C[slot] += (int)max(gb - ga, 0ll);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,14 +344,14 @@ cudaError_t set_kernel_attributes() {
 }
 
 // The pass launchers pick the FP32 or the tensor-core instantiation.
-cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
-  return g.tc_terms ? launch_fwd_cols_tc(g, in, out, twL, tw, st) : launch_fwd_cols_t<false>(g, in, out, twL, tw, st);
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
+  return g.tc_terms ? launch_fwd_cols_tc(g, in, out, tw, st) : launch_fwd_cols_t<false>(g, in, out, tw, st);
 }
 
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
-                            int apply_chirp, const float2* tw, cudaStream_t st) {
-  return g.tc_terms ? launch_fwd_rows_tc(g, in, out, tw2L, anc, clog, apply_chirp, tw, st)
-                    : launch_fwd_rows_t<false>(g, in, out, tw2L, anc, clog, apply_chirp, tw, st);
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+                            cudaStream_t st) {
+  return g.tc_terms ? launch_fwd_rows_tc(g, in, out, twL, tw2L, tw, st)
+                    : launch_fwd_rows_t<false>(g, in, out, twL, tw2L, tw, st);
 }
 
 cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
@@ -316,15 +383,19 @@ cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, i
   long long chunk;
   const int parts = fold_parts(n, &chunk);
   k_fold_partial<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, chunk, psum, phits);
-  k_fold_merge<<<(nbins * 32 + 255) / 256, 256, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
+  k_fold_merge<<<(nbins + 31) / 32, MERGE_WARPS * 32, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decimate(const float* P, long long n, long long g0, long long num, long long den,
                             long long j_lo, long long nj, float* T, int* C, long long ring, cudaStream_t st) {
   if (n <= 0 || nj <= 0) return cudaSuccess;
-  const long long threads = nj * 32;
-  k_decimate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, n, g0, num, den, j_lo, nj, T, C, ring);
+  if (num < 64 * den) {   // fewer than 64 channel samples per series sample
+    k_decimate_short<<<(unsigned)((nj + 255) / 256), 256, 0, st>>>(P, n, g0, num, den, j_lo, nj, T, C, ring);
+  } else {
+    const long long threads = nj * 32;
+    k_decimate<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, n, g0, num, den, j_lo, nj, T, C, ring);
+  }
   return cudaGetLastError();
 }
 

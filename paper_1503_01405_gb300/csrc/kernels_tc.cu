@@ -9,13 +9,13 @@ namespace pond {
 
 cudaError_t set_kernel_attributes_tc() { return set_attributes_t<true>(); }
 
-cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
-  return launch_fwd_cols_t<true>(g, in, out, twL, tw, st);
+cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
+  return launch_fwd_cols_t<true>(g, in, out, tw, st);
 }
 
-cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc,
-                               int clog, int apply_chirp, const float2* tw, cudaStream_t st) {
-  return launch_fwd_rows_t<true>(g, in, out, tw2L, anc, clog, apply_chirp, tw, st);
+cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+                               cudaStream_t st) {
+  return launch_fwd_rows_t<true>(g, in, out, twL, tw2L, tw, st);
 }
 
 cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,

@@ -5,19 +5,23 @@
 // kernels_tc.cu the tensor-core form; both share everything else.
 //
 //  F1 k_fwd_cols   : unpack z[n] = x[2n] + i x[2n+1]; length-R2 FFTs down the
-//                    R1 columns n1 of z viewed as [R2][R1]; multiply by
-//                    exp(-2 pi i n1 k2 / L); store in place of the column.
-//  F2 k_fwd_rows   : length-R1 FFTs along the rows k2 (Z[k2 + R2 k1]); rows k2
+//                    R1 columns n1 of z viewed as [R2][R1]; store in place.
+//  F2 k_fwd_rows   : multiply row k2 by exp(-2 pi i n1 k2 / L) as it is loaded,
+//                    length-R1 FFTs along the rows (Z[k2 + R2 k1]); rows k2
 //                    and R2-k2 share a CTA so the real-input split
 //                    X[k] = (Z[k] + Z*[L-k])/2 - i e^{-i pi k/L} (Z[k] - Z*[L-k])/2
-//                    is local; multiply by the inverse ISM response (Eq. 4);
-//                    store Y[k] in natural order.
-//  I1 k_inv_cols   : per sub-channel c (bins cM..cM+M-1), inverse length-Q2
-//                    FFTs down the Q1 columns j1, multiply by exp(+2 pi i j1 m2 / M).
+//                    is local; store X[k] at row k2, column k1.
+//  I1 k_inv_cols   : per sub-channel c (bins cM..cM+M-1): multiply each bin by
+//                    the inverse ISM response (Eq. 4) as it is loaded, inverse
+//                    length-Q2 FFTs down the Q1 columns j1, multiply by
+//                    exp(+2 pi i j1 m2 / M).
 //  I2 k_inv_rows   : inverse length-Q1 FFTs along rows m2 for all sub-channels
 //                    of the same m2 in one CTA: v_c[m2 + Q2 m1] / M, keep the
 //                    valid span n_past <= m < M - n_fut, detect |v|^2 and sum
 //                    over sub-channels into P (and optionally store v).
+//  Table lookups (twiddles, chirp anchors) sit in the load phases, where their
+//  latency overlaps the tile's own loads; I1 stages its CTA's chirp anchors in
+//  shared memory when they are few (one anchor covers up to 2^15 bins).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -30,18 +34,26 @@
 
 namespace pond {
 
-// exp(-2 pi i phi(k)) from the anchor table (phase error < 1e-7 cycles).
-__device__ __forceinline__ float2 chirp_factor(const ChirpAnchor* __restrict__ anc, int clog, unsigned k) {
-  const ChirpAnchor a = anc[k >> clog];
-  const int d = (int)(k & ((1u << clog) - 1)) - (int)((1u << clog) >> 1);
-  const unsigned u = a.p0 + a.p1 * (unsigned)d;           // mod 2^32: phase mod 1 cycle
+// exp(-2 pi i phi(k)) from the anchor table: the phase mod 1 is exact to
+// < 1e-7 cycles (FP64-built fixed point, see k_make_chirp_anchors); the final
+// sine and cosine of 2 pi r, |r| <= 1/2 + 1e-3, use the hardware approximation
+// (absolute error about 4e-7 on [-pi, pi]).
+__device__ __forceinline__ float2 chirp_from(const ChirpAnchor& a, int clog, unsigned k) {
+  const long long d = (long long)(k & ((1u << clog) - 1)) - (long long)((1u << clog) >> 1);
+  const unsigned long long ud = (unsigned long long)d;
+  // phi0 + phi1 d + phi2 d^2 mod 1, exact in Q0.64 (two's-complement wrap = mod 1)
+  const unsigned long long ph = ((unsigned long long)a.p0 << 32) + a.p1 * ud + a.p2 * (ud * ud);
   const float df = (float)d;
-  float r = (float)(int)u * 2.3283064365386963e-10f;      // 2^-32
-  r += fmaf(a.p3, df, a.p2) * (df * df);
+  float r = (float)(int)(unsigned)(ph >> 32) * 2.3283064365386963e-10f;   // 2^-32
+  r = fmaf(a.p3 * df, df * df, r);
   float s, c;
-  sincospif(2.0f * r, &s, &c);
+  __sincosf(6.2831853071795865f * r, &s, &c);
   return make_float2(c, -s);
 }
+
+// Chirp anchors an I1 CTA stages in shared memory (16 KiB) before its lookups.
+constexpr int ANC_STAGE = 512;
+constexpr int ANC_BYTES = ANC_STAGE * (int)sizeof(ChirpAnchor);
 
 
 __device__ __forceinline__ float2 tw2(const Tw2& t, unsigned e) {
@@ -75,9 +87,9 @@ __device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
 }
 
 // z viewed as [R2][R1] (z[n1 + R1 n2]); a CTA transforms nl adjacent columns n1
-// and stores them in place, scaled by exp(-2 pi i n1 k2 / L).
+// and stores them in place (the twiddle exp(-2 pi i n1 k2 / L) is F2's).
 template <int R2, bool TC>
-__global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1, Tw2 twL,
+__global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict__ out, int logR1,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
@@ -143,8 +155,7 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int k2 = idx >> lognl, b = idx & (nl - 1);
-    const unsigned n1 = (unsigned)(n1_0 + b);
-    out[(size_t)n1 + ((size_t)k2 << logR1)] = cmul(sm[pidx(b, k2, LSTR)], tw2(twL, n1 * (unsigned)k2));
+    out[(size_t)(n1_0 + b) + ((size_t)k2 << logR1)] = sm[pidx(b, k2, LSTR)];
   }
 }
 
@@ -157,9 +168,8 @@ __global__ void __launch_bounds__(NT) k_fwd_cols(SegIn in, float2* __restrict__ 
 // X[k] can be formed from Z[k] and Z[L-k]; the chirped spectrum Y[k2 + R2 k1] is
 // stored at row k2, column k1 of the output (the same place the row was read).
 template <int R1, bool TC>
-__global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logR2, int logL, Tw2 tw2L,
-                                                    const ChirpAnchor* __restrict__ anc, int clog, int apply_chirp,
+__global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
+                                                    int logR2, int logL, Tw2 twL, Tw2 tw2L,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
   float2* stw = smem;
@@ -181,37 +191,77 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
     if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
     return R2 - (q0 + t);
   };
-  float2 r[EPT];
+  {  // 16-byte loads (two consecutive columns n1, n1 + 1 of row k2) scaled by
+     // w^{n1 k2} and w^{(n1+1) k2}, w = exp(-2 pi i / L): the second factor is
+     // the first times w^{k2}, one per slot
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    constexpr int H = EPT / 2;
+    float4 r[H];
+    float2 wa[H];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) r[u] = in[((size_t)line_of(idx >> LOGR1) << LOGR1) + (idx & (R1 - 1))];
-  }
+    for (int u = 0; u < H; ++u) {
+      const int idx = 2 * (threadIdx.x + u * NT);
+      if (idx < tot) {
+        const unsigned k2 = (unsigned)line_of(idx >> LOGR1), n1 = (unsigned)(idx & (R1 - 1));
+        r[u] = __ldg(in4 + ((((size_t)k2 << LOGR1) + n1) >> 1));
+        wa[u] = tw2(twL, n1 * k2);
+      }
+    }
+    float2 wk[2] = {tw2(twL, (unsigned)line_of(0)), tw2(twL, (unsigned)line_of(nl - 1))};
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) sm[pidx(idx >> LOGR1, idx & (R1 - 1), LSTR)] = r[u];
+    for (int u = 0; u < H; ++u) {
+      const int idx = 2 * (threadIdx.x + u * NT);
+      if (idx < tot) {
+        const int slot = idx >> LOGR1;
+        float2 wb = wa[u];
+        if (slot == 0) wb = cmul(wb, wk[0]);
+        else if (slot == nl - 1) wb = cmul(wb, wk[1]);
+        else wb = cmul(wb, tw2(twL, (unsigned)line_of(slot)));
+        float2* p = sm + pidx(slot, idx & (R1 - 1), LSTR);   // idx even: no pad between the two
+        p[0] = cmul(make_float2(r[u].x, r[u].y), wa[u]);
+        p[1] = cmul(make_float2(r[u].z, r[u].w), wb);
+      }
+    }
   }
   __syncthreads();
   fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
+  // Real-input split by conjugate pairs: with A = Z[k], B = conj(Z[L-k]),
+  // E = (A + B)/2, O = (A - B)/2 and W = exp(-i pi k / L),
+  //   X[k] = E - i W O   and   X[L-k] = conj(E) - i conj(W O),
+  // so one item produces both bins of a pair (slot t < np, column k1) and
+  // (slot t + np, column R1-1-k1).  In tile 0 lines 0 and R2/2 pair with
+  // themselves: line 0 pairs columns k1 and R1-k1 (k1 = 0 and R1/2 alone),
+  // line R2/2 columns k1 and R1-1-k1.
   const unsigned lmask = (1u << logL) - 1;
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
-    const int line = line_of(slot);
-    const unsigned k = (unsigned)line + ((unsigned)k1 << logR2);
-    const unsigned kp = (0u - k) & lmask;
-    const int linep = (int)(kp & (unsigned)(R2 - 1));
-    const int k1p = (int)(kp >> logR2);
-    const int slotp = (linep == line) ? slot : (slot < np ? slot + np : slot - np);
-    const float2 A = sm[pidx(slot, k1, LSTR)];
-    const float2 B = cconj(sm[pidx(slotp, k1p, LSTR)]);
+  auto emit = [&](int slot, int k1, float2 X) { out[((size_t)line_of(slot) << LOGR1) + k1] = X; };
+  auto split = [&](int sa, int ka, int sb, int kb, bool both) {
+    const unsigned k = (unsigned)line_of(sa) + ((unsigned)ka << logR2);
+    const float2 A = sm[pidx(sa, ka, LSTR)];
+    const float2 B = cconj(sm[pidx(sb, kb, LSTR)]);
     const float2 E = cscale(cadd(A, B), 0.5f);
     const float2 O = cscale(csub(A, B), 0.5f);
-    float2 X = cadd(E, rot90<false>(cmul(tw2(tw2L, k), O)));   // E - i exp(-i pi k/L) O
-    if (apply_chirp) X = cmul(X, chirp_factor(anc, clog, k));
-    out[((size_t)line << LOGR1) + k1] = X;
+    const float2 WO = cmul(tw2(tw2L, k & lmask), O);
+    emit(sa, ka, cadd(E, rot90<false>(WO)));
+    if (both) emit(sb, kb, cadd(cconj(E), rot90<false>(cconj(WO))));
+  };
+  const int items = np * R1;
+#pragma unroll 2
+  for (int it = threadIdx.x; it < items; it += NT) {
+    const int t = it >> LOGR1, k1 = it & (R1 - 1);
+    if (q0 == 0 && t == 0) {
+      if (k1 == 0) {
+        split(0, 0, 0, 0, false);
+        split(0, R1 >> 1, 0, R1 >> 1, false);
+      } else if (k1 < (R1 >> 1)) {
+        split(0, k1, 0, R1 - k1, true);
+      } else {
+        const int j = k1 - (R1 >> 1);
+        split(np, j, np, R1 - 1 - j, true);
+      }
+    } else {
+      split(t, k1, t + np, R1 - 1 - k1, true);
+    }
   }
 }
 
@@ -225,13 +275,14 @@ __global__ void __launch_bounds__(NT) k_fwd_rows(const float2* __restrict__ in, 
 // consecutive addresses in j2hi).  The inverse column transform, scaled by
 // exp(+2 pi i j1 m2 / M), is stored in natural order c M + j1 + Q1 m2.
 template <int Q2, bool TC>
-__global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
+__global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
                                                     int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
                                                     const ChirpAnchor* __restrict__ anc, int clog,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(Q2);
+  ChirpAnchor* sanc = reinterpret_cast<ChirpAnchor*>(smem);   // [ANC_STAGE]
+  float2* stw = smem + ANC_BYTES / sizeof(float2);
+  float2* sm = stw + stage_table_size(Q2);
   constexpr int LSTR = line_stride(Q2);
   constexpr int LOGQ2 = ilog2c(Q2);
   const int Q1 = 1 << logQ1;
@@ -245,6 +296,17 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
   const int l0 = tile * nl;
   const int s = logR2 - logQ1;                 // j2 = j2lo + 2^s j2hi
   const int logrun = LOGQ2 - s;                // run length M / R2 (>= 1)
+  // the CTA's bins lie in the sub-channels of its lines: stage their anchors
+  long long a_lo = 0;
+  bool staged = false;
+  if (anc) {
+    const long long c0 = l0 >> logQ1, c1 = (l0 + nl - 1) >> logQ1;
+    a_lo = (c0 << logM) >> clog;
+    const long long na = ((((c1 + 1) << logM) - 1) >> clog) - a_lo + 1;
+    staged = na <= ANC_STAGE;
+    if (staged)
+      for (int i = threadIdx.x; i < (int)na; i += NT) sanc[i] = anc[a_lo + i];
+  }
   float2 r[EPT];
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
@@ -258,9 +320,9 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
       const size_t k1 = ((size_t)c << (logM - logR2)) + j2hi;
       const size_t k2 = (size_t)j1 + ((size_t)j2lo << logQ1);
       r[u] = in[k1 + (k2 << logR1)];
-      if (anc) r[u] = cmul(r[u], chirp_factor(anc, clog, (unsigned)(k2 + (k1 << logR2))));
     }
   }
+  if (anc) __syncthreads();   // staged anchors visible
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
     const int idx = threadIdx.x + u * NT;
@@ -268,6 +330,14 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
       const int j2hi = idx & ((1 << logrun) - 1);
       const int rest = idx >> logrun;
       const int j2lo = rest & ((1 << s) - 1);
+      if (anc) {
+        const int l = l0 + (rest >> s);
+        const int c = l >> logQ1, j1 = l & (Q1 - 1);
+        const unsigned k = (unsigned)((size_t)j1 + ((size_t)j2lo << logQ1) +
+                                      ((((size_t)c << (logM - logR2)) + j2hi) << logR2));
+        const ChirpAnchor& a = staged ? sanc[(long long)(k >> clog) - a_lo] : anc[k >> clog];
+        r[u] = cmul(r[u], chirp_from(a, clog, k));
+      }
       sm[pidx(rest >> s, j2lo + (j2hi << s), LSTR)] = r[u];
     }
   }
@@ -289,7 +359,7 @@ __global__ void __launch_bounds__(NT) k_inv_cols(const float2* __restrict__ in, 
 // ---------------------------------------------------------------------------
 
 template <int Q1, bool TC>
-__global__ void __launch_bounds__(NT) k_inv_rows(const float2* __restrict__ buf, float* __restrict__ P,
+__global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ buf, float* __restrict__ P,
                                                     float2* __restrict__ vout, long long vstride,
                                                     long long vofs, int logQ2, int logM, int nchan,
                                                     int m_lo, int m_hi, float scale,
@@ -368,7 +438,7 @@ size_t max_smem_t() {
 
 template <bool TC>
 cudaError_t set_attributes_t() {
-  const int max_smem = (int)max_smem_t<TC>();
+  const int max_smem = (int)max_smem_t<TC>() + ANC_BYTES;   // I1 adds its staged anchors
   cudaError_t e = cudaSuccess;
 #define SET_ATTR(R)                                                                                   \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
@@ -381,12 +451,12 @@ cudaError_t set_attributes_t() {
 }
 
 template <bool TC>
-cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st) {
+cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R2, R1);
   const unsigned grid = (unsigned)(R1 / nl);
   switch (R2) {
-#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR1, twL, tw, g.tc_fwd); break;
+#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR1, tw, g.tc_fwd); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -395,13 +465,13 @@ cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, Tw2 twL, con
 }
 
 template <bool TC>
-cudaError_t launch_fwd_rows_t(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc,
-                              int clog, int apply_chirp, const float2* tw, cudaStream_t st) {
+cudaError_t launch_fwd_rows_t(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+                              cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   const unsigned grid = (unsigned)(R2 / nl);
   switch (R1) {
-#define CASE(R) case R: k_fwd_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR2, g.logL, tw2L, anc, clog, apply_chirp, tw, g.tc_fwd); break;
+#define CASE(R) case R: k_fwd_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR2, g.logL, twL, tw2L, tw, g.tc_fwd); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -417,7 +487,7 @@ cudaError_t launch_inv_cols_t(const Geom& g, const float2* in, float2* out, Tw2 
   const int nl = std::min(TILE / Q2, lines);
   const unsigned grid = (unsigned)(lines / nl);
   switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, anc, clog, tw, g.tc_inv); break;
+#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + ANC_BYTES, st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, anc, clog, tw, g.tc_inv); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -443,9 +513,9 @@ cudaError_t launch_inv_rows_t(const Geom& g, const float2* buf, float* P, float2
 }
 
 // Tensor-core instantiations (kernels_tc.cu).
-cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc,
-                               int clog, int apply_chirp, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+                               cudaStream_t st);
 cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
                                int clog, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows_tc(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,

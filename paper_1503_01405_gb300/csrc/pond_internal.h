@@ -9,16 +9,20 @@
 
 namespace pond {
 
-constexpr int CHIRP_LOG_MAX = 8;             // at most 2^8 bins per chirp anchor
+constexpr int CHIRP_LOG_MAX = 15;            // at most 2^15 bins per chirp anchor
 constexpr int MAX_NBINS = 4096;              // fold bins (per-warp FP64 histograms in smem)
 constexpr int MAX_FOLD_PARTS = 304;          // fold CTAs per segment (2 per SM)
 
-// Taylor coefficients of the dedispersion phase about an anchor bin.
+// Taylor coefficients of the dedispersion phase phi (cycles) about an anchor
+// bin: phi(k_a + d) = phi0 + phi1 d + phi2 d^2 + phi3 d^3.  The first three
+// terms are evaluated exactly mod 1 in 64-bit fixed point (d is an integer),
+// so only the small cubic term is rounded in FP32.
 struct __align__(16) ChirpAnchor {
-  unsigned p0;   // phi(k_a) mod 1, Q0.32
-  unsigned p1;   // phi'(k_a) mod 1 (cycles per bin), Q0.32
-  float p2;      // phi''(k_a) / 2
-  float p3;      // phi'''(k_a) / 6
+  unsigned long long p1;   // phi1 mod 1, Q0.64
+  unsigned long long p2;   // phi2 mod 1, Q0.64
+  unsigned p0;             // phi0 mod 1, Q0.32
+  float p3;                // phi3
+  unsigned pad[2];
 };
 
 // Two-level twiddle table for exponents e < n: w^e = hi[e >> 12] * lo[e & 4095].
@@ -77,9 +81,9 @@ cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du,
 cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st);
 cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st);
 int stage_tw_entries(int R);
-cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, Tw2 twL, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 tw2L, const ChirpAnchor* anc, int clog,
-                            int apply_chirp, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+                            cudaStream_t st);
 cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
                             int clog, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
