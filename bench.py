@@ -503,6 +503,9 @@ def main():
                          "learned: classifier training and evaluation beside the boxcar detector; "
                          "precision: split-BF16 tensor-core FFT stages vs the FP32 path and the oracle")
     ap.add_argument("--chunks", type=int, default=40, help="learned: 8 s training chunks")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x5"],
+                    help="full-rate: arithmetic of the radix-16 FFT stages (FP32, or split-BF16 tensor-core "
+                         "DFT products with three or five terms)")
     args = ap.parse_args()
     rank, ws, dist = dist_init()
     if args.impl == "reference":
@@ -533,8 +536,9 @@ def main():
     n = spec.n
     x_dev = synth.make_stream_torch(spec, dev)
     torch.cuda.synchronize()
+    prec = {"fp32": pond.POND_FP32, "bf16x3": pond.POND_SPLIT_BF16, "bf16x5": pond.POND_SPLIT_BF16_5T}[args.precision]
     eng = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
-                      t_dec=PLAN["t_dec"], timing=True, device=local)
+                      t_dec=PLAN["t_dec"], timing=True, device=local, precision=prec)
     stream = torch.cuda.current_stream(dev)
 
     def step_device():
@@ -586,7 +590,7 @@ def main():
     xh = x_host.numpy()
     torch.cuda.synchronize()
     eng_h = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
-                        t_dec=PLAN["t_dec"], device=local)
+                        t_dec=PLAN["t_dec"], device=local, precision=prec)
     prof = {}
 
     def step_host():
@@ -619,8 +623,10 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(n), "realtime_factor": value / REALTIME_MSPS,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32acc", "bf16x5": "bf16x5+f32acc"}[args.precision],
+                "data": "synthetic", "config": dict(workload_config(n), fft_stages=args.precision),
+                "realtime_factor": value / REALTIME_MSPS,
                 "e2e": e2e, "gpu_launches": int(st1["kernel_launches"]) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
         print(json.dumps(line), flush=True)

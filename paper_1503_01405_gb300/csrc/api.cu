@@ -111,7 +111,9 @@ struct Lane {
   float2* stw = nullptr;                    // stage twiddle tables of R1, R2, Q1, Q2
   const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
   float2* tw2buf = nullptr;
-  Tw2 twL, tw2L, twM;                       // exp(-2 pi i e/L), exp(-2 pi i e/(2L)), exp(+2 pi i e/M)
+  Tw2 tw2L;                                 // exp(-2 pi i e/(2L))
+  float2* tw3L = nullptr;                   // three-level exp(-2 pi i e/L)
+  float2* tw3M = nullptr;                   // three-level exp(+2 pi i e/M)
   int8_t* carry[2] = {nullptr, nullptr};
   int carry_cur = 0;
   long long seg_start = 0, carry_pos = 0, segments = 0;
@@ -303,23 +305,22 @@ int build_lane(pond_t h, Lane* ln) {
   ln->stwQ1 = ln->stwR2 + n2;
   ln->stwQ2 = ln->stwQ1 + n3;
   auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
-  const long long total = 3ll * TW2_LO + nhi(g.logL) + nhi(g.logL + 1) + nhi(g.logM);
+  const long long total = TW2_LO + nhi(g.logL + 1) + 2 * 768;
   CK(cudaMalloc(&ln->tw2buf, total * sizeof(float2)));
   float2* p = ln->tw2buf;
-  ln->twL = {p, p + TW2_LO};
-  p += TW2_LO + nhi(g.logL);
+  ln->tw3L = p;
+  ln->tw3M = p + 768;
+  p += 2 * 768;
   ln->tw2L = {p, p + TW2_LO};
-  p += TW2_LO + nhi(g.logL + 1);
-  ln->twM = {p, p + TW2_LO};
   CK(cudaMalloc(&ln->carry[0], g.N));
   CK(cudaMalloc(&ln->carry[1], g.N));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwR1), 1 << g.logR1, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwR2), 1 << g.logR2, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwQ1), 1 << g.logQ1, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwQ2), 1 << g.logQ2, h->st));
-  CK(launch_tw2(const_cast<float2*>(ln->twL.lo), const_cast<float2*>(ln->twL.hi), g.logL, -1, h->st));
+  CK(launch_tw3(ln->tw3L, g.logL, -1, h->st));
   CK(launch_tw2(const_cast<float2*>(ln->tw2L.lo), const_cast<float2*>(ln->tw2L.hi), g.logL + 1, -1, h->st));
-  CK(launch_tw2(const_cast<float2*>(ln->twM.lo), const_cast<float2*>(ln->twM.hi), g.logM, +1, h->st));
+  CK(launch_tw3(ln->tw3M, g.logM, +1, h->st));
   return POND_OK;
 }
 
@@ -467,16 +468,16 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   RC(record(h, 0));
   CK(launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st));
   RC(record(h, 1 + ST_F1));
-  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.twL, ln.tw2L, ln.stwR1, h->st));
+  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw3L, ln.tw2L, ln.stwR1, h->st));
   RC(record(h, 1 + ST_F2));
   h->launches += 2;
   for (size_t q = 0; q < ln.trials.size(); ++q) {
     const int d = ln.trials[q];
     const Trial& t = h->trials[d];
     // every trial's chirp is applied as I1 loads the shared forward spectrum
-    CK(launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, t.anc, t.clog, ln.stwQ2, h->st));
+    CK(launch_inv_cols(g, ln.bufB, ln.bufA, t.anc, t.clog, ln.stwQ2, h->st));
     if (q == 0) RC(record(h, 1 + ST_I1));
-    CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.stwQ1, h->st));
+    CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, h->st));
     if (q == 0) RC(record(h, 1 + ST_I2));
     if (!h->multi) {
       CK(launch_fold(ln.P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
@@ -636,14 +637,15 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {      // first pass warms up
     if (it == 1) ce = cudaEventRecord(e[0], h->st);
     if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st);
-    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.twL, ln.tw2L, ln.stwR1, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw3L, ln.tw2L, ln.stwR1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[1], h->st);
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
     if (it == 1) ce = cudaEventRecord(e[2], h->st);
-    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB, ln.bufA, ln.twM, anc, clog, ln.stwQ2, h->st);
+    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB, ln.bufA, anc, clog, ln.stwQ2, h->st);
     if (ce == cudaSuccess)
-      ce = launch_inv_rows(g, ln.bufA, ln.P, nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.stwQ1, h->st);
+      ce = launch_inv_rows(g, ln.bufA, ln.P, nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.tw3M, ln.stwQ1,
+                           h->st);
     if (ce == cudaSuccess) ce = launch_decimate(ln.P, nv, 0, 8, 1, 0, nv / 8, T, C, nv / 8 + 1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[3], h->st);

@@ -94,6 +94,17 @@ __global__ void k_make_chirp_anchors(ChirpAnchor* anc, long long nanc, int clog,
   anc[a] = r;
 }
 
+// Three-level table for exponents e < 2^24: entry 256 l + j holds
+// w^(j 2^(8 l)), w = exp(sign 2 pi i / 2^logn) (FP64 sincospi).
+__global__ void k_make_tw3(float2* out, int logn, int sign) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 768) return;
+  const long long e = (long long)(i & 255) << (8 * (i >> 8));
+  double s, c;
+  sincospi(2.0 * sign * (double)e / (double)(1ll << logn), &s, &c);
+  out[i] = make_float2((float)c, (float)s);
+}
+
 // ---------------------------------------------------------------------------
 // Two-level twiddle tables: w^e = hi[e >> 12] * lo[e & 4095], w = exp(+-2 pi i / n)
 // ---------------------------------------------------------------------------
@@ -330,6 +341,11 @@ cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_tw3(float2* out, int logn, int sign, cudaStream_t st) {
+  k_make_tw3<<<3, 256, 0, st>>>(out, logn, sign);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st) {
   k_make_chirp_anchors<<<(unsigned)((nanc + 127) / 128), 128, 0, st>>>(anc, nanc, clog, du, half, f0, alpha, sgn);
@@ -348,22 +364,23 @@ cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* 
   return g.tc_terms ? launch_fwd_cols_tc(g, in, out, tw, st) : launch_fwd_cols_t<false>(g, in, out, tw, st);
 }
 
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L, const float2* tw,
                             cudaStream_t st) {
-  return g.tc_terms ? launch_fwd_rows_tc(g, in, out, twL, tw2L, tw, st)
-                    : launch_fwd_rows_t<false>(g, in, out, twL, tw2L, tw, st);
+  return g.tc_terms ? launch_fwd_rows_tc(g, in, out, tw3L, tw2L, tw, st)
+                    : launch_fwd_rows_t<false>(g, in, out, tw3L, tw2L, tw, st);
 }
 
-cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc,
                             int clog, const float2* tw, cudaStream_t st) {
-  return g.tc_terms ? launch_inv_cols_tc(g, in, out, twM, anc, clog, tw, st)
-                    : launch_inv_cols_t<false>(g, in, out, twM, anc, clog, tw, st);
+  return g.tc_terms ? launch_inv_cols_tc(g, in, out, anc, clog, tw, st)
+                    : launch_inv_cols_t<false>(g, in, out, anc, clog, tw, st);
 }
 
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                            long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st) {
-  return g.tc_terms ? launch_inv_rows_tc(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw, st)
-                    : launch_inv_rows_t<false>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw, st);
+                            long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
+                               cudaStream_t st) {
+  return g.tc_terms ? launch_inv_rows_tc(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw3M, tw, st)
+                    : launch_inv_rows_t<false>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw3M, tw, st);
 }
 
 size_t fold_smem_bytes(int nbins) {

@@ -13,19 +13,20 @@ cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, const float
   return launch_fwd_cols_t<true>(g, in, out, tw, st);
 }
 
-cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L, const float2* tw,
                                cudaStream_t st) {
-  return launch_fwd_rows_t<true>(g, in, out, twL, tw2L, tw, st);
+  return launch_fwd_rows_t<true>(g, in, out, tw3L, tw2L, tw, st);
 }
 
-cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc,
                                int clog, const float2* tw, cudaStream_t st) {
-  return launch_inv_cols_t<true>(g, in, out, twM, anc, clog, tw, st);
+  return launch_inv_cols_t<true>(g, in, out, anc, clog, tw, st);
 }
 
 cudaError_t launch_inv_rows_tc(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                               long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st) {
-  return launch_inv_rows_t<true>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw, st);
+                               long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
+                               cudaStream_t st) {
+  return launch_inv_rows_t<true>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw3M, tw, st);
 }
 
 namespace {

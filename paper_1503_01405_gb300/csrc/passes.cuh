@@ -13,9 +13,9 @@
 //                    is local; store X[k] at row k2, column k1.
 //  I1 k_inv_cols   : per sub-channel c (bins cM..cM+M-1): multiply each bin by
 //                    the inverse ISM response (Eq. 4) as it is loaded, inverse
-//                    length-Q2 FFTs down the Q1 columns j1, multiply by
-//                    exp(+2 pi i j1 m2 / M).
-//  I2 k_inv_rows   : inverse length-Q1 FFTs along rows m2 for all sub-channels
+//                    length-Q2 FFTs down the Q1 columns j1; store in natural order.
+//  I2 k_inv_rows   : multiply row m2 by exp(+2 pi i j1 m2 / M) as it is loaded,
+//                    inverse length-Q1 FFTs along rows m2 for all sub-channels
 //                    of the same m2 in one CTA: v_c[m2 + Q2 m1] / M, keep the
 //                    valid span n_past <= m < M - n_fut, detect |v|^2 and sum
 //                    over sub-channels into P (and optionally store v).
@@ -39,12 +39,17 @@ namespace pond {
 // sine and cosine of 2 pi r, |r| <= 1/2 + 1e-3, use the hardware approximation
 // (absolute error about 4e-7 on [-pi, pi]).
 __device__ __forceinline__ float2 chirp_from(const ChirpAnchor& a, int clog, unsigned k) {
-  const long long d = (long long)(k & ((1u << clog) - 1)) - (long long)((1u << clog) >> 1);
-  const unsigned long long ud = (unsigned long long)d;
-  // phi0 + phi1 d + phi2 d^2 mod 1, exact in Q0.64 (two's-complement wrap = mod 1)
-  const unsigned long long ph = ((unsigned long long)a.p0 << 32) + a.p1 * ud + a.p2 * (ud * ud);
+  const int d = (int)(k & ((1u << clog) - 1)) - (int)((1u << clog) >> 1);   // |d| <= 2^14
+  const unsigned dd = (unsigned)(d * d);
+  // top 32 bits of phi0 + phi1 d + phi2 d^2 mod 1 in Q0.64: the high words
+  // multiply mod 2^32, the low words contribute their products' high words
+  // (each truncation loses < 2^-32 cycles)
+  const unsigned p1h = (unsigned)(a.p1 >> 32), p1l = (unsigned)a.p1;
+  const unsigned p2h = (unsigned)(a.p2 >> 32), p2l = (unsigned)a.p2;
+  const unsigned u = a.p0 + p1h * (unsigned)d + (unsigned)(((long long)p1l * d) >> 32) + p2h * dd +
+                     __umulhi(p2l, dd);
   const float df = (float)d;
-  float r = (float)(int)(unsigned)(ph >> 32) * 2.3283064365386963e-10f;   // 2^-32
+  float r = (float)(int)u * 2.3283064365386963e-10f;   // 2^-32
   r = fmaf(a.p3 * df, df * df, r);
   float s, c;
   __sincosf(6.2831853071795865f * r, &s, &c);
@@ -61,6 +66,22 @@ __device__ __forceinline__ float2 tw2(const Tw2& t, unsigned e) {
 }
 
 constexpr int EPT = TILE / NT;   // tile elements per thread
+
+// Three-level table of w^e, e < 2^24, held in shared memory by F2 and I2:
+// w^e = t0[e0] t1[e1] t2[e2], e = e0 + 2^8 e1 + 2^16 e2 (each level built in
+// FP64 on the device; two FP32 products).  In shared memory level 0 is padded
+// by one entry every 16 (entry e0 at e0 + e0/16) so that lanes whose
+// exponents step by a multiple of 16 still fall in different banks.
+constexpr int TW3_N = 768;                 // global table: three levels of 256
+constexpr int TW3_SN = 784;                // shared copy: padded level 0 (272) + 512
+constexpr int TW3_BYTES = TW3_SN * (int)sizeof(float2);
+__device__ __forceinline__ void load_tw3(float2* st, const float2* __restrict__ g) {
+  for (int i = threadIdx.x; i < TW3_N; i += blockDim.x) st[i < 256 ? i + (i >> 4) : i + 16] = __ldg(g + i);
+}
+__device__ __forceinline__ float2 tw3(const float2* t, unsigned e) {
+  const unsigned e0 = e & 255u;
+  return cmul(cmul(t[e0 + (e0 >> 4)], t[272 + ((e >> 8) & 255u)]), t[528 + (e >> 16)]);
+}
 
 
 // Tile entries (float2) a pass allocates for nl lines of length R.  The
@@ -169,13 +190,15 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
 // stored at row k2, column k1 of the output (the same place the row was read).
 template <int R1, bool TC>
 __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logR2, int logL, Tw2 twL, Tw2 tw2L,
+                                                    int logR2, int logL, const float2* __restrict__ tw3L, Tw2 tw2L,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(R1);
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stw = smem + TW3_SN;
+  float2* sm = stw + stage_table_size(R1);
   constexpr int LSTR = line_stride(R1);
   constexpr int LOGR1 = ilog2c(R1);
+  load_tw3(st3, tw3L);
   const int R2 = 1 << logR2;
   const int nl = min(TILE / R1, R2);   // 2 * pairs
   const int np = nl >> 1;
@@ -191,35 +214,29 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
     if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
     return R2 - (q0 + t);
   };
-  {  // 16-byte loads (two consecutive columns n1, n1 + 1 of row k2) scaled by
-     // w^{n1 k2} and w^{(n1+1) k2}, w = exp(-2 pi i / L): the second factor is
-     // the first times w^{k2}, one per slot
+  {  // 16-byte loads (two consecutive columns n1, n1 + 1 of row k2), scaled by
+     // w^{n1 k2} and w^{(n1+1) k2}, w = exp(-2 pi i / L), once the table is in
     const float4* in4 = reinterpret_cast<const float4*>(in);
     constexpr int H = EPT / 2;
     float4 r[H];
-    float2 wa[H];
 #pragma unroll
     for (int u = 0; u < H; ++u) {
       const int idx = 2 * (threadIdx.x + u * NT);
       if (idx < tot) {
         const unsigned k2 = (unsigned)line_of(idx >> LOGR1), n1 = (unsigned)(idx & (R1 - 1));
         r[u] = __ldg(in4 + ((((size_t)k2 << LOGR1) + n1) >> 1));
-        wa[u] = tw2(twL, n1 * k2);
       }
     }
-    float2 wk[2] = {tw2(twL, (unsigned)line_of(0)), tw2(twL, (unsigned)line_of(nl - 1))};
+    __syncthreads();   // st3 filled
 #pragma unroll
     for (int u = 0; u < H; ++u) {
       const int idx = 2 * (threadIdx.x + u * NT);
       if (idx < tot) {
         const int slot = idx >> LOGR1;
-        float2 wb = wa[u];
-        if (slot == 0) wb = cmul(wb, wk[0]);
-        else if (slot == nl - 1) wb = cmul(wb, wk[1]);
-        else wb = cmul(wb, tw2(twL, (unsigned)line_of(slot)));
-        float2* p = sm + pidx(slot, idx & (R1 - 1), LSTR);   // idx even: no pad between the two
-        p[0] = cmul(make_float2(r[u].x, r[u].y), wa[u]);
-        p[1] = cmul(make_float2(r[u].z, r[u].w), wb);
+        const unsigned k2 = (unsigned)line_of(slot), n1 = (unsigned)(idx & (R1 - 1));
+        float2* p = sm + pidx(slot, (int)n1, LSTR);   // n1 even: no pad between the two
+        p[0] = cmul(make_float2(r[u].x, r[u].y), tw3(st3, n1 * k2));
+        p[1] = cmul(make_float2(r[u].z, r[u].w), tw3(st3, (n1 + 1) * k2));
       }
     }
   }
@@ -276,7 +293,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
 // exp(+2 pi i j1 m2 / M), is stored in natural order c M + j1 + Q1 m2.
 template <int Q2, bool TC>
 __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logQ1, int logM, int logR1, int logR2, int nchan, Tw2 twM,
+                                                    int logQ1, int logM, int logR1, int logR2, int nchan,
                                                     const ChirpAnchor* __restrict__ anc, int clog,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
@@ -333,9 +350,9 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
       if (anc) {
         const int l = l0 + (rest >> s);
         const int c = l >> logQ1, j1 = l & (Q1 - 1);
-        const unsigned k = (unsigned)((size_t)j1 + ((size_t)j2lo << logQ1) +
-                                      ((((size_t)c << (logM - logR2)) + j2hi) << logR2));
-        const ChirpAnchor& a = staged ? sanc[(long long)(k >> clog) - a_lo] : anc[k >> clog];
+        const unsigned k = (unsigned)j1 + ((unsigned)j2lo << logQ1) +
+                           ((((unsigned)c << (logM - logR2)) + (unsigned)j2hi) << logR2);
+        const ChirpAnchor& a = staged ? sanc[(int)((long long)(k >> clog) - a_lo)] : anc[k >> clog];
         r[u] = cmul(r[u], chirp_from(a, clog, k));
       }
       sm[pidx(rest >> s, j2lo + (j2hi << s), LSTR)] = r[u];
@@ -348,9 +365,8 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int m2 = idx >> lognl, b = idx & (nl - 1);
     const int l = l0 + b;
-    const unsigned j1 = (unsigned)(l & (Q1 - 1));
-    const size_t addr = ((size_t)(l >> logQ1) << logM) + j1 + ((size_t)m2 << logQ1);
-    out[addr] = cmul(sm[pidx(b, m2, LSTR)], tw2(twM, j1 * (unsigned)m2));
+    const size_t addr = ((size_t)(l >> logQ1) << logM) + (size_t)(l & (Q1 - 1)) + ((size_t)m2 << logQ1);
+    out[addr] = sm[pidx(b, m2, LSTR)];
   }
 }
 
@@ -363,10 +379,13 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
                                                     float2* __restrict__ vout, long long vstride,
                                                     long long vofs, int logQ2, int logM, int nchan,
                                                     int m_lo, int m_hi, float scale,
+                                                    const float2* __restrict__ tw3M,
                                                     const float2* __restrict__ tw, TcArgs tca) {
   extern __shared__ float2 smem[];
-  float2* stw = smem;
-  float2* sm = smem + stage_table_size(Q1);
+  float2* st3 = smem;                              // [TW3_SN], w = exp(+2 pi i / M)
+  float2* stw = smem + TW3_SN;
+  float2* sm = stw + stage_table_size(Q1);
+  load_tw3(st3, tw3M);
   constexpr int LSTR = line_stride(Q1);
   constexpr int LOGQ1 = ilog2c(Q1);
   const int Q2 = 1 << logQ2;
@@ -389,10 +408,25 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
       r[u] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
     }
   }
+  __syncthreads();   // st3 filled
+  // element j1 = e of row m2 carries I1's twiddle exp(+2 pi i j1 m2 / M); the
+  // sub-channels of a row share it, so a thread reuses it while j1 m2 repeats
+  {
+    unsigned last = 0xffffffffu;
+    float2 w = make_float2(1.f, 0.f);
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) sm[pidx(idx >> LOGQ1, idx & (Q1 - 1), LSTR)] = r[u];
+    for (int u = 0; u < EPT; ++u) {
+      const int idx = threadIdx.x + u * NT;
+      if (idx < tot) {
+        const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
+        const unsigned ex = (unsigned)e * (unsigned)(m2_0 + (slot & (b2 - 1)));
+        if (ex != last) {
+          w = tw3(st3, ex);
+          last = ex;
+        }
+        sm[pidx(slot, e, LSTR)] = cmul(r[u], w);
+      }
+    }
   }
   __syncthreads();
   fft_lines<Q1, true, TC>(sm, nl, stw, &tcc);
@@ -438,7 +472,8 @@ size_t max_smem_t() {
 
 template <bool TC>
 cudaError_t set_attributes_t() {
-  const int max_smem = (int)max_smem_t<TC>() + ANC_BYTES;   // I1 adds its staged anchors
+  // I1 adds its staged anchors, F2 its twiddle table (the larger of the two)
+  const int max_smem = (int)max_smem_t<TC>() + (ANC_BYTES > TW3_BYTES ? ANC_BYTES : TW3_BYTES);
   cudaError_t e = cudaSuccess;
 #define SET_ATTR(R)                                                                                   \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols<R, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem); \
@@ -465,13 +500,13 @@ cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, const float2
 }
 
 template <bool TC>
-cudaError_t launch_fwd_rows_t(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+cudaError_t launch_fwd_rows_t(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L, const float2* tw,
                               cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   const unsigned grid = (unsigned)(R2 / nl);
   switch (R1) {
-#define CASE(R) case R: k_fwd_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR2, g.logL, twL, tw2L, tw, g.tc_fwd); break;
+#define CASE(R) case R: k_fwd_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + TW3_BYTES, st>>>(in, out, g.logR2, g.logL, tw3L, tw2L, tw, g.tc_fwd); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -480,14 +515,14 @@ cudaError_t launch_fwd_rows_t(const Geom& g, const float2* in, float2* out, Tw2 
 }
 
 template <bool TC>
-cudaError_t launch_inv_cols_t(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+cudaError_t launch_inv_cols_t(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc,
                               int clog, const float2* tw, cudaStream_t st) {
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int lines = g.nchan * Q1;
   const int nl = std::min(TILE / Q2, lines);
   const unsigned grid = (unsigned)(lines / nl);
   switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + ANC_BYTES, st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, twM, anc, clog, tw, g.tc_inv); break;
+#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + ANC_BYTES, st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, anc, clog, tw, g.tc_inv); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -497,14 +532,15 @@ cudaError_t launch_inv_cols_t(const Geom& g, const float2* in, float2* out, Tw2 
 
 template <bool TC>
 cudaError_t launch_inv_rows_t(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                              long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st) {
+                              long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
+                               cudaStream_t st) {
   const int Q2 = 1 << g.logQ2, Q1 = 1 << g.logQ1;
   const int b2 = std::min(TILE / (Q1 * g.nchan), Q2);
   const int nl = g.nchan * b2;
   const unsigned grid = (unsigned)(Q2 / b2);
   const float scale = 1.0f / (float)(1u << g.logM);
   switch (Q1) {
-#define CASE(R) case R: k_inv_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, m_lo, m_hi, scale, tw, g.tc_inv); break;
+#define CASE(R) case R: k_inv_rows<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + TW3_BYTES, st>>>(buf, P, vout, vstride, vofs, g.logQ2, g.logM, g.nchan, m_lo, m_hi, scale, tw3M, tw, g.tc_inv); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -514,11 +550,12 @@ cudaError_t launch_inv_rows_t(const Geom& g, const float2* buf, float* P, float2
 
 // Tensor-core instantiations (kernels_tc.cu).
 cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+cudaError_t launch_fwd_rows_tc(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L, const float2* tw,
                                cudaStream_t st);
-cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+cudaError_t launch_inv_cols_tc(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc,
                                int clog, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows_tc(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                               long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st);
+                               long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
+                               cudaStream_t st);
 
 }  // namespace pond

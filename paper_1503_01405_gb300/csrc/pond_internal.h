@@ -79,15 +79,18 @@ int set_error(int code, const char* msg);
 cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du, double half,
                           double f0, double alpha, int sgn, cudaStream_t st);
 cudaError_t launch_tw2(float2* lo, float2* hi, int logn, int sign, cudaStream_t st);
+// Three-level table (768 entries) of w^e, w = exp(sign 2 pi i / 2^logn), e < 2^24.
+cudaError_t launch_tw3(float2* out, int logn, int sign, cudaStream_t st);
 cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st);
 int stage_tw_entries(int R);
 cudaError_t launch_fwd_cols(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st);
-cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, Tw2 twL, Tw2 tw2L, const float2* tw,
+cudaError_t launch_fwd_rows(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L, const float2* tw,
                             cudaStream_t st);
-cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, Tw2 twM, const ChirpAnchor* anc,
+cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, const ChirpAnchor* anc,
                             int clog, const float2* tw, cudaStream_t st);
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
-                            long long vofs, int m_lo, int m_hi, const float2* tw, cudaStream_t st);
+                            long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
+                               cudaStream_t st);
 size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,
