@@ -362,7 +362,7 @@ def run_precision(args, rank, ws, dist):
     peaks = measured_peaks()
     achieved = stages[dom]["algo_bytes"] / (stages[dom]["ms"] / stages[dom]["launches"] / 1e3) / 1e9
     kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
-             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_partial", "decimate": "k_decimate"}[dom]
+             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_dec", "decimate": "k_decimate"}[dom]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname + " (tensor-core form)",
             "peak_src": peaks["src"],
@@ -466,14 +466,14 @@ def run_learned(args, rank):
 
     pbuild.build()
     t0 = time.perf_counter()
-    Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000)
-    Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000)
+    Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000, shifts=args.shifts)
+    Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000, shifts=args.shifts)
     gen_s = time.perf_counter() - t0
     theta = _cnn_init.init_params(synth.uniform(99, 0, 0, _cnn_init.n_params())).astype(np.float32)
     clf = pond.Classifier(theta, max_batch=512)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = learn.train(clf, Xtr, Ytr, epochs=30, batch=256, lr=2e-3, seed=3)
+    hist = learn.train(clf, Xtr, Ytr, epochs=args.epochs, batch=256, lr=2e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     res = learn.evaluate(learn.predict(clf, Xte), Yte, Fte)
@@ -483,7 +483,8 @@ def run_learned(args, rank):
             "unit": "candidates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "learned: DM-time patches (32 trials x 256 samples of 32 us) from the batched "
                                    "engine on labelled 8 s chunks; pulse / DM-0 burst / narrowband / noise",
-                       "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)), "epochs": 30,
+                       "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)), "epochs": args.epochs,
+                       "shifts_per_event": args.shifts, "train_chunks": args.chunks,
                        "batch": 256, "lr": 2e-3},
             "evaluation": res, "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
             "dataset_s": gen_s}
@@ -498,11 +499,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cufft-baseline", action="store_true")
     ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned", "precision"],
                     help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks; "
                          "learned: classifier training and evaluation beside the boxcar detector; "
                          "precision: split-BF16 tensor-core FFT stages vs the FP32 path and the oracle")
     ap.add_argument("--chunks", type=int, default=40, help="learned: 8 s training chunks")
+    ap.add_argument("--shifts", type=int, default=16, help="learned: time-shifted patches per event")
+    ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x5"],
                     help="full-rate: arithmetic of the radix-16 FFT stages (FP32, or split-BF16 tensor-core "
                          "DFT products with three or five terms)")
@@ -578,11 +582,32 @@ def main():
     avg_s = stages[dom]["ms"] / stages[dom]["launches"] / 1e3
     achieved = stages[dom]["algo_bytes"] / avg_s / 1e9
     kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
-             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_partial", "decimate": "k_decimate"}[dom]
+             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_dec", "decimate": "k_decimate"}[dom]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profiles(kname),
             "kernel": kname, "peak_src": peaks["src"],
             "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in stages.items()}}
+
+    # the cuFFT comparison path on the same device-resident stream (one warm-up, one timed step)
+    cufft = None
+    if rank == 0 and not args.no_cufft_baseline:
+        from baseline.cufft_path import CufftPath
+        cp = CufftPath(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                       PLAN["t_dec"], dev)
+        cp.run(x_dev)
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cp.run(x_dev)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        cufft = {"value": n / (cms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": cms,
+                 "kind": "cuFFT R2C + inverse-filter multiply + batched C2C inverse (torch.fft) + torch detect, "
+                         "fold, decimate; same outputs (tests/test_gpu_cufft_baseline.py)",
+                 "engine_speedup": (value / ws) / (n / (cms / 1e3) / 1e6)}
+        del cp
 
     # end to end through pond_push from pinned host memory, results read back
     x_host = torch.empty(n, dtype=torch.int8, pin_memory=True)
@@ -628,7 +653,7 @@ def main():
                 "data": "synthetic", "config": dict(workload_config(n), fft_stages=args.precision),
                 "realtime_factor": value / REALTIME_MSPS,
                 "e2e": e2e, "gpu_launches": int(st1["kernel_launches"]) * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+                "roofline": roof, "cpu_baseline": cpu, "cufft_baseline": cufft, "clocks": clocks}
         print(json.dumps(line), flush=True)
     eng.close()
     eng_h.close()

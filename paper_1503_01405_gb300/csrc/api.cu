@@ -146,8 +146,8 @@ struct pond_s {
   // fold (single-DM plans)
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
-  double* psum = nullptr;
-  int* phits = nullptr;
+  double* psum = nullptr;                   // per-CTA fold partials, accumulated over the stream
+  long long* phits = nullptr;
   // time series rings: [ntrial][ring] sums and counts
   long long ring = 0;
   float* ts = nullptr;
@@ -480,13 +480,17 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, h->st));
     if (q == 0) RC(record(h, 1 + ST_I2));
     if (!h->multi) {
-      CK(launch_fold(ln.P, nv, g0, h->inc, h->nbins, h->psum, h->phits, h->prof_sum, h->prof_hits, h->st));
+      // fold and decimation in one launch; the profile is merged when read
+      CK(launch_fold_dec(ln.P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                         h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum, h->phits,
+                         h->st));
       RC(record(h, 1 + ST_FOLD));
-      h->launches += 2;
+      RC(record(h, 1 + ST_DEC, true));
+    } else {
+      CK(launch_decimate(ln.P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
+                         h->ts_cnt + (size_t)d * h->ring, h->ring, h->st));
+      if (q == 0) RC(record(h, 1 + ST_DEC, true));
     }
-    CK(launch_decimate(ln.P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
-                       h->ts_cnt + (size_t)d * h->ring, h->ring, h->st));
-    if (q == 0) RC(record(h, 1 + ST_DEC, true));
     h->launches += 3;
   }
   if (h->want_voltages) h->v_len += nv;
@@ -849,9 +853,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     CKD(cudaMalloc(&h->prof_sum, h->nbins * sizeof(double)));
     CKD(cudaMalloc(&h->prof_hits, h->nbins * sizeof(long long)));
     CKD(cudaMalloc(&h->psum, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(double)));
-    CKD(cudaMalloc(&h->phits, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(int)));
+    CKD(cudaMalloc(&h->phits, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(long long)));
     CKD(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
     CKD(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
+    CKD(cudaMemsetAsync(h->psum, 0, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(double), h->st));
+    CKD(cudaMemsetAsync(h->phits, 0, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(long long), h->st));
   }
   if (h->want_voltages) {
     h->v_cap = std::max<long long>(4 * h->lanes[0].g.S_c, 1 << 16);
@@ -988,6 +994,8 @@ int pond_reset(pond_t h) {
   if (!h->multi) {
     CK(cudaMemsetAsync(h->prof_sum, 0, h->nbins * sizeof(double), h->st));
     CK(cudaMemsetAsync(h->prof_hits, 0, h->nbins * sizeof(long long), h->st));
+    CK(cudaMemsetAsync(h->psum, 0, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(double), h->st));
+    CK(cudaMemsetAsync(h->phits, 0, (size_t)MAX_FOLD_PARTS * h->nbins * sizeof(long long), h->st));
   }
   CK(cudaMemsetAsync(h->ts, 0, (size_t)ntr * h->ring * sizeof(float), h->st));
   CK(cudaMemsetAsync(h->ts_cnt, 0, (size_t)ntr * h->ring * sizeof(int), h->st));
@@ -1016,6 +1024,7 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta) {
   if (!h) return fail(POND_E_ARG, "null handle");
   if (h->multi) return fail(POND_E_STATE, "a batched plan does not fold");
   CK(cudaSetDevice(h->device));
+  CK(launch_fold_snapshot(h->psum, h->phits, h->nbins, h->prof_sum, h->prof_hits, h->st));
   if (sum) CK(cudaMemcpyAsync(sum, h->prof_sum, h->nbins * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (hits) CK(cudaMemcpyAsync(hits, h->prof_hits, h->nbins * sizeof(long long), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));

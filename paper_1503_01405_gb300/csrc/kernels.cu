@@ -139,25 +139,12 @@ __device__ __forceinline__ int fold_bin(long long g, double inc, int nbins) {
   return b < nbins - 1 ? b : nbins - 1;
 }
 
-__global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* __restrict__ P, long long n,
-                                                                  long long g0, double inc, int nbins,
-                                                                  long long chunk, double* __restrict__ psum,
-                                                                  int* __restrict__ phits) {
-  extern __shared__ unsigned char fsm[];
-  double* hsum = reinterpret_cast<double*>(fsm);                  // [FOLD_WARPS][nbins]
-  int* hcnt = reinterpret_cast<int*>(hsum + FOLD_WARPS * nbins);  // [FOLD_WARPS][nbins]
-  float* pbuf = reinterpret_cast<float*>(hcnt + FOLD_WARPS * nbins);  // [FOLD_WARPS][32]
-  for (int i = threadIdx.x; i < FOLD_WARPS * nbins; i += blockDim.x) {
-    hsum[i] = 0.0;
-    hcnt[i] = 0;
-  }
-  __syncthreads();
+// Fold channel samples [c0, c1) of P (global index g0 + c) into this warp's
+// histogram (FOLD_WARPS warps share the chunk: warp w takes groups of
+// 32 * FOLD_U samples w, w + FOLD_WARPS, ...).
+__device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long long c0, long long c1, long long g0,
+                                           double inc, int nbins, double* myh, int* myc, float* mybuf) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long c0 = (long long)blockIdx.x * chunk;
-  const long long c1 = min(n, c0 + chunk);
-  double* myh = hsum + w * nbins;
-  int* myc = hcnt + w * nbins;
-  float* mybuf = pbuf + w * 32;
   // FOLD_U groups of 32 samples per warp and iteration: their loads and FP64
   // bin computations are all in flight before the groups are scanned in order
   for (long long base = c0 + (long long)w * 32 * FOLD_U; base < c1; base += FOLD_WARPS * 32 * FOLD_U) {
@@ -212,27 +199,134 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
       __syncwarp();
     }
   }
+}
+
+// Shared-memory layout of the fold kernels: [FOLD_WARPS][nbins] FP64 sums,
+// [FOLD_WARPS][nbins] int32 hits, [FOLD_WARPS][32] FP32 staging.
+struct FoldSmem {
+  double* hsum;
+  int* hcnt;
+  float* pbuf;
+};
+
+__device__ __forceinline__ FoldSmem fold_smem_init(unsigned char* fsm, int nbins) {
+  FoldSmem f;
+  f.hsum = reinterpret_cast<double*>(fsm);
+  f.hcnt = reinterpret_cast<int*>(f.hsum + FOLD_WARPS * nbins);
+  f.pbuf = reinterpret_cast<float*>(f.hcnt + FOLD_WARPS * nbins);
+  for (int i = threadIdx.x; i < FOLD_WARPS * nbins; i += blockDim.x) {
+    f.hsum[i] = 0.0;
+    f.hcnt[i] = 0;
+  }
+  __syncthreads();
+  return f;
+}
+
+// One CTA per chunk of channel samples: the CTA's histogram (warps added in
+// order) is written to row blockIdx.x of the partials.
+__global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* __restrict__ P, long long n,
+                                                                  long long g0, double inc, int nbins,
+                                                                  long long chunk, double* __restrict__ psum,
+                                                                  int* __restrict__ phits) {
+  extern __shared__ unsigned char fsm[];
+  const FoldSmem f = fold_smem_init(fsm, nbins);
+  const int w = threadIdx.x >> 5;
+  const long long c0 = (long long)blockIdx.x * chunk;
+  fold_chunk(P, c0, min(n, c0 + chunk), g0, inc, nbins, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
     double s = 0.0;
     int h = 0;
 #pragma unroll
     for (int k = 0; k < FOLD_WARPS; ++k) {
-      s += hsum[k * nbins + b];
-      h += hcnt[k * nbins + b];
+      s += f.hsum[k * nbins + b];
+      h += f.hcnt[k * nbins + b];
     }
     psum[(size_t)blockIdx.x * nbins + b] = s;
     phits[(size_t)blockIdx.x * nbins + b] = h;
   }
 }
 
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// Fold + decimation of one segment's valid span [g0, g0 + n) in one launch.
+// CTA b owns the series samples j in [j_lo + b jpc, j_lo + (b+1) jpc) and the
+// channel samples they cover: it folds them (its histogram is added to
+// partial row b, which accumulates over the segments of the stream and is
+// merged when the profile is read) and then sums each of its series samples
+// (one thread per j for spans under 64 channel samples, else one warp per j
+// with four partial sums).  Every j belongs to one CTA, so no atomics.
+__global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_dec(const float* __restrict__ P, long long n,
+                                                              long long g0, double inc, int nbins,
+                                                              long long num, long long den, long long j_lo,
+                                                              long long nj, long long jpc,
+                                                              float* __restrict__ T, int* __restrict__ C,
+                                                              long long ring, double* __restrict__ psum,
+                                                              long long* __restrict__ phits) {
+  extern __shared__ unsigned char fsm[];
+  const FoldSmem f = fold_smem_init(fsm, nbins);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ja = j_lo + (long long)blockIdx.x * jpc;
+  const long long jb = min(j_lo + nj, ja + jpc);
+  const long long ga = max(ceil_div_ll(ja * num, den), g0);
+  const long long gb = min(ceil_div_ll(jb * num, den), g0 + n);
+  fold_chunk(P, ga - g0, gb - g0, g0, inc, nbins, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    double s = 0.0;
+    int h = 0;
+#pragma unroll
+    for (int k = 0; k < FOLD_WARPS; ++k) {
+      s += f.hsum[k * nbins + b];
+      h += f.hcnt[k * nbins + b];
+    }
+    psum[(size_t)blockIdx.x * nbins + b] += s;
+    phits[(size_t)blockIdx.x * nbins + b] += h;
+  }
+  if (num < 64 * den) {
+    for (long long j = ja + threadIdx.x; j < jb; j += blockDim.x) {
+      const long long a = max(ceil_div_ll(j * num, den), g0), e = min(ceil_div_ll((j + 1) * num, den), g0 + n);
+      float s = 0.f;
+      for (long long g = a; g < e; ++g) s += __ldg(P + (g - g0));
+      const long long slot = j % ring;
+      T[slot] += s;
+      C[slot] += (int)max(e - a, 0ll);
+    }
+  } else {
+    for (long long j = ja + w; j < jb; j += FOLD_WARPS) {
+      const long long a = max(ceil_div_ll(j * num, den), g0), e = min(ceil_div_ll((j + 1) * num, den), g0 + n);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      long long g = a + lane;
+      for (; g + 96 < e; g += 128) {
+        s0 += __ldg(P + (g - g0));
+        s1 += __ldg(P + (g + 32 - g0));
+        s2 += __ldg(P + (g + 64 - g0));
+        s3 += __ldg(P + (g + 96 - g0));
+      }
+      if (g < e) s0 += __ldg(P + (g - g0));
+      if (g + 32 < e) s1 += __ldg(P + (g + 32 - g0));
+      if (g + 64 < e) s2 += __ldg(P + (g + 64 - g0));
+      float s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+      if (lane == 0) {
+        const long long slot = j % ring;
+        T[slot] += s;
+        C[slot] += (int)max(e - a, 0ll);
+      }
+    }
+  }
+}
+
 // A CTA merges 32 consecutive bins: warp y sums parts y, y + 8, y + 16, ... in
 // order (lanes read 32 consecutive bins of a part: coalesced), then lane x of
-// warp 0 adds the eight warp sums of bin x in a fixed order.
+// warp 0 adds the eight warp sums of bin x in a fixed order.  ACC adds the
+// result to the profile, otherwise it replaces it.
 constexpr int MERGE_WARPS = 8;
 
+template <typename H, bool ACC>
 __global__ void __launch_bounds__(MERGE_WARPS * 32) k_fold_merge(const double* __restrict__ psum,
-                                                                 const int* __restrict__ phits, int nparts,
+                                                                 const H* __restrict__ phits, int nparts,
                                                                  int nbins, double* __restrict__ prof_sum,
                                                                  long long* __restrict__ prof_hits) {
   __shared__ double ss[MERGE_WARPS][32];
@@ -245,7 +339,7 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_fold_merge(const double* _
 #pragma unroll 4
     for (int k = y; k < nparts; k += MERGE_WARPS) {
       s += __ldg(psum + (size_t)k * nbins + b);
-      h += __ldg(phits + (size_t)k * nbins + b);
+      h += (long long)__ldg(phits + (size_t)k * nbins + b);
     }
   }
   ss[y][x] = s;
@@ -255,20 +349,23 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_fold_merge(const double* _
     double t = 0.0;
     long long c = 0;
 #pragma unroll
-    for (int w = 0; w < MERGE_WARPS; ++w) {
-      t += ss[w][x];
-      c += sh[w][x];
+    for (int k = 0; k < MERGE_WARPS; ++k) {
+      t += ss[k][x];
+      c += sh[k][x];
     }
-    prof_sum[b] += t;
-    prof_hits[b] += c;
+    if (ACC) {
+      prof_sum[b] += t;
+      prof_hits[b] += c;
+    } else {
+      prof_sum[b] = t;
+      prof_hits[b] = c;
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Decimation: T[j] += sum of P[g], floor(g den / num) = j; one warp per j
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
 
 // One warp per series sample j (spans of 64 or more channel samples): four
 // independent partial sums keep four loads in flight per lane, combined in a
@@ -356,6 +453,8 @@ cudaError_t set_kernel_attributes() {
   cudaError_t e = set_attributes_t<false>();
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fold_dec, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
   return e;
 }
 
@@ -400,7 +499,29 @@ cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, i
   long long chunk;
   const int parts = fold_parts(n, &chunk);
   k_fold_partial<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, chunk, psum, phits);
-  k_fold_merge<<<(nbins + 31) / 32, MERGE_WARPS * 32, 0, st>>>(psum, phits, parts, nbins, prof_sum, prof_hits);
+  k_fold_merge<int, true><<<(nbins + 31) / 32, MERGE_WARPS * 32, 0, st>>>(psum, phits, parts, nbins, prof_sum,
+                                                                          prof_hits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double inc, int nbins, long long num,
+                            long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
+                            double* psum, long long* phits, cudaStream_t st) {
+  if (n <= 0 || nj <= 0) return cudaSuccess;
+  // whole series samples per CTA: at least 1024 channel samples each, at most MAX_FOLD_PARTS CTAs
+  const long long per_j = std::max(1ll, num / den);
+  long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (1024 + per_j - 1) / per_j);
+  jpc = std::min(jpc, nj);
+  const unsigned parts = (unsigned)((nj + jpc - 1) / jpc);
+  k_fold_dec<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, num, den, j_lo, nj, jpc, T,
+                                                                     C, ring, psum, phits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_snapshot(const double* psum, const long long* phits, int nbins, double* prof_sum,
+                                 long long* prof_hits, cudaStream_t st) {
+  k_fold_merge<long long, false><<<(nbins + 31) / 32, MERGE_WARPS * 32, 0, st>>>(psum, phits, MAX_FOLD_PARTS, nbins,
+                                                                                prof_sum, prof_hits);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,9 @@ __device__ __forceinline__ float2 tw3(const float2* t, unsigned e) {
 }
 
 
+// Offsets into the segment buffers are 32-bit: every buffer holds L <= 2^24
+// elements (nfft <= 2^25).
+
 // Tile entries (float2) a pass allocates for nl lines of length R.  The
 // tensor-core form pads its tile so that the CTA's shared memory (tables +
 // tile + extras) is at least tc::MIN_SMEM_BYTES: then at most two CTAs share
@@ -173,10 +176,12 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   __syncthreads();
   fft_lines<R2, false, TC>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
+  // neighbouring threads take the nl columns of one row, then the next rows:
+  // each warp store fills whole 32-byte sectors
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int k2 = idx >> lognl, b = idx & (nl - 1);
-    out[(size_t)(n1_0 + b) + ((size_t)k2 << logR1)] = sm[pidx(b, k2, LSTR)];
+    out[(unsigned)(n1_0 + b) + ((unsigned)k2 << logR1)] = sm[pidx(b, k2, LSTR)];
   }
 }
 
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
       const int idx = 2 * (threadIdx.x + u * NT);
       if (idx < tot) {
         const unsigned k2 = (unsigned)line_of(idx >> LOGR1), n1 = (unsigned)(idx & (R1 - 1));
-        r[u] = __ldg(in4 + ((((size_t)k2 << LOGR1) + n1) >> 1));
+        r[u] = __ldg(in4 + (((k2 << LOGR1) + n1) >> 1));
       }
     }
     __syncthreads();   // st3 filled
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   // themselves: line 0 pairs columns k1 and R1-k1 (k1 = 0 and R1/2 alone),
   // line R2/2 columns k1 and R1-1-k1.
   const unsigned lmask = (1u << logL) - 1;
-  auto emit = [&](int slot, int k1, float2 X) { out[((size_t)line_of(slot) << LOGR1) + k1] = X; };
+  auto emit = [&](int slot, int k1, float2 X) { out[((unsigned)line_of(slot) << LOGR1) + (unsigned)k1] = X; };
   auto split = [&](int sa, int ka, int sb, int kb, bool both) {
     const unsigned k = (unsigned)line_of(sa) + ((unsigned)ka << logR2);
     const float2 A = sm[pidx(sa, ka, LSTR)];
@@ -334,8 +339,8 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
       const int j2lo = rest & ((1 << s) - 1);
       const int l = l0 + (rest >> s);
       const int c = l >> logQ1, j1 = l & (Q1 - 1);
-      const size_t k1 = ((size_t)c << (logM - logR2)) + j2hi;
-      const size_t k2 = (size_t)j1 + ((size_t)j2lo << logQ1);
+      const unsigned k1 = ((unsigned)c << (logM - logR2)) + (unsigned)j2hi;
+      const unsigned k2 = (unsigned)j1 + ((unsigned)j2lo << logQ1);
       r[u] = in[k1 + (k2 << logR1)];
     }
   }
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
     const int m2 = idx >> lognl, b = idx & (nl - 1);
     const int l = l0 + b;
-    const size_t addr = ((size_t)(l >> logQ1) << logM) + (size_t)(l & (Q1 - 1)) + ((size_t)m2 << logQ1);
+    const unsigned addr = ((unsigned)(l >> logQ1) << logM) + (unsigned)(l & (Q1 - 1)) + ((unsigned)m2 << logQ1);
     out[addr] = sm[pidx(b, m2, LSTR)];
   }
 }
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
     if (idx < tot) {
       const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
       const int c = slot >> logb2, bb = slot & (b2 - 1);
-      r[u] = buf[((size_t)c << logM) + ((size_t)(m2_0 + bb) << LOGQ1) + e];
+      r[u] = buf[((unsigned)c << logM) + ((unsigned)(m2_0 + bb) << LOGQ1) + (unsigned)e];
     }
   }
   __syncthreads();   // st3 filled

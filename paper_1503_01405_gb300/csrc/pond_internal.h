@@ -95,6 +95,14 @@ size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,
                         int* phits, double* prof_sum, long long* prof_hits, cudaStream_t st);
+// Fold + decimation of one segment (single-DM plans): the fold adds to
+// per-CTA partial rows [MAX_FOLD_PARTS][nbins] that accumulate over the
+// stream; launch_fold_snapshot merges them into the profile (replacing it).
+cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double inc, int nbins, long long num,
+                            long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
+                            double* psum, long long* phits, cudaStream_t st);
+cudaError_t launch_fold_snapshot(const double* psum, const long long* phits, int nbins, double* prof_sum,
+                                 long long* prof_hits, cudaStream_t st);
 cudaError_t launch_decimate(const float* P, long long n, long long g0, long long num, long long den,
                             long long j_lo, long long nj, float* T, int* C, long long ring, cudaStream_t st);
 

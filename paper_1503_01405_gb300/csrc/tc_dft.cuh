@@ -164,8 +164,11 @@ constexpr int D_COLS = GROUPS * NCOL;          // 128 accumulator columns
 constexpr int TMEM_ALLOC = 2 * D_COLS;         // + 128 columns of A operands
 constexpr int W_BYTES = TC_W_BYTES;            // W16 hi, mid, lo: 6 KiB
 // Extra dynamic shared memory of a tensor-core kernel after its tile: alignment
-// slack, the W16 parts, the barrier, the TMEM address slot and the fail flag.
-constexpr int EXTRA_BYTES = 1024 + W_BYTES + 64;
+// slack (the no-swizzle operand needs 16-byte alignment; it is placed on a
+// 128-byte core-matrix boundary), the W16 parts, the barrier, the TMEM address
+// slot and the fail flag.  Kept small: F2 at R = 4096 then still fits two CTAs
+// per SM (115,712 bytes each).
+constexpr int EXTRA_BYTES = 128 + W_BYTES + 64;
 // Smallest dynamic shared memory of a tensor-core pass: with more than a third
 // of the SM's shared memory per CTA at most two CTAs (2 x 256 TMEM columns)
 // share an SM, so tcgen05.alloc never waits.  MIN_TILE_F2 counts the float2
@@ -173,15 +176,15 @@ constexpr int EXTRA_BYTES = 1024 + W_BYTES + 64;
 constexpr int MIN_SMEM_BYTES = 78 * 1024;
 constexpr int MIN_TILE_F2 = (MIN_SMEM_BYTES - EXTRA_BYTES + 7) / 8;
 
-__device__ __forceinline__ unsigned char* align1k(void* p) {
-  const uint32_t off = (1024u - (smem_addr(p) & 1023u)) & 1023u;
+__device__ __forceinline__ unsigned char* align128(void* p) {
+  const uint32_t off = (128u - (smem_addr(p) & 127u)) & 127u;
   return static_cast<unsigned char*>(p) + off;
 }
 
 // Allocate tensor memory, initialise the barrier and copy the W16 parts.
 // `tile` holds tile_f2 float2 entries followed by EXTRA_BYTES; all threads call.
 __device__ __forceinline__ void setup(Ctx& c, float2* tile, int tile_f2, const TcArgs& ta) {
-  unsigned char* x = align1k(tile + tile_f2);
+  unsigned char* x = align128(tile + tile_f2);
   unsigned char* bar = x + W_BYTES;
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 8);
   c.fail = reinterpret_cast<int*>(bar + 16);
