@@ -145,7 +145,7 @@ def traffic_from_profiles(kernel: str):
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
-    for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh", "pond_internal.h"):
+    for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh"):
         with open(os.path.join(ROOT, "paper_1503_01405_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     src = h.hexdigest()[:16]

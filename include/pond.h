@@ -320,6 +320,20 @@ int pond_cnn_destroy(pond_cnn_t net);
 int pond_patches(const float* d_series, int32_t ndm, int64_t n, int64_t stride, const int32_t* d_corners,
                  int32_t npatch, void* d_out, void* cuda_stream);
 
+/*
+ * pond_candidates_scored: pond_candidates, then each candidate's patch
+ *   (trials trial-16 .. trial+15, clamped into the block, and series samples
+ *   index-128 .. index+127 of the same undrained block, cut as by
+ *   pond_patches) is classified by net on the handle's device and stream;
+ *   score = the network's probability of the dispersed-pulse class.  net must
+ *   live on the handle's device.  Allocates device scratch for the block, the
+ *   patches (16 KiB each) and the probabilities; batches are at most the
+ *   network's max_batch.  Errors: as pond_candidates; POND_E_ARG for a null
+ *   net.
+ */
+int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand* out, size_t cap,
+                           size_t* n_found);
+
 /* pond_stats: counters and per-stage GPU times (waits for the device). */
 int pond_stats(pond_t h, pond_stats_t* s);
 

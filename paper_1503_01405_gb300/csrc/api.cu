@@ -1093,7 +1093,10 @@ int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntria
   return POND_OK;
 }
 
-int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found) {
+// Boxcar candidates over the undrained series block; with net, each is scored
+// by the classifier on its patch of the same block.
+static int candidates_impl(pond_t h, pond_cnn_t net, double threshold, pond_cand* out, size_t cap,
+                           size_t* n_found) {
   if (!h || !n_found || (cap > 0 && !out)) return fail(POND_E_ARG, "null argument");
   CK(cudaSetDevice(h->device));
   *n_found = 0;
@@ -1119,14 +1122,61 @@ int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size
     cudaFree(blk);
     return fail(POND_E_CUDA, "gather series: %s", cudaGetErrorString(e));
   }
-  const int rc = run_boxcar(blk, ntr, n, n, threshold, out, cap, n_found, h->st);
-  cudaFree(blk);
+  int rc = run_boxcar(blk, ntr, n, n, threshold, out, cap, n_found, h->st);
   const size_t m = std::min(*n_found, cap);
+  if (net && m > 0 && (rc == POND_OK || rc == POND_E_OVERRUN)) {
+    const int maxb = cnn_max_batch(net);
+    std::vector<int32_t> corners(2 * m);
+    for (size_t i = 0; i < m; ++i) {
+      corners[2 * i] = std::max(0, std::min(out[i].trial - 16, std::max(ntr - 32, 0)));
+      corners[2 * i + 1] = (int32_t)(out[i].index - 128);
+    }
+    int32_t* d_corners = nullptr;
+    void* d_patch = nullptr;
+    float* d_prob = nullptr;
+    const size_t patch_bytes = 32 * 256 * 2;
+    e = cudaMalloc(&d_corners, corners.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_patch, (size_t)maxb * patch_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_prob, m * 4 * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_corners, corners.data(), corners.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+    int rs = e == cudaSuccess ? POND_OK : fail(POND_E_CUDA, "score scratch: %s", cudaGetErrorString(e));
+    for (size_t b = 0; b < m && rs == POND_OK; b += (size_t)maxb) {
+      const int nb = (int)std::min<size_t>((size_t)maxb, m - b);
+      rs = pond_patches(blk, ntr, n, n, d_corners + 2 * b, nb, d_patch, h->st);
+      if (rs == POND_OK) rs = pond_cnn_forward(net, d_patch, nb, d_prob + 4 * b, h->st);
+    }
+    std::vector<float> prob(m * 4);
+    if (rs == POND_OK) {
+      e = cudaMemcpyAsync(prob.data(), d_prob, m * 4 * sizeof(float), cudaMemcpyDeviceToHost, h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      if (e != cudaSuccess) rs = fail(POND_E_CUDA, "scores: %s", cudaGetErrorString(e));
+    }
+    cudaFree(d_corners);
+    cudaFree(d_patch);
+    cudaFree(d_prob);
+    if (rs != POND_OK) {
+      cudaFree(blk);
+      return rs;
+    }
+    for (size_t i = 0; i < m; ++i) out[i].score = prob[4 * i];
+  }
+  cudaFree(blk);
   for (size_t i = 0; i < m; ++i) {
     out[i].index += j0;
     out[i].dm = h->trials[out[i].trial].dm;
   }
   return rc;
+}
+
+int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found) {
+  return candidates_impl(h, nullptr, threshold, out, cap, n_found);
+}
+
+int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand* out, size_t cap,
+                           size_t* n_found) {
+  if (!net) return fail(POND_E_ARG, "pond_candidates_scored: null network");
+  return candidates_impl(h, net, threshold, out, cap, n_found);
 }
 
 int pond_stats(pond_t h, pond_stats_t* s) {

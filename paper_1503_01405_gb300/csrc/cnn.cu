@@ -140,6 +140,8 @@ int check_batch(pond_cnn_t n, const void* x, int B) {
 
 }  // namespace
 
+int pond::cnn_max_batch(pond_cnn_t n) { return n ? n->max_batch : 0; }
+
 extern "C" {
 
 int pond_cnn_create(pond_cnn_t* out, const float* init_params, int32_t max_batch, int32_t device) {

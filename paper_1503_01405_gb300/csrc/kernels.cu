@@ -141,9 +141,11 @@ __device__ __forceinline__ int fold_bin(long long g, double inc, int nbins) {
 
 // Fold channel samples [c0, c1) of P (global index g0 + c) into this warp's
 // histogram (FOLD_WARPS warps share the chunk: warp w takes groups of
-// 32 * FOLD_U samples w, w + FOLD_WARPS, ...).
+// 32 * FOLD_U samples w, w + FOLD_WARPS, ...).  Bin b is kept at entry
+// (b - b0) mod nbins, so a chunk that spans a short cyclic run of bins starting
+// at b0 needs only that run's entries.
 __device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long long c0, long long c1, long long g0,
-                                           double inc, int nbins, double* myh, int* myc, float* mybuf) {
+                                           double inc, int nbins, int b0, double* myh, int* myc, float* mybuf) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // FOLD_U groups of 32 samples per warp and iteration: their loads and FP64
   // bin computations are all in flight before the groups are scanned in order
@@ -178,8 +180,9 @@ __device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long lon
           if (lane - d >= first) x += y;
         }
         if (ok && lane == last) {
-          myh[b] += (double)x;
-          myc[b] += last - first + 1;
+          const int e = b >= b0 ? b - b0 : b - b0 + nbins;
+          myh[e] += (double)x;
+          myc[e] += last - first + 1;
         }
       } else {
         // a period shorter than a warp: the group leader sums its lanes in order
@@ -192,8 +195,9 @@ __device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long lon
             sum += mybuf[__ffs(m) - 1];
             m &= m - 1;
           }
-          myh[b] += (double)sum;
-          myc[b] += __popc(peers);
+          const int e = b >= b0 ? b - b0 : b - b0 + nbins;
+          myh[e] += (double)sum;
+          myc[e] += __popc(peers);
         }
       }
       __syncwarp();
@@ -209,14 +213,15 @@ struct FoldSmem {
   float* pbuf;
 };
 
-__device__ __forceinline__ FoldSmem fold_smem_init(unsigned char* fsm, int nbins) {
+__device__ __forceinline__ FoldSmem fold_smem_init(unsigned char* fsm, int nbins, int used) {
   FoldSmem f;
   f.hsum = reinterpret_cast<double*>(fsm);
   f.hcnt = reinterpret_cast<int*>(f.hsum + FOLD_WARPS * nbins);
   f.pbuf = reinterpret_cast<float*>(f.hcnt + FOLD_WARPS * nbins);
-  for (int i = threadIdx.x; i < FOLD_WARPS * nbins; i += blockDim.x) {
-    f.hsum[i] = 0.0;
-    f.hcnt[i] = 0;
+  for (int i = threadIdx.x; i < FOLD_WARPS * used; i += blockDim.x) {
+    const int k = (i / used) * nbins + i % used;
+    f.hsum[k] = 0.0;
+    f.hcnt[k] = 0;
   }
   __syncthreads();
   return f;
@@ -229,10 +234,11 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
                                                                   long long chunk, double* __restrict__ psum,
                                                                   int* __restrict__ phits) {
   extern __shared__ unsigned char fsm[];
-  const FoldSmem f = fold_smem_init(fsm, nbins);
+  const FoldSmem f = fold_smem_init(fsm, nbins, nbins);
   const int w = threadIdx.x >> 5;
   const long long c0 = (long long)blockIdx.x * chunk;
-  fold_chunk(P, c0, min(n, c0 + chunk), g0, inc, nbins, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
+  fold_chunk(P, c0, min(n, c0 + chunk), g0, inc, nbins, 0, f.hsum + w * nbins, f.hcnt + w * nbins,
+             f.pbuf + w * 32);
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
     double s = 0.0;
@@ -264,22 +270,31 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_dec(const float* __res
                                                               long long ring, double* __restrict__ psum,
                                                               long long* __restrict__ phits) {
   extern __shared__ unsigned char fsm[];
-  const FoldSmem f = fold_smem_init(fsm, nbins);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ja = j_lo + (long long)blockIdx.x * jpc;
   const long long jb = min(j_lo + nj, ja + jpc);
   const long long ga = max(ceil_div_ll(ja * num, den), g0);
   const long long gb = min(ceil_div_ll(jb * num, den), g0 + n);
-  fold_chunk(P, ga - g0, gb - g0, g0, inc, nbins, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
+  // the phase grows with g, so a chunk shorter than one period (with a margin
+  // of two bins) covers the cyclic run of bins fold_bin(ga) .. fold_bin(gb - 1)
+  int b0 = 0, used = nbins;
+  if (gb > ga && (double)(gb - 1 - ga) * inc < 1.0 - 2.0 / nbins) {
+    b0 = fold_bin(ga, inc, nbins);
+    const int b1 = fold_bin(gb - 1, inc, nbins);
+    used = (b1 >= b0 ? b1 - b0 : b1 - b0 + nbins) + 1;
+  }
+  const FoldSmem f = fold_smem_init(fsm, nbins, used);
+  fold_chunk(P, ga - g0, gb - g0, g0, inc, nbins, b0, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
   __syncthreads();
-  for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+  for (int e = threadIdx.x; e < used; e += blockDim.x) {
     double s = 0.0;
     int h = 0;
 #pragma unroll
     for (int k = 0; k < FOLD_WARPS; ++k) {
-      s += f.hsum[k * nbins + b];
-      h += f.hcnt[k * nbins + b];
+      s += f.hsum[k * nbins + e];
+      h += f.hcnt[k * nbins + e];
     }
+    const int b = b0 + e < nbins ? b0 + e : b0 + e - nbins;
     psum[(size_t)blockIdx.x * nbins + b] += s;
     phits[(size_t)blockIdx.x * nbins + b] += h;
   }
@@ -508,9 +523,9 @@ cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double in
                             long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
                             double* psum, long long* phits, cudaStream_t st) {
   if (n <= 0 || nj <= 0) return cudaSuccess;
-  // whole series samples per CTA: at least 1024 channel samples each, at most MAX_FOLD_PARTS CTAs
+  // whole series samples per CTA: at least 256 channel samples each, at most MAX_FOLD_PARTS CTAs
   const long long per_j = std::max(1ll, num / den);
-  long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (1024 + per_j - 1) / per_j);
+  long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (256 + per_j - 1) / per_j);
   jpc = std::min(jpc, nj);
   const unsigned parts = (unsigned)((nj + jpc - 1) / jpc);
   k_fold_dec<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, num, den, j_lo, nj, jpc, T,

@@ -68,6 +68,8 @@ struct Geom {
 };
 
 cudaError_t set_kernel_attributes();
+// Largest batch a classifier accepts (its scratch size).
+int cnn_max_batch(pond_cnn_t net);
 cudaError_t set_kernel_attributes_tc();
 // W16 parts for the tensor-core stages, host-built: [fwd, inv][hi, mid, lo] in
 // the K-major operand layout (2 x 6 KiB).

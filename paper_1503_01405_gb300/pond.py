@@ -38,7 +38,7 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
            "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials",
-           "pond_boxcar", "pond_candidates", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
+           "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches"]
 
 
@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "pond_boxcar": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp,
                         ctypes.c_size_t, P(ctypes.c_size_t), vp],
         "pond_candidates": [vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
+        "pond_candidates_scored": [vp, vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
         "pond_cnn_create": [P(vp), vp, ctypes.c_int32, ctypes.c_int32],
         "pond_cnn_set_params": [vp, vp],
         "pond_cnn_params": [vp, vp],
@@ -253,11 +254,16 @@ class Engine:
         C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
         return (T if self.ndm else T[0]), C, first
 
-    def candidates(self, threshold: float = 6.0, cap: int = 1 << 16):
-        """Boxcar candidates over the completed, undrained series: list of dicts."""
+    def candidates(self, threshold: float = 6.0, cap: int = 1 << 16, classifier=None):
+        """Boxcar candidates over the completed, undrained series: list of dicts.
+        With ``classifier`` (a Classifier on the same device) each candidate's
+        score is the network's dispersed-pulse probability for its patch."""
         out = (pond_cand * cap)()
         n = ctypes.c_size_t()
-        _check(lib().pond_candidates(self._h, threshold, out, cap, ctypes.byref(n)))
+        if classifier is None:
+            _check(lib().pond_candidates(self._h, threshold, out, cap, ctypes.byref(n)))
+        else:
+            _check(lib().pond_candidates_scored(self._h, classifier.handle, threshold, out, cap, ctypes.byref(n)))
         return [cand_dict(out[i]) for i in range(n.value)]
 
     def trials(self):
@@ -330,6 +336,10 @@ class Classifier:
         _check(lib().pond_cnn_create(ctypes.byref(h), _ptr(p), max_batch, device))
         self._h = h
         self.max_batch = max_batch
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
 
     def params(self) -> np.ndarray:
         out = np.zeros(CNN_NPARAM, np.float32)

@@ -41,3 +41,35 @@ def test_learned_pipeline_small():
     clf.close()
     assert hist[-1] < hist[0]
     assert res["cnn_accuracy_4class"] > 0.5, res
+
+
+def test_scored_candidates_match_patches_and_forward():
+    """pond_candidates_scored = the boxcar candidates, each scored by the network
+    on its patch of the same series block: bit-identical to cutting the patches
+    with pond_patches and running pond_cnn_forward separately."""
+    import torch
+    dev = torch.device("cuda", 0)
+    dms = learn.trial_grid(48, 30.0)
+    spec = synth.StreamSpec(n=int(3.0 * learn.FS), seed=77, dm=0.0, period=0.0, snr=0.0)
+    events = [e for e in synth.draw_events(78, 8, 3.0, dm_max=dms[-1])]
+    x = synth.make_labelled_chunk_torch(spec, events, dev)
+    theta = cnn.init_params(synth.uniform(19, 0, 0, cnn.n_params())).astype(np.float32)
+    clf = pond.Classifier(theta, max_batch=7)          # several batches
+    with learn.make_engine(dms) as e:
+        e.push_tensor(x)
+        e.flush()
+        scored = e.candidates(6.0, classifier=clf)
+        plain = e.candidates(6.0)
+        T, _, j0 = e.timeseries()
+    assert len(scored) == len(plain) > 0
+    for a, b in zip(scored, plain):
+        assert (a["trial"], a["index"], a["width"], a["snr"]) == (b["trial"], b["index"], b["width"], b["snr"])
+        assert b["score"] == -1.0 and 0.0 <= a["score"] <= 1.0
+    ndm = T.shape[0]
+    corners = np.array([[min(max(c["trial"] - 16, 0), max(ndm - 32, 0)), c["index"] - j0 - 128] for c in plain],
+                       np.int32)
+    series = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).to(dev)
+    X = pond.patches(series, torch.from_numpy(corners).to(dev))
+    prob = learn.predict(clf, X)
+    clf.close()
+    assert np.array_equal(np.array([c["score"] for c in scored], np.float32), prob[:, 0].astype(np.float32))
