@@ -11,8 +11,10 @@
 // DFT in natural order.
 //
 // Shared-memory layout: line b, element e lives at b*LSTR + e + e/16 with
-// LSTR = R + R/16 + 1 (odd), so that both line-major and element-major sweeps
-// of 8-byte elements avoid bank conflicts.
+// LSTR = R + R/16 + 1 (odd) by default, so that both line-major and
+// element-major sweeps of 8-byte elements avoid bank conflicts; a pass whose
+// epilogue sweeps a few lines at a time may use R + R/16 + 16/nl instead
+// (the stages sweep along lines and accept any stride).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -168,9 +170,8 @@ __device__ __forceinline__ void load_twiddles(float2* stw, const float2* __restr
   }
 }
 
-template <int R, int RAD, int LS, bool INV>
+template <int R, int RAD, int LS, bool INV, int LSTR = line_stride(R)>
 __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* stw) {
-  constexpr int LSTR = line_stride(R);
   constexpr int NB = R / RAD;        // butterflies per line
   constexpr int BPT = 16 / RAD;      // butterflies per thread for a full tile
   constexpr int LOGNB = ilog2c(NB);
@@ -226,12 +227,12 @@ __device__ __forceinline__ void stockham_stage(float2* s, int nl, const float2* 
   __syncthreads();
 }
 
-template <int R, int LS, bool INV> struct Stages {
+template <int R, int LS, bool INV, int LSTR = line_stride(R)> struct Stages {
   static __device__ __forceinline__ void run(float2* s, int nl, const float2* stw) {
     if constexpr (LS < R) {
       constexpr int RAD = stage_radix(R, LS);
-      stockham_stage<R, RAD, LS, INV>(s, nl, stw);
-      Stages<R, LS * RAD, INV>::run(s, nl, stw);
+      stockham_stage<R, RAD, LS, INV, LSTR>(s, nl, stw);
+      Stages<R, LS * RAD, INV, LSTR>::run(s, nl, stw);
     }
   }
 };

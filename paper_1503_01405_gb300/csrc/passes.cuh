@@ -91,12 +91,18 @@ __device__ __forceinline__ float2 tw3(const float2* t, unsigned e) {
 // tensor-core form pads its tile so that the CTA's shared memory (tables +
 // tile + extras) is at least tc::MIN_SMEM_BYTES: then at most two CTAs share
 // an SM and their 2 x 256 TMEM columns always fit.
-template <int R, bool TC>
+template <int R, bool TC, int LS = line_stride(R)>
 __host__ __device__ constexpr int tile_f2(int nl) {
-  return TC ? (nl * line_stride(R) > tc::MIN_TILE_F2 - stage_table_size(R)
-                   ? nl * line_stride(R)
-                   : tc::MIN_TILE_F2 - stage_table_size(R))
-            : nl * line_stride(R);
+  return TC ? (nl * LS > tc::MIN_TILE_F2 - stage_table_size(R) ? nl * LS : tc::MIN_TILE_F2 - stage_table_size(R))
+            : nl * LS;
+}
+
+// F1's line stride: its epilogue reads TILE/R lines x (16 R / TILE) consecutive
+// elements per half-warp, which fall in distinct banks when the stride is
+// 16 R / TILE (mod 16) in 8-byte words.
+template <int R>
+__host__ __device__ constexpr int f1_stride() {
+  return R + R / 16 + (TILE / R >= 16 ? 1 : 16 / (TILE / R));
 }
 
 // ---------------------------------------------------------------------------
@@ -118,14 +124,14 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   extern __shared__ float2 smem[];
   float2* stw = smem;
   float2* sm = smem + stage_table_size(R2);
-  constexpr int LSTR = line_stride(R2);
+  constexpr int LSTR = f1_stride<R2>();
   const int R1 = 1 << logR1;
   const int nl = min(TILE / R2, R1);
   const int lognl = __ffs(nl) - 1;
   const int tot = nl * R2;
   load_twiddles<R2>(stw, tw);
   tc::Ctx tcc;
-  if constexpr (TC) tc::setup(tcc, sm, tile_f2<R2, TC>(nl), tca);
+  if constexpr (TC) tc::setup(tcc, sm, tile_f2<R2, TC, LSTR>(nl), tca);
   const int tile = blockIdx.x;
   const int n1_0 = tile * nl;
   if (in.vec8) {
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
     }
   }
   __syncthreads();
-  fft_lines<R2, false, TC>(sm, nl, stw, &tcc);
+  fft_lines<R2, false, TC, LSTR>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
   // neighbouring threads take the nl columns of one row, then the next rows:
   // each warp store fills whole 32-byte sectors
@@ -457,9 +463,9 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
 // ---------------------------------------------------------------------------
 
 // Stage twiddle tables + padded tile (+ the tensor-core extras).
-template <int R, bool TC>
+template <int R, bool TC, int LS = line_stride(R)>
 size_t smem_bytes(int nl) {
-  return ((size_t)stage_table_size(R) + (size_t)tile_f2<R, TC>(nl)) * sizeof(float2) +
+  return ((size_t)stage_table_size(R) + (size_t)tile_f2<R, TC, LS>(nl)) * sizeof(float2) +
          (TC ? (size_t)tc::EXTRA_BYTES : 0);
 }
 
@@ -469,7 +475,7 @@ size_t smem_bytes(int nl) {
 template <bool TC>
 size_t max_smem_t() {
   size_t m = 0;
-#define MAXS(R) m = std::max(m, smem_bytes<R, TC>(TILE / R));
+#define MAXS(R) m = std::max(m, std::max(smem_bytes<R, TC>(TILE / R), smem_bytes<R, TC, f1_stride<R>()>(TILE / R)));
   POND_FOR_R(MAXS)
 #undef MAXS
   return m;
@@ -496,7 +502,7 @@ cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, const float2
   const int nl = std::min(TILE / R2, R1);
   const unsigned grid = (unsigned)(R1 / nl);
   switch (R2) {
-#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl), st>>>(in, out, g.logR1, tw, g.tc_fwd); break;
+#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC, f1_stride<R>()>(nl), st>>>(in, out, g.logR1, tw, g.tc_fwd); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;

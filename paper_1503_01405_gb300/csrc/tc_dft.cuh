@@ -271,9 +271,8 @@ __device__ __forceinline__ void issue(const Ctx& c) {
 // One radix-16 Stockham stage (same data movement as stockham_stage) whose
 // 16-point DFTs run on the tensor cores; one butterfly per thread, whose row
 // of A and D is the thread's own TMEM lane.
-template <int R, int LS, bool INV>
+template <int R, int LS, bool INV, int LSTR = line_stride(R)>
 __device__ __forceinline__ void stage16(float2* s, int nl, const float2* stw, Ctx& c) {
-  constexpr int LSTR = line_stride(R);
   constexpr int NB = R / 16;
   constexpr int LOGNB = ilog2c(NB);
   const int total = nl * NB;
@@ -339,22 +338,22 @@ __device__ __forceinline__ void stage16(float2* s, int nl, const float2* stw, Ct
 
 }  // namespace tc
 
-template <int R, int LS, bool INV, bool TC> struct StagesSel {
+template <int R, int LS, bool INV, bool TC, int LSTR> struct StagesSel {
   static __device__ __forceinline__ void run(float2* s, int nl, const float2* stw, tc::Ctx* c) {
     if constexpr (LS < R) {
       constexpr int RAD = stage_radix(R, LS);
-      if constexpr (TC && RAD == 16) tc::stage16<R, LS, INV>(s, nl, stw, *c);
-      else stockham_stage<R, RAD, LS, INV>(s, nl, stw);
-      StagesSel<R, LS * RAD, INV, TC>::run(s, nl, stw, c);
+      if constexpr (TC && RAD == 16) tc::stage16<R, LS, INV, LSTR>(s, nl, stw, *c);
+      else stockham_stage<R, RAD, LS, INV, LSTR>(s, nl, stw);
+      StagesSel<R, LS * RAD, INV, TC, LSTR>::run(s, nl, stw, c);
     }
   }
 };
 
 // block_fft with the radix-16 stages on the tensor cores when TC (the radix-2/4/8
 // stage of a length that is not a power of 16 stays on the FP32 path).
-template <int R, bool INV, bool TC>
+template <int R, bool INV, bool TC, int LSTR = line_stride(R)>
 __device__ __forceinline__ void fft_lines(float2* s, int nl, const float2* stw, tc::Ctx* c) {
-  StagesSel<R, 1, INV, TC>::run(s, nl, stw, c);
+  StagesSel<R, 1, INV, TC, LSTR>::run(s, nl, stw, c);
 }
 
 }  // namespace pond

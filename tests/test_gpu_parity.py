@@ -82,6 +82,9 @@ CONFIGS = [
     (1 << 20, 8, 2.0, -16.0, 512, 0.1),
     (1 << 12, 2, 0.0, 16.0, 1, 0.01),
     (1 << 15, 512, 0.0, 16.0, 32, 0.02),
+    # fold periods shorter than a warp's 32 channel samples (64 channels: 4 us each)
+    (1 << 14, 64, 0.01, 16.0, 16, 8e-5),     # 20 samples, bins of 1.25 samples
+    (1 << 14, 64, 0.01, 16.0, 8, 1.6e-4),    # 40 samples
 ]
 
 
