@@ -334,6 +334,18 @@ int pond_patches(const float* d_series, int32_t ndm, int64_t n, int64_t stride, 
 int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand* out, size_t cap,
                            size_t* n_found);
 
+/*
+ * pond_check_bounded_wait: self-check of the bounded device wait the
+ *   tensor-core stages use for their MMA completions.  One CTA on `device`
+ *   waits on a barrier that nothing ever arrives on, polling it against the
+ *   GPU's global timer with a limit of limit_s seconds (0 < limit_s <= 10);
+ *   *waited_s receives how long it waited.  Returns POND_E_TIMEOUT when the
+ *   wait gave up (the expected result: the kernel ended by itself and the
+ *   context stays usable), POND_OK if the barrier somehow completed,
+ *   POND_E_ARG or POND_E_CUDA otherwise.
+ */
+int pond_check_bounded_wait(double limit_s, int32_t device, double* waited_s);
+
 /* pond_stats: counters and per-stage GPU times (waits for the device). */
 int pond_stats(pond_t h, pond_stats_t* s);
 

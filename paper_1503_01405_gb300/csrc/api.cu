@@ -1179,6 +1179,27 @@ int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand
   return candidates_impl(h, net, threshold, out, cap, n_found);
 }
 
+int pond_check_bounded_wait(double limit_s, int32_t device, double* waited_s) {
+  if (!(limit_s > 0) || limit_s > 10.0 || !waited_s) return fail(POND_E_ARG, "limit must be in (0, 10] s");
+  CK(cudaSetDevice(device));
+  int* d_status = nullptr;
+  unsigned long long* d_waited = nullptr;
+  CK(cudaMalloc(&d_status, sizeof(int)));
+  cudaError_t e = cudaMalloc(&d_waited, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_wait_probe((unsigned long long)(limit_s * 1e9), d_status, d_waited);
+  int status = 0;
+  unsigned long long waited = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&waited, d_waited, sizeof(waited), cudaMemcpyDeviceToHost);
+  cudaFree(d_status);
+  cudaFree(d_waited);
+  if (e != cudaSuccess) return fail(POND_E_CUDA, "bounded-wait check: %s", cudaGetErrorString(e));
+  *waited_s = (double)waited * 1e-9;
+  if (status) return fail(POND_E_TIMEOUT, "the bounded wait gave up after %.3f s, as it must", *waited_s);
+  return POND_OK;
+}
+
 int pond_stats(pond_t h, pond_stats_t* s) {
   if (!h || !s) return fail(POND_E_ARG, "null argument");
   CK(cudaSetDevice(h->device));

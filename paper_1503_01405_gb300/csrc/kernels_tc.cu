@@ -29,6 +29,26 @@ cudaError_t launch_inv_rows_tc(const Geom& g, const float2* buf, float* P, float
   return launch_inv_rows_t<true>(g, buf, P, vout, vstride, vofs, m_lo, m_hi, tw3M, tw, st);
 }
 
+// One CTA waits, with the tensor-core stages' bounded wait, on a barrier that
+// no thread or MMA ever arrives on: the wait must give up after limit_ns.
+__global__ void k_wait_probe(unsigned long long limit_ns, int* status, unsigned long long* waited) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) tc::mbar_init(tc::smem_addr(&bar), 1);
+  __syncthreads();
+  const unsigned long long t0 = tc::globaltimer_ns();
+  const bool done = tc::mbar_wait(tc::smem_addr(&bar), 0, limit_ns);
+  const unsigned long long t1 = tc::globaltimer_ns();
+  if (threadIdx.x == 0) {
+    *status = done ? 0 : 1;
+    *waited = t1 - t0;
+  }
+}
+
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* status, unsigned long long* waited) {
+  k_wait_probe<<<1, 32>>>(limit_ns, status, waited);
+  return cudaGetLastError();
+}
+
 namespace {
 
 // Round to the nearest BF16 (ties to even) through FP32.

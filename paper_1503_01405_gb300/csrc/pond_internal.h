@@ -71,6 +71,8 @@ cudaError_t set_kernel_attributes();
 // Largest batch a classifier accepts (its scratch size).
 int cnn_max_batch(pond_cnn_t net);
 cudaError_t set_kernel_attributes_tc();
+// One CTA waiting on a barrier nothing arrives on (bounded by limit_ns); status 1 = gave up.
+cudaError_t launch_wait_probe(unsigned long long limit_ns, int* status, unsigned long long* waited);
 // W16 parts for the tensor-core stages, host-built: [fwd, inv][hi, mid, lo] in
 // the K-major operand layout (2 x 6 KiB).
 void build_w16_parts(uint16_t* out);

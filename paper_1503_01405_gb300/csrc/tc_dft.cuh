@@ -84,8 +84,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Wait for the barrier phase `parity` to complete; false when WAIT_NS passes first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the barrier phase `parity` to complete; false when limit_ns passes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = WAIT_NS) {
   unsigned long long t0 = 0;
   for (unsigned i = 0;; ++i) {
     uint32_t done;
@@ -97,7 +97,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (done) return true;
     const unsigned long long t = globaltimer_ns();
     if (i == 0) t0 = t;
-    else if (t - t0 > WAIT_NS) return false;
+    else if (t - t0 > limit_ns) return false;
   }
 }
 

@@ -38,7 +38,7 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_reset",
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
            "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials",
-           "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
+           "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_check_bounded_wait", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches"]
 
 
@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
                         ctypes.c_size_t, P(ctypes.c_size_t), vp],
         "pond_candidates": [vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
         "pond_candidates_scored": [vp, vp, ctypes.c_double, vp, ctypes.c_size_t, P(ctypes.c_size_t)],
+        "pond_check_bounded_wait": [ctypes.c_double, ctypes.c_int32, P(ctypes.c_double)],
         "pond_cnn_create": [P(vp), vp, ctypes.c_int32, ctypes.c_int32],
         "pond_cnn_set_params": [vp, vp],
         "pond_cnn_params": [vp, vp],
@@ -144,6 +145,14 @@ def _check(rc: int) -> None:
 
 def cand_dict(c) -> dict:
     return {"trial": c.trial, "width": c.width, "index": c.index, "snr": c.snr, "dm": c.dm, "score": c.score}
+
+
+def check_bounded_wait(limit_s: float = 0.05, device: int = 0) -> tuple[int, float]:
+    """Run the bounded-wait self-check: (return code, seconds waited).  The
+    expected code is POND_E_TIMEOUT (the wait gave up by itself)."""
+    w = ctypes.c_double()
+    rc = lib().pond_check_bounded_wait(limit_s, device, ctypes.byref(w))
+    return rc, w.value
 
 
 def boxcar(d_series_ptr: int, ndm: int, n: int, stride: int, threshold: float = 6.0, cap: int = 1 << 16,
