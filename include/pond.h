@@ -84,7 +84,9 @@ typedef struct {
   double epoch_mjd_sec; /* ... and seconds into that day (reported in pond_meta) */
   int32_t precision;    /* POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T */
   int32_t want_voltages;/* nonzero: keep dedispersed voltages for pond_voltages (tests) */
-  int32_t timing;       /* nonzero: time each GPU stage with CUDA events (pond_stats) */
+  int32_t timing;       /* nonzero: time each GPU stage with CUDA events (pond_stats); the
+                           segments then run one after another on one stream (without it,
+                           consecutive segments run on two streams and overlap) */
   int32_t device;       /* CUDA device ordinal */
   /* Batched DM trials: ndm > 0 makes a batched plan over dm_list[0..ndm) (dm,
    * period and nbins are then ignored and nothing is folded).  Trials that use

@@ -105,9 +105,12 @@ struct Lane {
   Geom g;
   double dm_max = 0;                        // largest DM of the lane (sets the overlap)
   std::vector<int> trials;
-  float2* bufA = nullptr;
-  float2* bufB = nullptr;
-  float* P = nullptr;
+  // two buffer slots: consecutive segments alternate slots and streams
+  float2* bufA[2] = {nullptr, nullptr};
+  float2* bufB[2] = {nullptr, nullptr};
+  float* P[2] = {nullptr, nullptr};
+  // per trial of the lane and slot: after that trial's fold / decimation of a segment
+  std::vector<cudaEvent_t> ev_chain[2];
   float2* stw = nullptr;                    // stage twiddle tables of R1, R2, Q1, Q2
   const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
   float2* tw2buf = nullptr;
@@ -141,6 +144,8 @@ struct pond_s {
   long long g_first = 0, n_fut_max = 0;     // common emitted range: [g_first, total_c - n_fut_max)
   // streams
   cudaStream_t st = nullptr, cst = nullptr;
+  cudaStream_t st2 = nullptr;               // odd segments (joined into st after every push and flush)
+  cudaEvent_t ev_in = nullptr, ev_join = nullptr;
   cudaEvent_t ev_done = nullptr, ev_caller = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   // fold (single-DM plans)
@@ -294,9 +299,11 @@ int build_lane(pond_t h, Lane* ln) {
     ln->g.tc_inv = {h->wdft + TC_W_BYTES / 16, h->tc_terms, h->tc_err};
   }
   const Geom& g = ln->g;
-  CK(cudaMalloc(&ln->bufA, g.L * sizeof(float2)));
-  CK(cudaMalloc(&ln->bufB, g.L * sizeof(float2)));
-  CK(cudaMalloc(&ln->P, g.M * sizeof(float)));
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&ln->bufA[k], g.L * sizeof(float2)));
+    CK(cudaMalloc(&ln->bufB[k], g.L * sizeof(float2)));
+    CK(cudaMalloc(&ln->P[k], g.M * sizeof(float)));
+  }
   const int n1 = stage_tw_entries(1 << g.logR1), n2 = stage_tw_entries(1 << g.logR2);
   const int n3 = stage_tw_entries(1 << g.logQ1), n4 = stage_tw_entries(1 << g.logQ2);
   CK(cudaMalloc(&ln->stw, (size_t)std::max(1, n1 + n2 + n3 + n4) * sizeof(float2)));
@@ -325,9 +332,13 @@ int build_lane(pond_t h, Lane* ln) {
 }
 
 void free_lane(Lane* ln) {
-  cudaFree(ln->bufA);
-  cudaFree(ln->bufB);
-  cudaFree(ln->P);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(ln->bufA[k]);
+    cudaFree(ln->bufB[k]);
+    cudaFree(ln->P[k]);
+    for (auto e : ln->ev_chain[k]) cudaEventDestroy(e);
+    ln->ev_chain[k].clear();
+  }
   cudaFree(ln->stw);
   cudaFree(ln->tw2buf);
   cudaFree(ln->carry[0]);
@@ -336,7 +347,21 @@ void free_lane(Lane* ln) {
 }
 
 // Record boundary event i of the current segment (0 = before F1, i = after stage i-1).
-int record(pond_t h, int i, bool last = false) {
+// Order everything queued on the second stream before later work on st.
+int join_streams(pond_t h) {
+  CK(cudaEventRecord(h->ev_join, h->st2));
+  CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+  return POND_OK;
+}
+
+// Work on st2 may read what st produced before this point.
+int fork_streams(pond_t h) {
+  CK(cudaEventRecord(h->ev_in, h->st));
+  CK(cudaStreamWaitEvent(h->st2, h->ev_in, 0));
+  return POND_OK;
+}
+
+int record(pond_t h, int i, cudaStream_t cs, bool last = false) {
   if (!h->timing) return POND_OK;
   cudaEvent_t e;
   if (!h->ev_pool.empty()) {
@@ -345,7 +370,7 @@ int record(pond_t h, int i, bool last = false) {
   } else {
     CK(cudaEventCreate(&e));
   }
-  CK(cudaEventRecord(e, h->st));
+  CK(cudaEventRecord(e, cs));
   h->ev_cur.e[i] = e;
   if (last) h->ev_pending.push_back(h->ev_cur);
   return POND_OK;
@@ -353,6 +378,7 @@ int record(pond_t h, int i, bool last = false) {
 
 int collect_timing(pond_t h) {
   if (!h->timing) return POND_OK;
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   for (auto& se : h->ev_pending) {
     for (int i = 0; i < ST_COUNT; ++i) {
@@ -375,6 +401,7 @@ int collect_timing(pond_t h) {
 // Move completed time-series samples of every trial from the device rings to the host.
 int spill_ts(pond_t h) {
   if (h->ts_first < 0 || h->ts_complete <= h->ts_drained) return POND_OK;
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   const long long n = h->ts_complete - h->ts_drained;
   const int ntr = (int)h->trials.size();
@@ -405,6 +432,7 @@ int spill_ts(pond_t h) {
 
 int spill_voltages(pond_t h) {
   if (!h->want_voltages || h->v_len == 0) return POND_OK;
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   if (h->v_host_first < 0) h->v_host_first = h->v_base;
   for (int c = 0; c < h->nchan; ++c) {
@@ -464,33 +492,44 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     in.vec8 = (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
               (in.b_len == 0 || (uintptr_t)in.b % 8 == 0);
   }
+  // consecutive segments alternate buffer slots and streams, so one segment's
+  // passes fill the other's tail waves; fold / decimation stay in segment order.
+  // With per-stage timing everything runs on st, so each stage's events
+  // bracket that stage alone.
+  const int slot = (int)(s & 1);
+  cudaStream_t cs = (slot && !h->timing) ? h->st2 : h->st;
+  float2 *bufA = ln.bufA[slot], *bufB = ln.bufB[slot];
+  float* P = ln.P[slot];
   h->ev_cur = SegEvents{};
-  RC(record(h, 0));
-  CK(launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st));
-  RC(record(h, 1 + ST_F1));
-  CK(launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw3L, ln.tw2L, ln.stwR1, h->st));
-  RC(record(h, 1 + ST_F2));
+  RC(record(h, 0, cs));
+  CK(launch_fwd_cols(g, in, bufA, ln.stwR2, cs));
+  RC(record(h, 1 + ST_F1, cs));
+  CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
+  RC(record(h, 1 + ST_F2, cs));
   h->launches += 2;
   for (size_t q = 0; q < ln.trials.size(); ++q) {
     const int d = ln.trials[q];
     const Trial& t = h->trials[d];
     // every trial's chirp is applied as I1 loads the shared forward spectrum
-    CK(launch_inv_cols(g, ln.bufB, ln.bufA, t.anc, t.clog, ln.stwQ2, h->st));
-    if (q == 0) RC(record(h, 1 + ST_I1));
-    CK(launch_inv_rows(g, ln.bufA, ln.P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, h->st));
-    if (q == 0) RC(record(h, 1 + ST_I2));
+    CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
+    if (q == 0) RC(record(h, 1 + ST_I1, cs));
+    CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
+    if (q == 0) RC(record(h, 1 + ST_I2, cs));
+    // each trial's series row (and the fold partials) is updated in segment order
+    CK(cudaStreamWaitEvent(cs, ln.ev_chain[1 - slot][q], 0));
     if (!h->multi) {
       // fold and decimation in one launch; the profile is merged when read
-      CK(launch_fold_dec(ln.P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+      CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
                          h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum, h->phits,
-                         h->st));
-      RC(record(h, 1 + ST_FOLD));
-      RC(record(h, 1 + ST_DEC, true));
+                         cs));
+      RC(record(h, 1 + ST_FOLD, cs));
+      RC(record(h, 1 + ST_DEC, cs, true));
     } else {
-      CK(launch_decimate(ln.P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
-                         h->ts_cnt + (size_t)d * h->ring, h->ring, h->st));
-      if (q == 0) RC(record(h, 1 + ST_DEC, true));
+      CK(launch_decimate(P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
+                         h->ts_cnt + (size_t)d * h->ring, h->ring, cs));
+      if (q == 0) RC(record(h, 1 + ST_DEC, cs, true));
     }
+    CK(cudaEventRecord(ln.ev_chain[slot][q], cs));
     h->launches += 3;
   }
   if (h->want_voltages) h->v_len += nv;
@@ -502,6 +541,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
 // Ingest n samples at device pointer d into every lane (work ordered on h->st).
 int ingest_device(pond_t h, const int8_t* d, long long n) {
   const long long end = h->total_in + n;
+  RC(fork_streams(h));
   for (size_t li = 0; li < h->lanes.size(); ++li) {
     Lane& ln = h->lanes[li];
     const Geom& g = ln.g;
@@ -521,6 +561,8 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
       RC(run_segment(h, (int)li, in, ln.seg_start / g.S, 1ll << 62));
       ln.seg_start += g.S;
     }
+    // segments on st2 read the input and the carry: the carry update waits for them
+    RC(join_streams(h));
     // keep [seg_start, end) for the lane's next segment
     int8_t* dst = ln.carry[1 - ln.carry_cur];
     if (ln.seg_start < h->total_in) {
@@ -554,6 +596,7 @@ int check_tc(pond_t h) {
 
 void destroy_all(pond_t h) {
   if (!h) return;
+  if (h->st2) cudaStreamSynchronize(h->st2);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ln : h->lanes) free_lane(&ln);
   for (auto& t : h->trials) cudaFree(t.anc);
@@ -578,7 +621,10 @@ void destroy_all(pond_t h) {
   }
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->ev_caller) cudaEventDestroy(h->ev_caller);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->st) cudaStreamDestroy(h->st);
+  if (h->st2) cudaStreamDestroy(h->st2);
   if (h->cst) cudaStreamDestroy(h->cst);
   delete h;
 }
@@ -640,17 +686,17 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
   SegIn in{ln.carry[0], g.N, nullptr, 0, 0};
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {      // first pass warms up
     if (it == 1) ce = cudaEventRecord(e[0], h->st);
-    if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA, ln.stwR2, h->st);
-    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA, ln.bufB, ln.tw3L, ln.tw2L, ln.stwR1, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA[0], ln.stwR2, h->st);
+    if (ce == cudaSuccess) ce = launch_fwd_rows(g, ln.bufA[0], ln.bufB[0], ln.tw3L, ln.tw2L, ln.stwR1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[1], h->st);
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
     if (it == 1) ce = cudaEventRecord(e[2], h->st);
-    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB, ln.bufA, anc, clog, ln.stwQ2, h->st);
+    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB[0], ln.bufA[0], anc, clog, ln.stwQ2, h->st);
     if (ce == cudaSuccess)
-      ce = launch_inv_rows(g, ln.bufA, ln.P, nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.tw3M, ln.stwQ1,
+      ce = launch_inv_rows(g, ln.bufA[0], ln.P[0], nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.tw3M, ln.stwQ1,
                            h->st);
-    if (ce == cudaSuccess) ce = launch_decimate(ln.P, nv, 0, 8, 1, 0, nv / 8, T, C, nv / 8 + 1, h->st);
+    if (ce == cudaSuccess) ce = launch_decimate(ln.P[0], nv, 0, 8, 1, 0, nv / 8, T, C, nv / 8 + 1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[3], h->st);
   float ms_f = 0, ms_i = 0;
@@ -801,6 +847,9 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   }
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
+  CKD(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  CKD(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CKD(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_caller, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
@@ -841,6 +890,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     h->lanes[t.lane].trials.push_back((int)d);
     RCD(build_trial(h, o, &t));
   }
+  for (auto& ln : h->lanes)
+    for (int k = 0; k < 2; ++k) {
+      ln.ev_chain[k].assign(ln.trials.size(), nullptr);
+      for (auto& e : ln.ev_chain[k]) CKD(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
   // outputs
   const int ntr = (int)dms.size();
   h->ring = multi ? TS_RING_MULTI : TS_RING_SINGLE;
@@ -959,6 +1013,7 @@ int pond_flush(pond_t h) {
   CK(cudaSetDevice(h->device));
   const long long total_c = h->total_in / (2ll * h->nchan);
   const long long g_end = total_c - h->n_fut_max;
+  RC(fork_streams(h));
   for (size_t li = 0; li < h->lanes.size(); ++li) {
     Lane& ln = h->lanes[li];
     const Geom& g = ln.g;
@@ -972,6 +1027,7 @@ int pond_flush(pond_t h) {
       ln.seg_start += g.S;
     }
   }
+  RC(join_streams(h));
   h->flushed = true;
   if (h->ts_first >= 0) h->ts_complete = h->ts_hi;
   CK(cudaStreamSynchronize(h->st));
@@ -981,6 +1037,7 @@ int pond_flush(pond_t h) {
 int pond_sync(pond_t h) {
   if (!h) return fail(POND_E_ARG, "null handle");
   CK(cudaSetDevice(h->device));
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   return check_tc(h);
 }
