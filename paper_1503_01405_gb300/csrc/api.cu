@@ -62,10 +62,11 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr double K_DM = 1.0 / 2.41e-4;          // s MHz^2 (Eq. 1 constant)
-constexpr long long STAGE_BYTES = 64ll << 20;   // host-push staging chunk
+constexpr long long STAGE_BYTES = 256ll << 20;  // host-push staging chunk
 constexpr long long TS_RING_SINGLE = 1ll << 22; // time-series samples held on the device (one trial)
 constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched plan
 constexpr int MAX_TRIALS = 4096;
+constexpr int NSLOT = 2;                       // segments in flight (streams, FFT buffer sets)
 
 enum Stage { ST_F1 = 0, ST_F2, ST_I1, ST_I2, ST_FOLD, ST_DEC, ST_COUNT };
 const char* kStageName[POND_NSTAGE] = {"fwd_cols_unpack", "fwd_rows_split_chirp", "inv_cols",
@@ -106,11 +107,11 @@ struct Lane {
   double dm_max = 0;                        // largest DM of the lane (sets the overlap)
   std::vector<int> trials;
   // two buffer slots: consecutive segments alternate slots and streams
-  float2* bufA[2] = {nullptr, nullptr};
-  float2* bufB[2] = {nullptr, nullptr};
-  float* P[2] = {nullptr, nullptr};
+  float2* bufA[NSLOT] = {};
+  float2* bufB[NSLOT] = {};
+  float* P[NSLOT] = {};
   // per trial of the lane and slot: after that trial's fold / decimation of a segment
-  std::vector<cudaEvent_t> ev_chain[2];
+  std::vector<cudaEvent_t> ev_chain[NSLOT];
   float2* stw = nullptr;                    // stage twiddle tables of R1, R2, Q1, Q2
   const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
   float2* tw2buf = nullptr;
@@ -144,8 +145,10 @@ struct pond_s {
   long long g_first = 0, n_fut_max = 0;     // common emitted range: [g_first, total_c - n_fut_max)
   // streams
   cudaStream_t st = nullptr, cst = nullptr;
-  cudaStream_t st2 = nullptr;               // odd segments (joined into st after every push and flush)
-  cudaEvent_t ev_in = nullptr, ev_join = nullptr;
+  // streams of segments s with s mod NSLOT = 1 .. NSLOT-1 (slot 0 runs on st);
+  // joined into st after every push and flush
+  cudaStream_t sx[NSLOT] = {};
+  cudaEvent_t ev_in = nullptr, ev_join[NSLOT] = {};
   cudaEvent_t ev_done = nullptr, ev_caller = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
   // fold (single-DM plans)
@@ -299,7 +302,7 @@ int build_lane(pond_t h, Lane* ln) {
     ln->g.tc_inv = {h->wdft + TC_W_BYTES / 16, h->tc_terms, h->tc_err};
   }
   const Geom& g = ln->g;
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NSLOT; ++k) {
     CK(cudaMalloc(&ln->bufA[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->bufB[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->P[k], g.M * sizeof(float)));
@@ -332,7 +335,7 @@ int build_lane(pond_t h, Lane* ln) {
 }
 
 void free_lane(Lane* ln) {
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < NSLOT; ++k) {
     cudaFree(ln->bufA[k]);
     cudaFree(ln->bufB[k]);
     cudaFree(ln->P[k]);
@@ -347,17 +350,19 @@ void free_lane(Lane* ln) {
 }
 
 // Record boundary event i of the current segment (0 = before F1, i = after stage i-1).
-// Order everything queued on the second stream before later work on st.
+// Order everything queued on the segment streams before later work on st.
 int join_streams(pond_t h) {
-  CK(cudaEventRecord(h->ev_join, h->st2));
-  CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+  for (int k = 1; k < NSLOT; ++k) {
+    CK(cudaEventRecord(h->ev_join[k], h->sx[k]));
+    CK(cudaStreamWaitEvent(h->st, h->ev_join[k], 0));
+  }
   return POND_OK;
 }
 
-// Work on st2 may read what st produced before this point.
+// Work on the segment streams may read what st produced before this point.
 int fork_streams(pond_t h) {
   CK(cudaEventRecord(h->ev_in, h->st));
-  CK(cudaStreamWaitEvent(h->st2, h->ev_in, 0));
+  for (int k = 1; k < NSLOT; ++k) CK(cudaStreamWaitEvent(h->sx[k], h->ev_in, 0));
   return POND_OK;
 }
 
@@ -496,8 +501,8 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   // passes fill the other's tail waves; fold / decimation stay in segment order.
   // With per-stage timing everything runs on st, so each stage's events
   // bracket that stage alone.
-  const int slot = (int)(s & 1);
-  cudaStream_t cs = (slot && !h->timing) ? h->st2 : h->st;
+  const int slot = (int)(s % NSLOT);
+  cudaStream_t cs = (slot && !h->timing) ? h->sx[slot] : h->st;
   float2 *bufA = ln.bufA[slot], *bufB = ln.bufB[slot];
   float* P = ln.P[slot];
   h->ev_cur = SegEvents{};
@@ -516,7 +521,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
     if (q == 0) RC(record(h, 1 + ST_I2, cs));
     // each trial's series row (and the fold partials) is updated in segment order
-    CK(cudaStreamWaitEvent(cs, ln.ev_chain[1 - slot][q], 0));
+    CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
     if (!h->multi) {
       // fold and decimation in one launch; the profile is merged when read
       CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
@@ -561,7 +566,7 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
       RC(run_segment(h, (int)li, in, ln.seg_start / g.S, 1ll << 62));
       ln.seg_start += g.S;
     }
-    // segments on st2 read the input and the carry: the carry update waits for them
+    // the segment streams read the input and the carry: the carry update waits for them
     RC(join_streams(h));
     // keep [seg_start, end) for the lane's next segment
     int8_t* dst = ln.carry[1 - ln.carry_cur];
@@ -596,7 +601,8 @@ int check_tc(pond_t h) {
 
 void destroy_all(pond_t h) {
   if (!h) return;
-  if (h->st2) cudaStreamSynchronize(h->st2);
+  for (int k = 1; k < NSLOT; ++k)
+    if (h->sx[k]) cudaStreamSynchronize(h->sx[k]);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ln : h->lanes) free_lane(&ln);
   for (auto& t : h->trials) cudaFree(t.anc);
@@ -622,9 +628,11 @@ void destroy_all(pond_t h) {
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->ev_caller) cudaEventDestroy(h->ev_caller);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->st) cudaStreamDestroy(h->st);
-  if (h->st2) cudaStreamDestroy(h->st2);
+  for (int k = 1; k < NSLOT; ++k) {
+    if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    if (h->sx[k]) cudaStreamDestroy(h->sx[k]);
+  }
   if (h->cst) cudaStreamDestroy(h->cst);
   delete h;
 }
@@ -847,9 +855,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   }
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
-  CKD(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+  for (int k = 1; k < NSLOT; ++k) {
+    CKD(cudaStreamCreateWithFlags(&h->sx[k], cudaStreamNonBlocking));
+    CKD(cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming));
+  }
   CKD(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
-  CKD(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_caller, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
@@ -891,7 +901,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     RCD(build_trial(h, o, &t));
   }
   for (auto& ln : h->lanes)
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NSLOT; ++k) {
       ln.ev_chain[k].assign(ln.trials.size(), nullptr);
       for (auto& e : ln.ev_chain[k]) CKD(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
