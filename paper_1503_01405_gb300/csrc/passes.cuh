@@ -239,15 +239,34 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
       }
     }
     __syncthreads();   // st3 filled
+    // UPS consecutive loads of a thread fall in one row, n1 apart by 2 NT: there
+    // w^{n1 k2} advances by one product with w^{2 NT k2} (at most UPS - 1 steps)
+    // and w^{(n1+1) k2} = w^{n1 k2} w^{k2}
+    constexpr int UPS = R1 / (2 * NT) > 1 ? R1 / (2 * NT) : 1;
+    float2 wa = make_float2(1.f, 0.f), wk = wa, ws = wa;
 #pragma unroll
     for (int u = 0; u < H; ++u) {
       const int idx = 2 * (threadIdx.x + u * NT);
       if (idx < tot) {
         const int slot = idx >> LOGR1;
         const unsigned k2 = (unsigned)line_of(slot), n1 = (unsigned)(idx & (R1 - 1));
+        float2 wb;
+        if constexpr (UPS > 1) {
+          if (u % UPS == 0) {
+            wk = tw3(st3, k2);
+            ws = tw3(st3, (unsigned)(2 * NT) * k2);
+            wa = tw3(st3, n1 * k2);
+          } else {
+            wa = cmul(wa, ws);
+          }
+          wb = cmul(wa, wk);
+        } else {
+          wa = tw3(st3, n1 * k2);
+          wb = tw3(st3, (n1 + 1) * k2);
+        }
         float2* p = sm + pidx(slot, (int)n1, LSTR);   // n1 even: no pad between the two
-        p[0] = cmul(make_float2(r[u].x, r[u].y), tw3(st3, n1 * k2));
-        p[1] = cmul(make_float2(r[u].z, r[u].w), tw3(st3, (n1 + 1) * k2));
+        p[0] = cmul(make_float2(r[u].x, r[u].y), wa);
+        p[1] = cmul(make_float2(r[u].z, r[u].w), wb);
       }
     }
   }
