@@ -97,11 +97,11 @@ __host__ __device__ constexpr int tile_f2(int nl) {
             : nl * LS;
 }
 
-// F1's line stride: its epilogue reads TILE/R lines x (16 R / TILE) consecutive
-// elements per half-warp, which fall in distinct banks when the stride is
-// 16 R / TILE (mod 16) in 8-byte words.
+// Line stride of the column passes (F1, I1): their epilogues read TILE/R lines x
+// (16 R / TILE) consecutive elements per half-warp, which fall in distinct
+// banks when the stride is 16 R / TILE (mod 16) in 8-byte words.
 template <int R>
-__host__ __device__ constexpr int f1_stride() {
+__host__ __device__ constexpr int col_stride() {
   return R + R / 16 + (TILE / R >= 16 ? 1 : 16 / (TILE / R));
 }
 
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   extern __shared__ float2 smem[];
   float2* stw = smem;
   float2* sm = smem + stage_table_size(R2);
-  constexpr int LSTR = f1_stride<R2>();
+  constexpr int LSTR = col_stride<R2>();
   const int R1 = 1 << logR1;
   const int nl = min(TILE / R2, R1);
   const int lognl = __ffs(nl) - 1;
@@ -282,19 +282,28 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   // line R2/2 columns k1 and R1-1-k1.
   const unsigned lmask = (1u << logL) - 1;
   auto emit = [&](int slot, int k1, float2 X) { out[((unsigned)line_of(slot) << LOGR1) + (unsigned)k1] = X; };
-  auto split = [&](int sa, int ka, int sb, int kb, bool both) {
-    const unsigned k = (unsigned)line_of(sa) + ((unsigned)ka << logR2);
+  auto split_w = [&](int sa, int ka, int sb, int kb, bool both, float2 W) {
     const float2 A = sm[pidx(sa, ka, LSTR)];
     const float2 B = cconj(sm[pidx(sb, kb, LSTR)]);
     const float2 E = cscale(cadd(A, B), 0.5f);
     const float2 O = cscale(csub(A, B), 0.5f);
-    const float2 WO = cmul(tw2(tw2L, k & lmask), O);
+    const float2 WO = cmul(W, O);
     emit(sa, ka, cadd(E, rot90<false>(WO)));
     if (both) emit(sb, kb, cadd(cconj(E), rot90<false>(cconj(WO))));
   };
+  auto split = [&](int sa, int ka, int sb, int kb, bool both) {
+    const unsigned k = (unsigned)line_of(sa) + ((unsigned)ka << logR2);
+    split_w(sa, ka, sb, kb, both, tw2(tw2L, k & lmask));
+  };
+  // a thread's items of one row are NT columns apart, so W advances by
+  // exp(-i pi NT R2 / L) (refreshed from the table every fourth item)
+  constexpr int UPI = R1 / NT > 1 ? R1 / NT : 1;
+  const float2 wstep = tw2(tw2L, ((unsigned)NT << logR2) & lmask);
+  float2 W = make_float2(1.f, 0.f);
   const int items = np * R1;
+  int u = 0;
 #pragma unroll 2
-  for (int it = threadIdx.x; it < items; it += NT) {
+  for (int it = threadIdx.x; it < items; it += NT, ++u) {
     const int t = it >> LOGR1, k1 = it & (R1 - 1);
     if (q0 == 0 && t == 0) {
       if (k1 == 0) {
@@ -307,7 +316,9 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
         split(np, j, np, R1 - 1 - j, true);
       }
     } else {
-      split(t, k1, t + np, R1 - 1 - k1, true);
+      if (UPI > 1 && u % UPI != 0 && (u & 3) != 0) W = cmul(W, wstep);
+      else W = tw2(tw2L, ((unsigned)line_of(t) + ((unsigned)k1 << logR2)) & lmask);
+      split_w(t, k1, t + np, R1 - 1 - k1, true, W);
     }
   }
 }
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
   ChirpAnchor* sanc = reinterpret_cast<ChirpAnchor*>(smem);   // [ANC_STAGE]
   float2* stw = smem + ANC_BYTES / sizeof(float2);
   float2* sm = stw + stage_table_size(Q2);
-  constexpr int LSTR = line_stride(Q2);
+  constexpr int LSTR = col_stride<Q2>();
   constexpr int LOGQ2 = ilog2c(Q2);
   const int Q1 = 1 << logQ1;
   const int nl = min(TILE / Q2, nchan * Q1);
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
   const int tot = nl * Q2;
   load_twiddles<Q2>(stw, tw);
   tc::Ctx tcc;
-  if constexpr (TC) tc::setup(tcc, sm, tile_f2<Q2, TC>(nl), tca);
+  if constexpr (TC) tc::setup(tcc, sm, tile_f2<Q2, TC, LSTR>(nl), tca);
   const int tile = blockIdx.x;
   const int l0 = tile * nl;
   const int s = logR2 - logQ1;                 // j2 = j2lo + 2^s j2hi
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
     }
   }
   __syncthreads();
-  fft_lines<Q2, true, TC>(sm, nl, stw, &tcc);
+  fft_lines<Q2, true, TC, LSTR>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += NT) {
@@ -494,7 +505,7 @@ size_t smem_bytes(int nl) {
 template <bool TC>
 size_t max_smem_t() {
   size_t m = 0;
-#define MAXS(R) m = std::max(m, std::max(smem_bytes<R, TC>(TILE / R), smem_bytes<R, TC, f1_stride<R>()>(TILE / R)));
+#define MAXS(R) m = std::max(m, std::max(smem_bytes<R, TC>(TILE / R), smem_bytes<R, TC, col_stride<R>()>(TILE / R)));
   POND_FOR_R(MAXS)
 #undef MAXS
   return m;
@@ -521,7 +532,7 @@ cudaError_t launch_fwd_cols_t(const Geom& g, SegIn in, float2* out, const float2
   const int nl = std::min(TILE / R2, R1);
   const unsigned grid = (unsigned)(R1 / nl);
   switch (R2) {
-#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC, f1_stride<R>()>(nl), st>>>(in, out, g.logR1, tw, g.tc_fwd); break;
+#define CASE(R) case R: k_fwd_cols<R, TC><<<grid, NT, smem_bytes<R, TC, col_stride<R>()>(nl), st>>>(in, out, g.logR1, tw, g.tc_fwd); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -552,7 +563,7 @@ cudaError_t launch_inv_cols_t(const Geom& g, const float2* in, float2* out, cons
   const int nl = std::min(TILE / Q2, lines);
   const unsigned grid = (unsigned)(lines / nl);
   switch (Q2) {
-#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC>(nl) + ANC_BYTES, st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, anc, clog, tw, g.tc_inv); break;
+#define CASE(R) case R: k_inv_cols<R, TC><<<grid, NT, smem_bytes<R, TC, col_stride<R>()>(nl) + ANC_BYTES, st>>>(in, out, g.logQ1, g.logM, g.logR1, g.logR2, g.nchan, anc, clog, tw, g.tc_inv); break;
     POND_FOR_R(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
