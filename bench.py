@@ -630,6 +630,15 @@ def main():
     x_host.copy_(x_dev)
     xh = x_host.numpy()
     torch.cuda.synchronize()
+    # the host link's copy rate at this moment: the e2e step overlaps the copies with the
+    # compute, so it is copy-bound only when this rate falls below n / device step time
+    h2d_s = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        x_dev.copy_(x_host, non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_s.append(time.perf_counter() - t0)
+    h2d_gbs = n / min(h2d_s) / 1e9
     eng_h = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
                         t_dec=PLAN["t_dec"], device=local, precision=prec)
     prof = {}
@@ -647,12 +656,17 @@ def main():
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    marks = [t0]
     for _ in range(args.steps):
         step_host()
-    t1 = time.perf_counter()
+        marks.append(time.perf_counter())
+    t1 = marks[-1]
     e2e_s = max_over_ranks(dist, t1 - t0)
+    step_ms = sorted(1e3 * (b - a) for a, b in zip(marks, marks[1:]))
     e2e = {"value": ws * n * args.steps / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": n,
-           "d2h_bytes_per_step": prof["bytes"]}
+           "d2h_bytes_per_step": prof["bytes"], "h2d_copy_gbs": h2d_gbs,
+           "copy_bound_below_gbs": n / (ms / args.steps / 1e3) / 1e9,
+           "step_ms_min_median_max": [step_ms[0], statistics.median(step_ms), step_ms[-1]]}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -67,6 +67,35 @@ __device__ __forceinline__ float2 tw2(const Tw2& t, unsigned e) {
 
 constexpr int EPT = TILE / NT;   // tile elements per thread
 
+// Element maps of the load and store phases.  A thread visits
+// idx = threadIdx.x + u NT (u < NU, NT a power of two), and each map f used
+// there (global offset, bin number, shared-memory slot) is a sum of terms
+// that each depend on one bit field of idx, with disjoint fields placed at
+// disjoint bits or (the padded slot) scaled linearly; so f is additive over
+// disjoint bits: f(a | b) = f(a) + f(b) - f(0).  Lin keeps f(threadIdx.x) and
+// the warp-uniform weights f(NT 2^b) - f(0) of the bits b of u: f at an
+// unrolled u is then one add of a uniform sum.
+template <int NU>
+struct Lin {
+  static constexpr int NB = ilog2c(NU);
+  unsigned base;
+  unsigned w[NB > 0 ? NB : 1];
+  template <class F>
+  __device__ __forceinline__ explicit Lin(F f) {
+    const unsigned f0 = f(0u);
+    base = f((unsigned)threadIdx.x);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) w[b] = f((unsigned)NT << b) - f0;
+  }
+  __device__ __forceinline__ unsigned operator()(int u) const {
+    unsigned o = 0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if ((u >> b) & 1) o += w[b];
+    return base + o;
+  }
+};
+
 // Three-level table of w^e, e < 2^24, held in shared memory by F2 and I2:
 // w^e = t0[e0] t1[e1] t2[e2], e = e0 + 2^8 e1 + 2^16 e2 (each level built in
 // FP64 on the device; two FP32 products).  In shared memory level 0 is padded
@@ -138,13 +167,16 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
     // 8-byte loads: 4 consecutive columns of one row per load (runs 8-aligned)
     constexpr int CPT = EPT / 4;
     const int logq = lognl - 2;            // chunks per row = nl / 4
+    const unsigned qm = (unsigned)(nl >> 2) - 1;
+    // chunk c: row n2 = c / (nl/4), columns b0..b0+3 with b0 = 4 (c mod nl/4);
+    // int8 offset 2 (n1_0 + b0 + n2 R1), shared slot of (b0, n2)
+    const Lin<CPT> xofs([&](unsigned c) { return 2u * ((unsigned)n1_0 + ((c & qm) << 2) + ((c >> logq) << logR1)); });
+    const Lin<CPT> slot([&](unsigned c) { return (unsigned)pidx((int)((c & qm) << 2), (int)(c >> logq), LSTR); });
     uint2 w[CPT];
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
-      const int c = threadIdx.x + u * NT;
-      if (c < tot / 4) {
-        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
-        const long long r = 2 * ((long long)(n1_0 + b0) + ((long long)n2 << logR1));
+      if ((int)threadIdx.x + u * NT < tot / 4) {
+        const long long r = xofs(u);
         if (r < in.a_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.a + r));
         else if (r - in.a_len < in.b_len) w[u] = __ldg(reinterpret_cast<const uint2*>(in.b + (r - in.a_len)));
         else w[u] = make_uint2(0u, 0u);
@@ -152,14 +184,13 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
     }
 #pragma unroll
     for (int u = 0; u < CPT; ++u) {
-      const int c = threadIdx.x + u * NT;
-      if (c < tot / 4) {
-        const int n2 = c >> logq, b0 = (c & ((nl >> 2) - 1)) << 2;
+      if ((int)threadIdx.x + u * NT < tot / 4) {
         const unsigned lo = w[u].x, hi = w[u].y;
-        sm[pidx(b0 + 0, n2, LSTR)] = make_float2((float)(signed char)(lo & 0xff), (float)(signed char)((lo >> 8) & 0xff));
-        sm[pidx(b0 + 1, n2, LSTR)] = make_float2((float)(signed char)((lo >> 16) & 0xff), (float)(signed char)(lo >> 24));
-        sm[pidx(b0 + 2, n2, LSTR)] = make_float2((float)(signed char)(hi & 0xff), (float)(signed char)((hi >> 8) & 0xff));
-        sm[pidx(b0 + 3, n2, LSTR)] = make_float2((float)(signed char)((hi >> 16) & 0xff), (float)(signed char)(hi >> 24));
+        float2* p = sm + slot(u);
+        p[0] = make_float2((float)(signed char)(lo & 0xff), (float)(signed char)((lo >> 8) & 0xff));
+        p[LSTR] = make_float2((float)(signed char)((lo >> 16) & 0xff), (float)(signed char)(lo >> 24));
+        p[2 * LSTR] = make_float2((float)(signed char)(hi & 0xff), (float)(signed char)((hi >> 8) & 0xff));
+        p[3 * LSTR] = make_float2((float)(signed char)((hi >> 16) & 0xff), (float)(signed char)(hi >> 24));
       }
     }
   } else {
@@ -184,11 +215,11 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   if constexpr (TC) tc::teardown(tcc);
   // neighbouring threads take the nl columns of one row, then the next rows:
   // each warp store fills whole 32-byte sectors
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int k2 = idx >> lognl, b = idx & (nl - 1);
-    out[(unsigned)(n1_0 + b) + ((unsigned)k2 << logR1)] = sm[pidx(b, k2, LSTR)];
-  }
+  const Lin<EPT> oofs([&](unsigned idx) { return (unsigned)n1_0 + (idx & (nl - 1)) + ((idx >> lognl) << logR1); });
+  const Lin<EPT> oslot([&](unsigned idx) { return (unsigned)pidx((int)(idx & (nl - 1)), (int)(idx >> lognl), LSTR); });
+#pragma unroll
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) out[oofs(u)] = sm[oslot(u)];
 }
 
 // ---------------------------------------------------------------------------
@@ -365,50 +396,52 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
     if (staged)
       for (int i = threadIdx.x; i < (int)na; i += NT) sanc[i] = anc[a_lo + i];
   }
+  // line l = l0 + (rest >> s) (l0 a multiple of nl), c = l / Q1, j1 = l mod Q1:
+  // global offset k1 + k2 R1 with k1 = c M/R2 + j2hi, k2 = j1 + Q1 j2lo; bin
+  // k = k2 + k1 R2; shared slot (rest >> s, j2lo + 2^s j2hi)
+  const unsigned runm = (1u << logrun) - 1, sm1 = (1u << s) - 1;
+  const Lin<EPT> gofs([&](unsigned idx) {
+    const unsigned rest = idx >> logrun, l = (unsigned)l0 + (rest >> s);
+    const unsigned k1 = ((l >> logQ1) << (logM - logR2)) + (idx & runm);
+    return k1 + (((l & (Q1 - 1)) + ((rest & sm1) << logQ1)) << logR1);
+  });
+  const Lin<EPT> kbin([&](unsigned idx) {
+    const unsigned rest = idx >> logrun, l = (unsigned)l0 + (rest >> s);
+    const unsigned k1 = ((l >> logQ1) << (logM - logR2)) + (idx & runm);
+    return (l & (Q1 - 1)) + ((rest & sm1) << logQ1) + (k1 << logR2);
+  });
+  const Lin<EPT> slot([&](unsigned idx) {
+    const unsigned rest = idx >> logrun;
+    return (unsigned)pidx((int)(rest >> s), (int)((rest & sm1) + ((idx & runm) << s)), LSTR);
+  });
   float2 r[EPT];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int j2hi = idx & ((1 << logrun) - 1);
-      const int rest = idx >> logrun;
-      const int j2lo = rest & ((1 << s) - 1);
-      const int l = l0 + (rest >> s);
-      const int c = l >> logQ1, j1 = l & (Q1 - 1);
-      const unsigned k1 = ((unsigned)c << (logM - logR2)) + (unsigned)j2hi;
-      const unsigned k2 = (unsigned)j1 + ((unsigned)j2lo << logQ1);
-      r[u] = in[k1 + (k2 << logR1)];
-    }
-  }
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) r[u] = in[gofs(u)];
   if (anc) __syncthreads();   // staged anchors visible
 #pragma unroll
   for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int j2hi = idx & ((1 << logrun) - 1);
-      const int rest = idx >> logrun;
-      const int j2lo = rest & ((1 << s) - 1);
+    if ((int)threadIdx.x + u * NT < tot) {
       if (anc) {
-        const int l = l0 + (rest >> s);
-        const int c = l >> logQ1, j1 = l & (Q1 - 1);
-        const unsigned k = (unsigned)j1 + ((unsigned)j2lo << logQ1) +
-                           ((((unsigned)c << (logM - logR2)) + (unsigned)j2hi) << logR2);
+        const unsigned k = kbin(u);
         const ChirpAnchor& a = staged ? sanc[(int)((long long)(k >> clog) - a_lo)] : anc[k >> clog];
         r[u] = cmul(r[u], chirp_from(a, clog, k));
       }
-      sm[pidx(rest >> s, j2lo + (j2hi << s), LSTR)] = r[u];
+      sm[slot(u)] = r[u];
     }
   }
   __syncthreads();
   fft_lines<Q2, true, TC, LSTR>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < tot; idx += NT) {
-    const int m2 = idx >> lognl, b = idx & (nl - 1);
-    const int l = l0 + b;
-    const unsigned addr = ((unsigned)(l >> logQ1) << logM) + (unsigned)(l & (Q1 - 1)) + ((unsigned)m2 << logQ1);
-    out[addr] = sm[pidx(b, m2, LSTR)];
-  }
+  // element (line b, m2) goes to c M + j1 + Q1 m2 with l0 + b = c Q1 + j1
+  const Lin<EPT> oofs([&](unsigned idx) {
+    const unsigned l = (unsigned)l0 + (idx & (nl - 1));
+    return ((l >> logQ1) << logM) + (l & (Q1 - 1)) + ((idx >> lognl) << logQ1);
+  });
+  const Lin<EPT> oslot([&](unsigned idx) { return (unsigned)pidx((int)(idx & (nl - 1)), (int)(idx >> lognl), LSTR); });
+#pragma unroll
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) out[oofs(u)] = sm[oslot(u)];
 }
 
 // ---------------------------------------------------------------------------
@@ -439,16 +472,17 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
   if constexpr (TC) tc::setup(tcc, sm, tile_f2<Q1, TC>(nl), tca);
   const int tile = blockIdx.x;
   const int m2_0 = tile * b2;
+  // slot = c b2 + bb (row m2_0 + bb of sub-channel c), element j1: global
+  // offset c M + (m2_0 + bb) Q1 + j1
+  const Lin<EPT> gofs([&](unsigned idx) {
+    const unsigned sl = idx >> LOGQ1;
+    return ((sl >> logb2) << logM) + (((unsigned)m2_0 + (sl & (b2 - 1))) << LOGQ1) + (idx & (Q1 - 1));
+  });
+  const Lin<EPT> slot([&](unsigned idx) { return (unsigned)pidx((int)(idx >> LOGQ1), (int)(idx & (Q1 - 1)), LSTR); });
   float2 r[EPT];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    const int idx = threadIdx.x + u * NT;
-    if (idx < tot) {
-      const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
-      const int c = slot >> logb2, bb = slot & (b2 - 1);
-      r[u] = buf[((unsigned)c << logM) + ((unsigned)(m2_0 + bb) << LOGQ1) + (unsigned)e];
-    }
-  }
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) r[u] = buf[gofs(u)];
   __syncthreads();   // st3 filled
   // element j1 = e of row m2 carries I1's twiddle exp(+2 pi i j1 m2 / M); the
   // sub-channels of a row share it, so a thread reuses it while j1 m2 repeats
@@ -459,31 +493,62 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
     for (int u = 0; u < EPT; ++u) {
       const int idx = threadIdx.x + u * NT;
       if (idx < tot) {
-        const int slot = idx >> LOGQ1, e = idx & (Q1 - 1);
-        const unsigned ex = (unsigned)e * (unsigned)(m2_0 + (slot & (b2 - 1)));
+        const int sl = idx >> LOGQ1, e = idx & (Q1 - 1);
+        const unsigned ex = (unsigned)e * (unsigned)(m2_0 + (sl & (b2 - 1)));
         if (ex != last) {
           w = tw3(st3, ex);
           last = ex;
         }
-        sm[pidx(slot, e, LSTR)] = cmul(r[u], w);
+        sm[slot(u)] = cmul(r[u], w);
       }
     }
   }
   __syncthreads();
   fft_lines<Q1, true, TC>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
-  for (int idx = threadIdx.x; idx < b2 * Q1; idx += NT) {
-    const int m1 = idx >> logb2, bb = idx & (b2 - 1);
-    const int m = m2_0 + bb + (m1 << logQ2);
-    if (m < m_lo || m >= m_hi) continue;
-    float p = 0.f;
-    for (int c = 0; c < nchan; ++c) {
-      const float2 v = cscale(sm[pidx((c << logb2) + bb, m1, LSTR)], scale);
-      p = fmaf(v.x, v.x, p);
-      p = fmaf(v.y, v.y, p);
-      if (vout) vout[(size_t)c * vstride + vofs + (m - m_lo)] = v;
+  // Detect and sum over sub-channels.  The tile's no = b2 Q1 samples
+  // (m = m2_0 + bb + Q2 m1) are shared by G = NT / no thread groups when no < NT;
+  // group g sums sub-channels g, g + G, ..., and the G partial sums are added in
+  // group order through shared memory.  P = scale^2 sum_c |v_c|^2.
+  const int no = b2 * Q1;
+  const float s2 = scale * scale;
+  auto sample = [&](int o, int& m, int& bb, int& m1) {
+    m1 = o >> logb2;
+    bb = o & (b2 - 1);
+    m = m2_0 + bb + (m1 << logQ2);
+    return m >= m_lo && m < m_hi;
+  };
+  auto partial = [&](int bb, int m1, int m, int c0, int dc) {
+    float p0 = 0.f, p1 = 0.f;
+    for (int c = c0; c < nchan; c += dc) {
+      const float2 v = sm[pidx((c << logb2) + bb, m1, LSTR)];
+      p0 = fmaf(v.x, v.x, p0);
+      p1 = fmaf(v.y, v.y, p1);
+      if (vout) vout[(size_t)c * vstride + vofs + (m - m_lo)] = cscale(v, scale);
     }
-    P[m - m_lo] = p;
+    return p0 + p1;
+  };
+  if (no < NT && nchan > 1) {
+    const int G = min(NT / no, nchan);
+    const int tpg = NT / G;
+    const int g = threadIdx.x / tpg, o = threadIdx.x - g * tpg;
+    int m = 0, bb = 0, m1 = 0;
+    const bool ok = o < no && sample(o, m, bb, m1);
+    const float p = ok ? partial(bb, m1, m, g, G) : 0.f;
+    __syncthreads();   // every read of the tile done
+    float* red = reinterpret_cast<float*>(sm);   // [G][no]
+    if (o < no) red[g * no + o] = p;
+    __syncthreads();
+    if (g == 0 && ok) {
+      float q = red[o];
+      for (int j = 1; j < G; ++j) q += red[j * no + o];
+      P[m - m_lo] = q * s2;
+    }
+  } else {
+    for (int o = threadIdx.x; o < no; o += NT) {
+      int m, bb, m1;
+      if (sample(o, m, bb, m1)) P[m - m_lo] = partial(bb, m1, m, 0, 1) * s2;
+    }
   }
 }
 
