@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Msamples/s dedisperse+detect+fold (×real-time) and % HBM roofline vs plain FP32"
 UNIT = "Msamples/s"
 F0, BW, FS = 326.5, 16.0, 32e6
+# kernel behind each stage name of pond_stats
+KERNEL_OF_STAGE = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split": "k_fwd_rows",
+                   "fwd_rows_chirp_inv": "k_fwd_rows_inv", "inv_cols_chirp": "k_inv_cols",
+                   "inv_rows_detect": "k_inv_rows", "inv_cols_detect": "k_inv_cols_det",
+                   "fold": "k_fold_dec", "decimate": "k_decimate"}
 PLAN = dict(dm=26.8, nfft=1 << 24, nchan=64, nbins=1024, period=0.7145, t_dec=61.44e-6)
 REALTIME_MSPS = FS / 1e6
 
@@ -365,8 +370,7 @@ def run_precision(args, rank, ws, dist):
     dom = max(stages, key=lambda k: stages[k]["ms"])
     peaks = measured_peaks()
     achieved = stages[dom]["algo_bytes"] / (stages[dom]["ms"] / stages[dom]["launches"] / 1e3) / 1e9
-    kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
-             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_dec", "decimate": "k_decimate"}[dom]
+    kname = KERNEL_OF_STAGE[dom]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname + " (tensor-core form)",
             "peak_src": peaks["src"],
@@ -595,8 +599,7 @@ def main():
     peaks = measured_peaks()
     avg_s = stages[dom]["ms"] / stages[dom]["launches"] / 1e3
     achieved = stages[dom]["algo_bytes"] / avg_s / 1e9
-    kname = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split_chirp": "k_fwd_rows", "inv_cols": "k_inv_cols",
-             "inv_rows_detect": "k_inv_rows", "fold": "k_fold_dec", "decimate": "k_decimate"}[dom]
+    kname = KERNEL_OF_STAGE[dom]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_from_profiles(kname),
             "kernel": kname, "peak_src": peaks["src"],

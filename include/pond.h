@@ -67,6 +67,18 @@ extern "C" {
 #define POND_SPLIT_BF16_5T 2  /* as POND_SPLIT_BF16 with five terms (adds x_hi w_lo and
                                  x_lo w_mid): only the data split rounds to BF16 */
 
+/* Pass schedule of a segment (Sec. 3.7 path, same outputs either way). */
+#define POND_SCHEDULE_AUTO 0       /* single-trial FP32 plans whose sub-channel length M is
+                                      64 times the forward column length R2 (e.g. nfft 2^24
+                                      with 64 sub-channels) run three passes: the forward
+                                      row pass also applies Eq. 4 and the first length-64
+                                      factor of each sub-channel's inverse DFT, and one
+                                      column pass finishes the inverse, detects and sums
+                                      the sub-channels; every other plan runs four */
+#define POND_SCHEDULE_FOUR_PASS 1  /* always the four-pass schedule (forward columns,
+                                      forward rows, inverse columns with Eq. 4, inverse
+                                      rows with detection) */
+
 typedef struct pond_s* pond_t;
 
 /* Full plan description for pond_plan_ex.  Zero-initialise, then set fields. */
@@ -101,7 +113,8 @@ typedef struct {
                            each group one of nfft_choices, minimising the device time per
                            input sample predicted from timed launches of each length
                            (cached per nfft, nchan and device); zero: every trial uses nfft */
-  int32_t reserved[7];
+  int32_t schedule;     /* POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS (below) */
+  int32_t reserved[6];
 } pond_opts;
 
 /* Fold metadata returned with a profile snapshot. */

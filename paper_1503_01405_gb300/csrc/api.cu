@@ -68,9 +68,13 @@ constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched pl
 constexpr int MAX_TRIALS = 4096;
 constexpr int NSLOT = 2;                       // segments in flight (streams, FFT buffer sets)
 
-enum Stage { ST_F1 = 0, ST_F2, ST_I1, ST_I2, ST_FOLD, ST_DEC, ST_COUNT };
-const char* kStageName[POND_NSTAGE] = {"fwd_cols_unpack", "fwd_rows_split_chirp", "inv_cols",
-                                       "inv_rows_detect", "fold", "decimate", "", ""};
+// Stages in pipeline order (a segment runs F1, F2, I1, I2 or F1, F2f, Ic, then
+// fold / decimation).
+enum Stage { ST_F1 = 0, ST_F2, ST_F2F, ST_I1, ST_I2, ST_IC, ST_FOLD, ST_DEC, ST_COUNT };
+static_assert(ST_COUNT <= POND_NSTAGE, "stage slots");
+const char* kStageName[POND_NSTAGE] = {"fwd_cols_unpack", "fwd_rows_split", "fwd_rows_chirp_inv",
+                                       "inv_cols_chirp", "inv_rows_detect", "inv_cols_detect",
+                                       "fold", "decimate"};
 
 int ilog2ll(long long v) {
   int r = 0;
@@ -110,10 +114,14 @@ struct Lane {
   float2* bufA[NSLOT] = {};
   float2* bufB[NSLOT] = {};
   float* P[NSLOT] = {};
+  // fused schedule (F1, F2f, Ic): Ic's group partials and per-m1 tickets per slot
+  bool fused = false;
+  float* part[NSLOT] = {};
+  int* cnt[NSLOT] = {};
   // per trial of the lane and slot: after that trial's fold / decimation of a segment
   std::vector<cudaEvent_t> ev_chain[NSLOT];
   float2* stw = nullptr;                    // stage twiddle tables of R1, R2, Q1, Q2
-  const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr;
+  const float2 *stwR1 = nullptr, *stwR2 = nullptr, *stwQ1 = nullptr, *stwQ2 = nullptr, *stwJ = nullptr;
   float2* tw2buf = nullptr;
   Tw2 tw2L;                                 // exp(-2 pi i e/(2L))
   float2* tw3L = nullptr;                   // three-level exp(-2 pi i e/L)
@@ -136,6 +144,7 @@ struct pond_s {
   double epoch_sec;
   int want_voltages, timing, device;
   bool multi = false;
+  int schedule = POND_SCHEDULE_AUTO;
   double dtc = 0, inc = 0;
   long long dec_num = 1, dec_den = 1;
   int sgn = 1;
@@ -222,6 +231,8 @@ int validate(const pond_opts* o) {
   }
   if (o->precision != POND_FP32 && o->precision != POND_SPLIT_BF16 && o->precision != POND_SPLIT_BF16_5T)
     return fail(POND_E_ARG, "precision must be POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T");
+  if (o->schedule != POND_SCHEDULE_AUTO && o->schedule != POND_SCHEDULE_FOUR_PASS)
+    return fail(POND_E_ARG, "schedule must be POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS");
   return POND_OK;
 }
 
@@ -302,18 +313,26 @@ int build_lane(pond_t h, Lane* ln) {
     ln->g.tc_inv = {h->wdft + TC_W_BYTES / 16, h->tc_terms, h->tc_err};
   }
   const Geom& g = ln->g;
+  ln->fused = !h->multi && !h->tc_terms && h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g);
   for (int k = 0; k < NSLOT; ++k) {
     CK(cudaMalloc(&ln->bufA[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->bufB[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->P[k], g.M * sizeof(float)));
+    if (ln->fused && fused_groups(g) > 1) {
+      CK(cudaMalloc(&ln->part[k], (size_t)fused_groups(g) * g.M * sizeof(float)));
+      CK(cudaMalloc(&ln->cnt[k], FUSED_J * sizeof(int)));
+      CK(cudaMemsetAsync(ln->cnt[k], 0, FUSED_J * sizeof(int), h->st));
+    }
   }
   const int n1 = stage_tw_entries(1 << g.logR1), n2 = stage_tw_entries(1 << g.logR2);
   const int n3 = stage_tw_entries(1 << g.logQ1), n4 = stage_tw_entries(1 << g.logQ2);
-  CK(cudaMalloc(&ln->stw, (size_t)std::max(1, n1 + n2 + n3 + n4) * sizeof(float2)));
+  const int n5 = stage_tw_entries(FUSED_J);
+  CK(cudaMalloc(&ln->stw, (size_t)std::max(1, n1 + n2 + n3 + n4 + n5) * sizeof(float2)));
   ln->stwR1 = ln->stw;
   ln->stwR2 = ln->stwR1 + n1;
   ln->stwQ1 = ln->stwR2 + n2;
   ln->stwQ2 = ln->stwQ1 + n3;
+  ln->stwJ = ln->stwQ2 + n4;
   auto nhi = [](int logn) { return logn > TW2_LOG ? (1ll << (logn - TW2_LOG)) : 1ll; };
   const long long total = TW2_LO + nhi(g.logL + 1) + 2 * 768;
   CK(cudaMalloc(&ln->tw2buf, total * sizeof(float2)));
@@ -328,6 +347,7 @@ int build_lane(pond_t h, Lane* ln) {
   CK(launch_stage_tw(const_cast<float2*>(ln->stwR2), 1 << g.logR2, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwQ1), 1 << g.logQ1, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwQ2), 1 << g.logQ2, h->st));
+  CK(launch_stage_tw(const_cast<float2*>(ln->stwJ), FUSED_J, h->st));
   CK(launch_tw3(ln->tw3L, g.logL, -1, h->st));
   CK(launch_tw2(const_cast<float2*>(ln->tw2L.lo), const_cast<float2*>(ln->tw2L.hi), g.logL + 1, -1, h->st));
   CK(launch_tw3(ln->tw3M, g.logM, +1, h->st));
@@ -339,6 +359,8 @@ void free_lane(Lane* ln) {
     cudaFree(ln->bufA[k]);
     cudaFree(ln->bufB[k]);
     cudaFree(ln->P[k]);
+    cudaFree(ln->part[k]);
+    cudaFree(ln->cnt[k]);
     for (auto e : ln->ev_chain[k]) cudaEventDestroy(e);
     ln->ev_chain[k].clear();
   }
@@ -509,33 +531,51 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   RC(record(h, 0, cs));
   CK(launch_fwd_cols(g, in, bufA, ln.stwR2, cs));
   RC(record(h, 1 + ST_F1, cs));
-  CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
-  RC(record(h, 1 + ST_F2, cs));
-  h->launches += 2;
-  for (size_t q = 0; q < ln.trials.size(); ++q) {
-    const int d = ln.trials[q];
-    const Trial& t = h->trials[d];
-    // every trial's chirp is applied as I1 loads the shared forward spectrum
-    CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
-    if (q == 0) RC(record(h, 1 + ST_I1, cs));
-    CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
-    if (q == 0) RC(record(h, 1 + ST_I2, cs));
-    // each trial's series row (and the fold partials) is updated in segment order
-    CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
-    if (!h->multi) {
-      // fold and decimation in one launch; the profile is merged when read
-      CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
-                         h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum, h->phits,
-                         cs));
-      RC(record(h, 1 + ST_FOLD, cs));
-      RC(record(h, 1 + ST_DEC, cs, true));
-    } else {
-      CK(launch_decimate(P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
-                         h->ts_cnt + (size_t)d * h->ring, h->ring, cs));
-      if (q == 0) RC(record(h, 1 + ST_DEC, cs, true));
+  if (ln.fused) {
+    // three passes: F2f takes the chirp and the first inverse factor, Ic the rest
+    const Trial& t = h->trials[ln.trials[0]];
+    CK(launch_fwd_rows_inv(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, ln.stwJ, t.anc, t.clog, cs));
+    RC(record(h, 1 + ST_F2F, cs));
+    CK(launch_inv_cols_det(g, bufB, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
+                           (int)m_hi, ln.stwR2, cs));
+    RC(record(h, 1 + ST_IC, cs));
+    CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][0], 0));
+    CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                       h->ts + (size_t)ln.trials[0] * h->ring, h->ts_cnt + (size_t)ln.trials[0] * h->ring, h->ring,
+                       h->psum, h->phits, cs));
+    RC(record(h, 1 + ST_FOLD, cs));
+    RC(record(h, 1 + ST_DEC, cs, true));
+    CK(cudaEventRecord(ln.ev_chain[slot][0], cs));
+    h->launches += 4;
+  } else {
+    CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
+    RC(record(h, 1 + ST_F2, cs));
+    h->launches += 2;
+    for (size_t q = 0; q < ln.trials.size(); ++q) {
+      const int d = ln.trials[q];
+      const Trial& t = h->trials[d];
+      // every trial's chirp is applied as I1 loads the shared forward spectrum
+      CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
+      if (q == 0) RC(record(h, 1 + ST_I1, cs));
+      CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
+      if (q == 0) RC(record(h, 1 + ST_I2, cs));
+      // each trial's series row (and the fold partials) is updated in segment order
+      CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
+      if (!h->multi) {
+        // fold and decimation in one launch; the profile is merged when read
+        CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                           h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum,
+                           h->phits, cs));
+        RC(record(h, 1 + ST_FOLD, cs));
+        RC(record(h, 1 + ST_DEC, cs, true));
+      } else {
+        CK(launch_decimate(P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
+                           h->ts_cnt + (size_t)d * h->ring, h->ring, cs));
+        if (q == 0) RC(record(h, 1 + ST_DEC, cs, true));
+      }
+      CK(cudaEventRecord(ln.ev_chain[slot][q], cs));
+      h->launches += 3;
     }
-    CK(cudaEventRecord(ln.ev_chain[slot][q], cs));
-    h->launches += 3;
   }
   if (h->want_voltages) h->v_len += nv;
   h->ts_hi = std::max(h->ts_hi, j_hi + 1);
@@ -795,6 +835,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   h->device = o->device;
   h->sgn = o->bw_mhz > 0 ? 1 : -1;
   h->multi = multi;
+  h->schedule = o->schedule;
   h->dtc = 2.0 * o->nchan / o->fs_hz;
   h->inc = multi ? 0.0 : h->dtc / o->period_s;
   const double tdec = o->t_dec_s > 0 ? o->t_dec_s : 61.44e-6;
@@ -1289,8 +1330,10 @@ int pond_stats(pond_t h, pond_stats_t* s) {
   const double nv = (double)g.S_c;
   s->algo_bytes[ST_F1] = (double)g.N + spec;
   s->algo_bytes[ST_F2] = 2 * spec;
+  s->algo_bytes[ST_F2F] = 2 * spec;
   s->algo_bytes[ST_I1] = 2 * spec;
   s->algo_bytes[ST_I2] = spec + nv * sizeof(float);
+  s->algo_bytes[ST_IC] = spec + nv * sizeof(float);
   s->algo_bytes[ST_FOLD] = nv * sizeof(float);
   s->algo_bytes[ST_DEC] = nv * sizeof(float);
   for (int i = 0; i < POND_NSTAGE; ++i) {

@@ -464,8 +464,72 @@ cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du,
   return cudaGetLastError();
 }
 
+// Fused schedule: F2f for R1 = 512..4096 with J = 64, Ic for R2 = 4..2048.
+#define POND_FUSED_R1(X) X(512) X(1024) X(2048) X(4096)
+#define POND_FUSED_R2(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+
+bool fused_geometry(const Geom& g) {
+  return g.logM - g.logR2 == 6 && g.logR1 >= 9 && g.logR1 <= 12 && g.logR2 >= 2 && g.logR2 <= 11;
+}
+
+namespace {
+size_t smem_fwd_rows_inv(int R1, int nl) {
+  return ((size_t)TW3_SN + stage_table_size(R1) + stage_table_size(FUSED_J) + (size_t)nl * FUSED_J +
+          (size_t)nl * (R1 + R1 / 16)) * sizeof(float2);
+}
+template <int R2>
+size_t smem_inv_cols_det(int nl) {
+  return ((size_t)stage_table_size(R2) + (size_t)nl * col_stride<R2>()) * sizeof(float2);
+}
+}  // namespace
+
+cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L,
+                                const float2* tw, const float2* twJ, const ChirpAnchor* anc, int clog,
+                                cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R1, R2);
+  const unsigned grid = (unsigned)(R2 / nl);
+  switch (R1) {
+#define CASE(R) case R: k_fwd_rows_inv<R, FUSED_J><<<grid, NT, smem_fwd_rows_inv(R, nl), st>>>(in, out, g.logR2, g.logL, tw3L, tw2L, tw, twJ, anc, clog); break;
+    POND_FUSED_R1(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int fused_groups(const Geom& g) {
+  const int nl = std::min(TILE >> g.logR2, g.nchan);
+  return g.nchan / nl;
+}
+
+cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
+                                long long vstride, long long vofs, int m_lo, int m_hi, const float2* tw,
+                                cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R2, g.nchan);
+  const unsigned grid = (unsigned)(R1 / nl);
+  const float scale = 1.0f / (float)(1u << g.logM);
+  const int lognch = g.logR1 - (g.logM - g.logR2);
+  switch (R2) {
+#define CASE(R) case R: k_inv_cols_det<R><<<grid, NT, smem_inv_cols_det<R>(nl), st>>>(in, P, part, cnt, vout, vstride, vofs, g.logR1, lognch, g.logM - g.logR2, m_lo, m_hi, scale, tw); break;
+    POND_FUSED_R2(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t set_kernel_attributes() {
   cudaError_t e = set_attributes_t<false>();
+#define SET_F(R) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows_inv<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd_rows_inv(R, TILE / R));
+  POND_FUSED_R1(SET_F)
+#undef SET_F
+#define SET_C(R) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols_det<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_cols_det<R>(TILE / R));
+  POND_FUSED_R2(SET_C)
+#undef SET_C
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
   if (e == cudaSuccess)

@@ -19,6 +19,12 @@
 //                    of the same m2 in one CTA: v_c[m2 + Q2 m1] / M, keep the
 //                    valid span n_past <= m < M - n_fut, detect |v|^2 and sum
 //                    over sub-channels into P (and optionally store v).
+//
+//  Single-trial FP32 plans with J = M / R2 = 64 run three passes instead
+//  (F1, F2f, Ic): F2f k_fwd_rows_inv is F2 followed, in the same tile, by the
+//  chirp and the length-J first factor of every sub-channel's inverse; Ic
+//  k_inv_cols_det takes the remaining length-R2 factor down the columns, then
+//  discards, detects and sums over sub-channels.  F1 is shared.
 //  Table lookups (twiddles, chirp anchors) sit in the load phases, where their
 //  latency overlaps the tile's own loads; I1 stages its CTA's chirp anchors in
 //  shared memory when they are few (one anchor covers up to 2^15 bins).
@@ -223,96 +229,84 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// F2: row FFTs + real-input split + dedispersion chirp
+// F2: row FFTs + real-input split
 // ---------------------------------------------------------------------------
 
 // Row k2 of the column-transformed z holds, after a length-R1 FFT, Z[k2 + R2 k1].
 // Rows k2 and R2-k2 share a CTA (row 0 and row R2/2 pair with themselves) so that
-// X[k] can be formed from Z[k] and Z[L-k]; the chirped spectrum Y[k2 + R2 k1] is
-// stored at row k2, column k1 of the output (the same place the row was read).
-template <int R1, bool TC>
-__global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
-                                                    int logR2, int logL, const float2* __restrict__ tw3L, Tw2 tw2L,
-                                                    const float2* __restrict__ tw, TcArgs tca) {
-  extern __shared__ float2 smem[];
-  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
-  float2* stw = smem + TW3_SN;
-  float2* sm = stw + stage_table_size(R1);
-  constexpr int LSTR = line_stride(R1);
+// X[k] can be formed from Z[k] and Z[L-k].  Slot s < np of tile q0 np is row
+// q0 + s, slot np + t its partner.
+__device__ __forceinline__ int f2_line(int slot, int q0, int np, int R2) {
+  if (slot < np) return q0 + slot;
+  const int t = slot - np;
+  if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
+  return R2 - (q0 + t);
+}
+
+// Load the tile's rows (tot = 2 np R1 elements) into sm (line stride LSTR),
+// each element scaled by w^{n1 k2}, w = exp(-2 pi i / L), once st3 (being
+// filled by the caller) is in: 16-byte loads of columns n1, n1 + 1.
+template <int R1, int LSTR>
+__device__ __forceinline__ void f2_load(const float2* __restrict__ in, float2* sm, const float2* st3, int q0, int np,
+                                        int R2, int tot) {
   constexpr int LOGR1 = ilog2c(R1);
-  load_tw3(st3, tw3L);
-  const int R2 = 1 << logR2;
-  const int nl = min(TILE / R1, R2);   // 2 * pairs
-  const int np = nl >> 1;
-  const int tot = nl * R1;
-  load_twiddles<R1>(stw, tw);
-  tc::Ctx tcc;
-  if constexpr (TC) tc::setup(tcc, sm, tile_f2<R1, TC>(nl), tca);
-  const int tile = blockIdx.x;
-  const int q0 = tile * np;
-  auto line_of = [&](int slot) -> int {
-    if (slot < np) return q0 + slot;
-    const int t = slot - np;
-    if (q0 + t == 0) return R2 >> 1;          // row R2/2 pairs with itself
-    return R2 - (q0 + t);
-  };
-  {  // 16-byte loads (two consecutive columns n1, n1 + 1 of row k2), scaled by
-     // w^{n1 k2} and w^{(n1+1) k2}, w = exp(-2 pi i / L), once the table is in
-    const float4* in4 = reinterpret_cast<const float4*>(in);
-    constexpr int H = EPT / 2;
-    float4 r[H];
+  const float4* in4 = reinterpret_cast<const float4*>(in);
+  constexpr int H = EPT / 2;
+  float4 r[H];
 #pragma unroll
-    for (int u = 0; u < H; ++u) {
-      const int idx = 2 * (threadIdx.x + u * NT);
-      if (idx < tot) {
-        const unsigned k2 = (unsigned)line_of(idx >> LOGR1), n1 = (unsigned)(idx & (R1 - 1));
-        r[u] = __ldg(in4 + (((k2 << LOGR1) + n1) >> 1));
-      }
-    }
-    __syncthreads();   // st3 filled
-    // UPS consecutive loads of a thread fall in one row, n1 apart by 2 NT: there
-    // w^{n1 k2} advances by one product with w^{2 NT k2} (at most UPS - 1 steps)
-    // and w^{(n1+1) k2} = w^{n1 k2} w^{k2}
-    constexpr int UPS = R1 / (2 * NT) > 1 ? R1 / (2 * NT) : 1;
-    float2 wa = make_float2(1.f, 0.f), wk = wa, ws = wa;
-#pragma unroll
-    for (int u = 0; u < H; ++u) {
-      const int idx = 2 * (threadIdx.x + u * NT);
-      if (idx < tot) {
-        const int slot = idx >> LOGR1;
-        const unsigned k2 = (unsigned)line_of(slot), n1 = (unsigned)(idx & (R1 - 1));
-        float2 wb;
-        if constexpr (UPS > 1) {
-          if (u % UPS == 0) {
-            wk = tw3(st3, k2);
-            ws = tw3(st3, (unsigned)(2 * NT) * k2);
-            wa = tw3(st3, n1 * k2);
-          } else {
-            wa = cmul(wa, ws);
-          }
-          wb = cmul(wa, wk);
-        } else {
-          wa = tw3(st3, n1 * k2);
-          wb = tw3(st3, (n1 + 1) * k2);
-        }
-        float2* p = sm + pidx(slot, (int)n1, LSTR);   // n1 even: no pad between the two
-        p[0] = cmul(make_float2(r[u].x, r[u].y), wa);
-        p[1] = cmul(make_float2(r[u].z, r[u].w), wb);
-      }
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * (threadIdx.x + u * NT);
+    if (idx < tot) {
+      const unsigned k2 = (unsigned)f2_line(idx >> LOGR1, q0, np, R2), n1 = (unsigned)(idx & (R1 - 1));
+      r[u] = __ldg(in4 + (((k2 << LOGR1) + n1) >> 1));
     }
   }
-  __syncthreads();
-  fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
-  if constexpr (TC) tc::teardown(tcc);
-  // Real-input split by conjugate pairs: with A = Z[k], B = conj(Z[L-k]),
-  // E = (A + B)/2, O = (A - B)/2 and W = exp(-i pi k / L),
-  //   X[k] = E - i W O   and   X[L-k] = conj(E) - i conj(W O),
-  // so one item produces both bins of a pair (slot t < np, column k1) and
-  // (slot t + np, column R1-1-k1).  In tile 0 lines 0 and R2/2 pair with
-  // themselves: line 0 pairs columns k1 and R1-k1 (k1 = 0 and R1/2 alone),
-  // line R2/2 columns k1 and R1-1-k1.
+  __syncthreads();   // st3 filled
+  // UPS consecutive loads of a thread fall in one row, n1 apart by 2 NT: there
+  // w^{n1 k2} advances by one product with w^{2 NT k2} (at most UPS - 1 steps)
+  // and w^{(n1+1) k2} = w^{n1 k2} w^{k2}
+  constexpr int UPS = R1 / (2 * NT) > 1 ? R1 / (2 * NT) : 1;
+  float2 wa = make_float2(1.f, 0.f), wk = wa, ws = wa;
+#pragma unroll
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * (threadIdx.x + u * NT);
+    if (idx < tot) {
+      const int slot = idx >> LOGR1;
+      const unsigned k2 = (unsigned)f2_line(slot, q0, np, R2), n1 = (unsigned)(idx & (R1 - 1));
+      float2 wb;
+      if constexpr (UPS > 1) {
+        if (u % UPS == 0) {
+          wk = tw3(st3, k2);
+          ws = tw3(st3, (unsigned)(2 * NT) * k2);
+          wa = tw3(st3, n1 * k2);
+        } else {
+          wa = cmul(wa, ws);
+        }
+        wb = cmul(wa, wk);
+      } else {
+        wa = tw3(st3, n1 * k2);
+        wb = tw3(st3, (n1 + 1) * k2);
+      }
+      float2* p = sm + pidx(slot, (int)n1, LSTR);   // n1 even: no pad between the two
+      p[0] = cmul(make_float2(r[u].x, r[u].y), wa);
+      p[1] = cmul(make_float2(r[u].z, r[u].w), wb);
+    }
+  }
+}
+
+// Real-input split by conjugate pairs after the row FFTs: with A = Z[k],
+// B = conj(Z[L-k]), E = (A + B)/2, O = (A - B)/2 and W = exp(-i pi k / L),
+//   X[k] = E - i W O   and   X[L-k] = conj(E) - i conj(W O),
+// so one item produces both bins of a pair (slot t < np, column k1) and
+// (slot t + np, column R1-1-k1), handed to emit(slot, k1, X).  In tile 0 lines
+// 0 and R2/2 pair with themselves: line 0 pairs columns k1 and R1-k1 (k1 = 0
+// and R1/2 alone), line R2/2 columns k1 and R1-1-k1.  Both bins of a pair are
+// read before either is emitted, so emit may overwrite them in sm.
+template <int R1, int LSTR, class Emit>
+__device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int logR2, int logL, Tw2 tw2L,
+                                         Emit emit) {
+  constexpr int LOGR1 = ilog2c(R1);
   const unsigned lmask = (1u << logL) - 1;
-  auto emit = [&](int slot, int k1, float2 X) { out[((unsigned)line_of(slot) << LOGR1) + (unsigned)k1] = X; };
   auto split_w = [&](int sa, int ka, int sb, int kb, bool both, float2 W) {
     const float2 A = sm[pidx(sa, ka, LSTR)];
     const float2 B = cconj(sm[pidx(sb, kb, LSTR)]);
@@ -323,7 +317,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
     if (both) emit(sb, kb, cadd(cconj(E), rot90<false>(cconj(WO))));
   };
   auto split = [&](int sa, int ka, int sb, int kb, bool both) {
-    const unsigned k = (unsigned)line_of(sa) + ((unsigned)ka << logR2);
+    const unsigned k = (unsigned)f2_line(sa, q0, np, R2) + ((unsigned)ka << logR2);
     split_w(sa, ka, sb, kb, both, tw2(tw2L, k & lmask));
   };
   // a thread's items of one row are NT columns apart, so W advances by
@@ -348,8 +342,117 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
       }
     } else {
       if (UPI > 1 && u % UPI != 0 && (u & 3) != 0) W = cmul(W, wstep);
-      else W = tw2(tw2L, ((unsigned)line_of(t) + ((unsigned)k1 << logR2)) & lmask);
+      else W = tw2(tw2L, ((unsigned)f2_line(t, q0, np, R2) + ((unsigned)k1 << logR2)) & lmask);
       split_w(t, k1, t + np, R1 - 1 - k1, true, W);
+    }
+  }
+}
+
+// The spectrum X[k2 + R2 k1] is stored at row k2, column k1 of the output (the
+// same place the row was read); the chirp is I1's.
+template <int R1, bool TC>
+__global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ in, float2* __restrict__ out,
+                                                    int logR2, int logL, const float2* __restrict__ tw3L, Tw2 tw2L,
+                                                    const float2* __restrict__ tw, TcArgs tca) {
+  extern __shared__ float2 smem[];
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stw = smem + TW3_SN;
+  float2* sm = stw + stage_table_size(R1);
+  constexpr int LSTR = line_stride(R1);
+  constexpr int LOGR1 = ilog2c(R1);
+  load_tw3(st3, tw3L);
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);   // 2 * pairs
+  const int np = nl >> 1;
+  load_twiddles<R1>(stw, tw);
+  tc::Ctx tcc;
+  if constexpr (TC) tc::setup(tcc, sm, tile_f2<R1, TC>(nl), tca);
+  const int q0 = blockIdx.x * np;
+  f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
+  __syncthreads();
+  fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
+  if constexpr (TC) tc::teardown(tcc);
+  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int k1, float2 X) {
+    out[((unsigned)f2_line(slot, q0, np, R2) << LOGR1) + (unsigned)k1] = X;
+  });
+}
+
+// ---------------------------------------------------------------------------
+// F2f: F2 with the chirp and the first factor of every sub-channel's inverse
+// ---------------------------------------------------------------------------
+
+// When R2 divides M, row k2 holds for sub-channel c the J = M/R2 bins
+// c M + k2 + R2 j (j < J) at columns c J + j, and with m = m1 + J m2
+//   v_c[m] = sum_k2 e^{2 pi i k2 m2 / R2} e^{2 pi i k2 m1 / M}
+//            sum_j Y_c[k2 + R2 j] e^{2 pi i j m1 / J}
+// (times 1/M, applied on detection).  The inner sum is a length-J inverse DFT
+// within the row, so F2f applies the chirp (Eq. 4) to the split spectrum in
+// shared memory, transforms every (row, sub-channel) run of J bins, scales by
+// e^{2 pi i k2 m1 / M} and stores element (k2, m1, c) blocked for the column
+// pass (Ic): with nl = min(TILE/R2, NCH) sub-channels per Ic CTA and
+// c = g nl + ci, at ((m1 G + g) R2 + k2) nl + ci, so that each Ic CTA reads one
+// contiguous block (its stores here are runs of 4 sub-channels, 32 bytes).
+// The row stride R1 + R1/16 makes each run a line of stride J + J/16.
+template <int R1, int J>
+__global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict__ in, float2* __restrict__ out,
+                                                        int logR2, int logL, const float2* __restrict__ tw3L,
+                                                        Tw2 tw2L, const float2* __restrict__ tw,
+                                                        const float2* __restrict__ twJ,
+                                                        const ChirpAnchor* __restrict__ anc, int clog) {
+  static_assert(J >= 16 && J % 16 == 0 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
+  constexpr int NCH = R1 / J;                 // sub-channels
+  constexpr int LSTR = R1 + R1 / 16;
+  constexpr int LOGJ = ilog2c(J), LOGNCH = ilog2c(NCH), LOGR1 = ilog2c(R1);
+  extern __shared__ float2 smem[];
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stw = st3 + TW3_SN;
+  float2* stwj = stw + stage_table_size(R1);
+  float2* twk = stwj + stage_table_size(J);        // [nl][J]: e^{2 pi i k2 m1 / M}
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);
+  const int np = nl >> 1;
+  float2* sm = twk + nl * J;
+  load_tw3(st3, tw3L);
+  load_twiddles<R1>(stw, tw);
+  load_twiddles<J>(stwj, twJ);
+  const int q0 = blockIdx.x * np;
+  f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
+  __syncthreads();
+  fft_lines<R1, false, false, LSTR>(sm, nl, stw, nullptr);
+  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int k1, float2 X) {
+    const unsigned k = (unsigned)f2_line(slot, q0, np, R2) + ((unsigned)k1 << logR2);
+    const ChirpAnchor a = anc[k >> clog];
+    sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
+  });
+  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
+  for (int i = threadIdx.x; i < nl * J; i += NT) {
+    const unsigned k2 = (unsigned)f2_line(i >> LOGJ, q0, np, R2), m1 = (unsigned)(i & (J - 1));
+    twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
+  }
+  __syncthreads();
+  fft_lines<J, true, false, J + J / 16>(sm, nl * NCH, stwj, nullptr);
+  // idx bits: [0,2) c, [2,4) m1, then the rest of c, the rest of m1, the slot;
+  // a half-warp reads 4 runs x 4 elements (banks 4c + m1 apart: distinct) and
+  // writes 4 x 32 contiguous bytes
+  auto cof = [](unsigned idx) { return (idx & 3u) | (((idx >> 4) & (NCH / 4 - 1)) << 2); };
+  auto mof = [](unsigned idx) { return ((idx >> 2) & 3u) | (((idx >> (LOGNCH + 2)) & (J / 4 - 1)) << 2); };
+  const int lognl = min(13 - logR2, LOGNCH);      // Ic's sub-channels per CTA (log2)
+  // block (m1 G + g) of R2 nl elements, row k2 (added per u), sub-channel ci
+  const Lin<EPT> oofs([&](unsigned idx) {
+    const unsigned c = cof(idx);
+    return ((((mof(idx) << (LOGNCH - lognl)) + (c >> lognl)) << logR2) << lognl) + (c & ((1u << lognl) - 1));
+  });
+  const Lin<EPT> sidx([&](unsigned idx) {
+    return (unsigned)pidx((int)(idx >> LOGR1), (int)((cof(idx) << LOGJ) + mof(idx)), LSTR);
+  });
+  const Lin<EPT> tidx([&](unsigned idx) { return ((idx >> LOGR1) << LOGJ) + mof(idx); });
+  const int tot = nl * R1;
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    if ((int)threadIdx.x + u * NT < tot) {
+      const int slot = (u * NT) >> LOGR1;          // NT <= R1: the slot is the u's
+      const unsigned row = (unsigned)f2_line(slot, q0, np, R2);
+      out[(row << lognl) + oofs(u)] = cmul(sm[sidx(u)], twk[tidx(u)]);
     }
   }
 }
@@ -549,6 +652,84 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows(const float2* __restrict__ b
       int m, bb, m1;
       if (sample(o, m, bb, m1)) P[m - m_lo] = partial(bb, m1, m, 0, 1) * s2;
     }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Ic: column pass after F2f: inverse length-R2 FFTs, discard, detect, sum
+// ---------------------------------------------------------------------------
+
+// A CTA takes nl = min(TILE/R2, NCH) adjacent sub-channels c0.. of one m1 (one
+// contiguous block of F2f's output, rows k2 of nl elements), transforms them along k2
+// (v_c[m1 + J m2], m2 < R2), keeps the valid span m_lo <= m < m_hi, and detects.
+// With G = NCH / nl > 1 the CTAs of one m1 each write their group's partial
+// sum over sub-channels to part[g][m1][m2]; the last of the G to finish (an
+// atomic ticket per m1, no waiting) adds the G partials in group order into P
+// and clears the ticket.  P = scale^2 sum_c |v_c|^2.
+template <int R2>
+__global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict__ in, float* __restrict__ P,
+                                                        float* __restrict__ part, int* __restrict__ cnt,
+                                                        float2* __restrict__ vout, long long vstride,
+                                                        long long vofs, int logR1, int lognch, int logJ,
+                                                        int m_lo, int m_hi, float scale,
+                                                        const float2* __restrict__ tw) {
+  extern __shared__ float2 smem[];
+  __shared__ int s_last;
+  float2* stw = smem;
+  float2* sm = smem + stage_table_size(R2);
+  constexpr int LSTR = col_stride<R2>();
+  const int nl = min(TILE / R2, 1 << lognch);
+  const int lognl = __ffs(nl) - 1;
+  const int logG = lognch - lognl;
+  const int tot = nl * R2;
+  load_twiddles<R2>(stw, tw);
+  const int m1 = blockIdx.x >> logG, gi = blockIdx.x & ((1 << logG) - 1);
+  const float2* blk = in + (size_t)blockIdx.x * tot;   // block m1 G + g
+  const Lin<EPT> slot([&](unsigned idx) { return (unsigned)pidx((int)(idx & (nl - 1)), (int)(idx >> lognl), LSTR); });
+  float2 r[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) r[u] = blk[threadIdx.x + u * NT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u)
+    if ((int)threadIdx.x + u * NT < tot) sm[slot(u)] = r[u];
+  __syncthreads();
+  fft_lines<R2, true, false, LSTR>(sm, nl, stw, nullptr);
+  const float s2 = scale * scale;
+  for (int m2 = threadIdx.x; m2 < R2; m2 += NT) {
+    const int m = m1 + (m2 << logJ);
+    const bool ok = m >= m_lo && m < m_hi;
+    float p0 = 0.f, p1 = 0.f;
+    for (int b = 0; b < nl; ++b) {
+      const float2 v = sm[pidx(b, m2, LSTR)];
+      p0 = fmaf(v.x, v.x, p0);
+      p1 = fmaf(v.y, v.y, p1);
+      if (vout && ok) vout[(size_t)((gi << lognl) + b) * vstride + vofs + (m - m_lo)] = cscale(v, scale);
+    }
+    if (logG == 0) {
+      if (ok) P[m - m_lo] = (p0 + p1) * s2;
+    } else {
+      part[((((size_t)gi << logJ) + m1) << ilog2c(R2)) + m2] = p0 + p1;
+    }
+  }
+  if (logG == 0) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int t = atomicAdd(cnt + m1, 1);
+    s_last = t == (1 << logG) - 1;
+    if (s_last) cnt[m1] = 0;   // every group has taken its ticket
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int m2 = threadIdx.x; m2 < R2; m2 += NT) {
+    const int m = m1 + (m2 << logJ);
+    if (m < m_lo || m >= m_hi) continue;
+    float q = 0.f;
+    for (int g = 0; g < (1 << logG); ++g) q += __ldcg(part + ((((size_t)g << logJ) + m1) << ilog2c(R2)) + m2);
+    P[m - m_lo] = q * s2;
   }
 }
 

@@ -95,6 +95,17 @@ cudaError_t launch_inv_cols(const Geom& g, const float2* in, float2* out, const 
 cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* vout, long long vstride,
                             long long vofs, int m_lo, int m_hi, const float2* tw3M, const float2* tw,
                                cudaStream_t st);
+// Fused schedule (F1, F2f, Ic) for single-trial FP32 plans whose geometry has
+// J = M / R2 = FUSED_J; fused_groups = sub-channel groups per m1 in Ic.
+constexpr int FUSED_J = 64;
+bool fused_geometry(const Geom& g);
+int fused_groups(const Geom& g);
+cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L,
+                                const float2* tw, const float2* twJ, const ChirpAnchor* anc, int clog,
+                                cudaStream_t st);
+cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
+                                long long vstride, long long vofs, int m_lo, int m_hi, const float2* tw,
+                                cudaStream_t st);
 size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,

@@ -26,6 +26,8 @@ POND_E_UNIMPLEMENTED = -9
 POND_FP32 = 0
 POND_SPLIT_BF16 = 1
 POND_SPLIT_BF16_5T = 2
+POND_SCHEDULE_AUTO = 0
+POND_SCHEDULE_FOUR_PASS = 1
 POND_NSTAGE = 8
 POND_NOALLOC_MAX_NBINS = 1024
 
@@ -58,7 +60,7 @@ class pond_opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("ndm", ctypes.c_int32), ("dm_list", ctypes.POINTER(ctypes.c_double)),
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class pond_meta(ctypes.Structure):
@@ -174,7 +176,8 @@ class Engine:
     def __init__(self, f0: float, bw: float, fs: float, dm: float, nfft: int, nchan: int, nbins: int,
                  period: float, t_dec: float = 61.44e-6, want_voltages: bool = False,
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
-                 precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False):
+                 precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
+                 schedule: int = POND_SCHEDULE_AUTO):
         """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
@@ -185,6 +188,7 @@ class Engine:
         o.want_voltages = int(bool(want_voltages))
         o.timing = int(bool(timing))
         o.device = device
+        o.schedule = schedule
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])

@@ -32,9 +32,10 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
-def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6):
+def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6,
+               schedule=pond.POND_SCHEDULE_AUTO):
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
-                     want_voltages=want_voltages) as e:
+                     want_voltages=want_voltages, schedule=schedule) as e:
         if device_push:
             import torch
             t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -103,6 +104,40 @@ def test_matches_oracle(cfg):
     r = pcd.run(p, x, want_voltages=True)
     check(out, r)
     assert out["stats"]["outputs"] == len(r.power)
+
+
+# Plans with M / R2 = 64 (R1 = 64 nchan of 512..4096) run the three-pass
+# schedule: F2 also applies Eq. 4 and a length-64 inverse factor per
+# sub-channel, one column pass finishes each sub-channel's inverse and detects.
+# Its column pass takes min(8192 / R2, nchan) sub-channels per CTA, so these
+# cover one, two, four and sixteen sub-channel groups per output column.
+THREE_PASS = [
+    (1 << 18, 8, 1.0, 16.0, 128, 0.03),
+    (1 << 21, 16, 3.0, -16.0, 256, 0.07),
+    (1 << 22, 32, 5.0, 16.0, 512, 0.11),
+    (1 << 24, 64, 26.8, 16.0, 1024, 0.7145),
+]
+
+
+@pytest.mark.parametrize("cfg", THREE_PASS, ids=lambda c: f"N{c[0]}_c{c[1]}_dm{c[2]}_bw{c[3]}")
+def test_three_pass_schedule(cfg):
+    """Both schedules of the same plan against the oracle, and the three-pass
+    one runs four kernels per segment where the four-pass one runs five."""
+    nfft, nchan, dm, bw, nbins, period = cfg
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
+    if nfft >= 1 << 24:
+        x = synth.make_stream(synth.StreamSpec(n=p.nfft + p.S // 2 + 7, seed=5, dm=dm, period=period, snr=40.0,
+                                               duty=0.05, bw=bw, rfi_duty=0.005))
+    else:
+        x = _stream(p, seed=nfft + 3, extra=29)
+    r = pcd.run(p, x, want_voltages=True)
+    three = run_engine(x, p, chunks=[len(x) // 3, len(x) - len(x) // 3])
+    four = run_engine(x, p, schedule=pond.POND_SCHEDULE_FOUR_PASS)
+    check(three, r)
+    check(four, r)
+    segs = three["stats"]["segments"]
+    assert segs == four["stats"]["segments"] and segs >= 2
+    assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
 
 
 def test_streaming_invariance_bit_exact():
