@@ -636,7 +636,7 @@ def main():
     # the host link's copy rate at this moment: the e2e step overlaps the copies with the
     # compute, so it is copy-bound only when this rate falls below n / device step time
     h2d_s = []
-    for _ in range(2):
+    for _ in range(4):
         t0 = time.perf_counter()
         x_dev.copy_(x_host, non_blocking=True)
         torch.cuda.synchronize()
@@ -673,7 +673,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, nseg, samples, dt = oracle_rate(xh[:8 * (1 << 24)], seconds_budget=20.0)
+        v, nseg, samples, dt = oracle_rate(xh[:64 * (1 << 24)], seconds_budget=20.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nseg} whole nfft-2^24 segments ({samples} samples advanced) of the same stream, "
                          f"{dt:.1f} s of FP64 numpy on 1 host thread"}

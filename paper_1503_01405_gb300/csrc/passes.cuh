@@ -298,7 +298,7 @@ __device__ __forceinline__ void f2_load(const float2* __restrict__ in, float2* s
 // B = conj(Z[L-k]), E = (A + B)/2, O = (A - B)/2 and W = exp(-i pi k / L),
 //   X[k] = E - i W O   and   X[L-k] = conj(E) - i conj(W O),
 // so one item produces both bins of a pair (slot t < np, column k1) and
-// (slot t + np, column R1-1-k1), handed to emit(slot, k1, X).  In tile 0 lines
+// (slot t + np, column R1-1-k1), handed to emit(slot, row, k1, X).  In tile 0 lines
 // 0 and R2/2 pair with themselves: line 0 pairs columns k1 and R1-k1 (k1 = 0
 // and R1/2 alone), line R2/2 columns k1 and R1-1-k1.  Both bins of a pair are
 // read before either is emitted, so emit may overwrite them in sm.
@@ -307,18 +307,19 @@ __device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int
                                          Emit emit) {
   constexpr int LOGR1 = ilog2c(R1);
   const unsigned lmask = (1u << logL) - 1;
-  auto split_w = [&](int sa, int ka, int sb, int kb, bool both, float2 W) {
+  auto split_w = [&](int sa, int ra, int ka, int sb, int rb, int kb, bool both, float2 W) {
     const float2 A = sm[pidx(sa, ka, LSTR)];
     const float2 B = cconj(sm[pidx(sb, kb, LSTR)]);
     const float2 E = cscale(cadd(A, B), 0.5f);
     const float2 O = cscale(csub(A, B), 0.5f);
     const float2 WO = cmul(W, O);
-    emit(sa, ka, cadd(E, rot90<false>(WO)));
-    if (both) emit(sb, kb, cadd(cconj(E), rot90<false>(cconj(WO))));
+    emit(sa, ra, ka, cadd(E, rot90<false>(WO)));
+    if (both) emit(sb, rb, kb, cadd(cconj(E), rot90<false>(cconj(WO))));
   };
   auto split = [&](int sa, int ka, int sb, int kb, bool both) {
-    const unsigned k = (unsigned)f2_line(sa, q0, np, R2) + ((unsigned)ka << logR2);
-    split_w(sa, ka, sb, kb, both, tw2(tw2L, k & lmask));
+    const int ra = f2_line(sa, q0, np, R2), rb = f2_line(sb, q0, np, R2);
+    const unsigned k = (unsigned)ra + ((unsigned)ka << logR2);
+    split_w(sa, ra, ka, sb, rb, kb, both, tw2(tw2L, k & lmask));
   };
   // a thread's items of one row are NT columns apart, so W advances by
   // exp(-i pi NT R2 / L) (refreshed from the table every fourth item)
@@ -326,10 +327,15 @@ __device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int
   const float2 wstep = tw2(tw2L, ((unsigned)NT << logR2) & lmask);
   float2 W = make_float2(1.f, 0.f);
   const int items = np * R1;
-  int u = 0;
+  int u = 0, tl = -1, ra = 0, rb = 0;
 #pragma unroll 2
   for (int it = threadIdx.x; it < items; it += NT, ++u) {
     const int t = it >> LOGR1, k1 = it & (R1 - 1);
+    if (t != tl) {
+      tl = t;
+      ra = f2_line(t, q0, np, R2);
+      rb = f2_line(t + np, q0, np, R2);
+    }
     if (q0 == 0 && t == 0) {
       if (k1 == 0) {
         split(0, 0, 0, 0, false);
@@ -342,8 +348,8 @@ __device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int
       }
     } else {
       if (UPI > 1 && u % UPI != 0 && (u & 3) != 0) W = cmul(W, wstep);
-      else W = tw2(tw2L, ((unsigned)f2_line(t, q0, np, R2) + ((unsigned)k1 << logR2)) & lmask);
-      split_w(t, k1, t + np, R1 - 1 - k1, true, W);
+      else W = tw2(tw2L, ((unsigned)ra + ((unsigned)k1 << logR2)) & lmask);
+      split_w(t, ra, k1, t + np, rb, R1 - 1 - k1, true, W);
     }
   }
 }
@@ -372,8 +378,8 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   __syncthreads();
   fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
-  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int k1, float2 X) {
-    out[((unsigned)f2_line(slot, q0, np, R2) << LOGR1) + (unsigned)k1] = X;
+  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int, int row, int k1, float2 X) {
+    out[((unsigned)row << LOGR1) + (unsigned)k1] = X;
   });
 }
 
@@ -417,18 +423,18 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   load_twiddles<J>(stwj, twJ);
   const int q0 = blockIdx.x * np;
   f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
-  __syncthreads();
-  fft_lines<R1, false, false, LSTR>(sm, nl, stw, nullptr);
-  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int k1, float2 X) {
-    const unsigned k = (unsigned)f2_line(slot, q0, np, R2) + ((unsigned)k1 << logR2);
-    const ChirpAnchor a = anc[k >> clog];
-    sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
-  });
-  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
+  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L (st3 is in)
   for (int i = threadIdx.x; i < nl * J; i += NT) {
     const unsigned k2 = (unsigned)f2_line(i >> LOGJ, q0, np, R2), m1 = (unsigned)(i & (J - 1));
     twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
   }
+  __syncthreads();
+  fft_lines<R1, false, false, LSTR>(sm, nl, stw, nullptr);
+  f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int row, int k1, float2 X) {
+    const unsigned k = (unsigned)row + ((unsigned)k1 << logR2);
+    const ChirpAnchor a = anc[k >> clog];   // every row spans the band: L1/L2-resident table
+    sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
+  });
   __syncthreads();
   fft_lines<J, true, false, J + J / 16>(sm, nl * NCH, stwj, nullptr);
   // idx bits: [0,2) c, [2,4) m1, then the rest of c, the rest of m1, the slot;
@@ -527,7 +533,9 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols(const float2* __restrict__ i
     if ((int)threadIdx.x + u * NT < tot) {
       if (anc) {
         const unsigned k = kbin(u);
-        const ChirpAnchor& a = staged ? sanc[(int)((long long)(k >> clog) - a_lo)] : anc[k >> clog];
+        ChirpAnchor a;
+        if (staged) a = sanc[(int)((long long)(k >> clog) - a_lo)];
+        else a = anc[k >> clog];
         r[u] = cmul(r[u], chirp_from(a, clog, k));
       }
       sm[slot(u)] = r[u];
