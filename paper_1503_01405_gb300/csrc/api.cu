@@ -24,6 +24,7 @@
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <tuple>
 #include <vector>
 
@@ -63,6 +64,7 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr double K_DM = 1.0 / 2.41e-4;          // s MHz^2 (Eq. 1 constant)
 constexpr long long STAGE_BYTES = 256ll << 20;  // host-push staging chunk
+constexpr long long FIRST_STAGE_BYTES = 32ll << 20;  // first piece of a stream's host push
 constexpr long long TS_RING_SINGLE = 1ll << 22; // time-series samples held on the device (one trial)
 constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched plan
 constexpr int MAX_TRIALS = 4096;
@@ -183,6 +185,7 @@ struct pond_s {
   long long ts_first = -1, ts_drained = 0, ts_hi = 0, ts_complete = 0;
   std::vector<std::vector<float>> ts_host;  // per trial
   std::vector<int32_t> ts_host_cnt;
+  void* ts_pin = nullptr;                   // pinned staging of one ring row (ring * 4 B)
   long long ts_host_first = 0;
   // voltages: device [v_base, v_base + v_len), host spill before that
   long long v_len = 0, v_base = -1;
@@ -433,24 +436,37 @@ int spill_ts(pond_t h) {
   const long long n = h->ts_complete - h->ts_drained;
   const int ntr = (int)h->trials.size();
   if (h->ts_host[0].empty()) h->ts_host_first = h->ts_drained;
-  const size_t off = h->ts_host[0].size();
-  for (int d = 0; d < ntr; ++d) h->ts_host[d].resize(off + n);
-  h->ts_host_cnt.resize(off + n);
-  long long j = h->ts_drained, done = 0;
-  while (done < n) {
-    const long long slot = j % h->ring;
-    const long long run = std::min(n - done, h->ring - slot);
-    for (int d = 0; d < ntr; ++d) {
-      CK(cudaMemcpyAsync(h->ts_host[d].data() + off + done, h->ts + (size_t)d * h->ring + slot, run * sizeof(float),
-                         cudaMemcpyDeviceToHost, h->st));
-      CK(cudaMemsetAsync(h->ts + (size_t)d * h->ring + slot, 0, run * sizeof(float), h->st));
+  // each ring row (a trial's sums, then the counts) passes through a pinned
+  // buffer: device-to-pageable copies are several times slower
+  if (!h->ts_pin) CK(cudaMallocHost(&h->ts_pin, (size_t)h->ring * sizeof(float)));
+  const long long slot0 = h->ts_drained % h->ring;
+  auto drain = [&](auto* dev_row, auto& vec) -> int {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    static_assert(sizeof(T) == sizeof(float), "4-byte ring rows");
+    long long done = 0, slot = slot0;
+    while (done < n) {
+      const long long run = std::min(n - done, h->ring - slot);
+      CK(cudaMemcpyAsync(static_cast<T*>(h->ts_pin) + done, dev_row + slot, run * sizeof(T), cudaMemcpyDeviceToHost,
+                         h->st));
+      CK(cudaMemsetAsync(dev_row + slot, 0, run * sizeof(T), h->st));
+      done += run;
+      slot = 0;
     }
-    CK(cudaMemcpyAsync(h->ts_host_cnt.data() + off + done, h->ts_cnt + slot, run * sizeof(int),
-                       cudaMemcpyDeviceToHost, h->st));
-    for (int d = 0; d < ntr; ++d)
+    CK(cudaStreamSynchronize(h->st));
+    const T* p = static_cast<const T*>(h->ts_pin);
+    vec.insert(vec.end(), p, p + n);
+    return POND_OK;
+  };
+  for (int d = 0; d < ntr; ++d) RC(drain(h->ts + (size_t)d * h->ring, h->ts_host[d]));
+  RC(drain(h->ts_cnt, h->ts_host_cnt));
+  for (int d = 1; d < ntr; ++d) {   // every trial's counts row is the same: clear the others
+    long long done = 0, slot = slot0;
+    while (done < n) {
+      const long long run = std::min(n - done, h->ring - slot);
       CK(cudaMemsetAsync(h->ts_cnt + (size_t)d * h->ring + slot, 0, run * sizeof(int), h->st));
-    done += run;
-    j += run;
+      done += run;
+      slot = 0;
+    }
   }
   CK(cudaStreamSynchronize(h->st));
   h->ts_drained = h->ts_complete;
@@ -652,6 +668,7 @@ void destroy_all(pond_t h) {
   cudaFree(h->phits);
   cudaFree(h->ts);
   cudaFree(h->ts_cnt);
+  if (h->ts_pin) cudaFreeHost(h->ts_pin);
   cudaFree(h->stage[0]);
   cudaFree(h->stage[1]);
   cudaFree(h->vbuf);
@@ -1041,8 +1058,10 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     CK(cudaEventRecord(h->ev_used[1], h->st));
   }
   cudaEvent_t last = nullptr;
-  for (size_t off = 0; off < n; off += STAGE_BYTES) {
-    const long long len = std::min<long long>(STAGE_BYTES, (long long)(n - off));
+  for (size_t off = 0; off < n;) {
+    // a short first piece of a stream lets the passes start while the rest is copied
+    const long long cap = (h->total_in == 0 && off == 0) ? FIRST_STAGE_BYTES : STAGE_BYTES;
+    const long long len = std::min<long long>(cap, (long long)(n - off));
     const int i = h->stage_next;
     h->stage_next ^= 1;
     CK(cudaStreamWaitEvent(h->cst, h->ev_used[i], 0));
@@ -1052,6 +1071,7 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     RC(ingest_device(h, h->stage[i], len));
     CK(cudaEventRecord(h->ev_used[i], h->st));
     last = h->ev_copied[i];
+    off += (size_t)len;
   }
   // the caller's buffer is free once the copies have landed
   if (last) CK(cudaEventSynchronize(last));

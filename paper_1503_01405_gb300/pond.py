@@ -249,8 +249,8 @@ class Engine:
         rows = max(1, self.ndm)
         parts, cparts, first = [], [], None
         while True:
-            out = np.zeros((rows, cap), dtype=np.float32)
-            cnt = np.zeros(cap, dtype=np.int32)
+            out = np.empty((rows, cap), dtype=np.float32)   # the library fills [:, :n]
+            cnt = np.empty(cap, dtype=np.int32)
             n = ctypes.c_size_t()
             j0 = ctypes.c_int64()
             _check(lib().pond_timeseries(self._h, _ptr(out), _ptr(cnt), cap, ctypes.byref(n),
@@ -263,8 +263,11 @@ class Engine:
             cparts.append(cnt[:n.value])
             if n.value < cap:
                 break
-        T = np.concatenate(parts, axis=1) if parts else np.zeros((rows, 0), np.float32)
-        C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
+        if len(parts) == 1:   # a single drain: no concatenation (rows of a batched plan made contiguous)
+            T, C = (parts[0] if rows == 1 else np.ascontiguousarray(parts[0])), cparts[0]
+        else:
+            T = np.concatenate(parts, axis=1) if parts else np.zeros((rows, 0), np.float32)
+            C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
         return (T if self.ndm else T[0]), C, first
 
     def candidates(self, threshold: float = 6.0, cap: int = 1 << 16, classifier=None):
