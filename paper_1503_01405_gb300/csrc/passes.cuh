@@ -307,6 +307,7 @@ __device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int
                                          Emit emit) {
   constexpr int LOGR1 = ilog2c(R1);
   const unsigned lmask = (1u << logL) - 1;
+  int ra = 0, rb = 0;   // rows of the current slot pair
   auto split_w = [&](int sa, int ra, int ka, int sb, int rb, int kb, bool both, float2 W) {
     const float2 A = sm[pidx(sa, ka, LSTR)];
     const float2 B = cconj(sm[pidx(sb, kb, LSTR)]);
@@ -327,7 +328,27 @@ __device__ __forceinline__ void f2_split(float2* sm, int q0, int np, int R2, int
   const float2 wstep = tw2(tw2L, ((unsigned)NT << logR2) & lmask);
   float2 W = make_float2(1.f, 0.f);
   const int items = np * R1;
-  int u = 0, tl = -1, ra = 0, rb = 0;
+  if constexpr (R1 >= NT) {
+    if (q0 != 0) {
+      // every tile but tile 0: fully unrolled, a thread's items u are columns
+      // threadIdx.x + u NT of slot (u NT) / R1 (at most EPT/2 of them)
+#pragma unroll
+      for (int u = 0; u < EPT / 2; ++u) {
+        if (u * NT < items) {
+          const int t = (u * NT) >> LOGR1, k1 = (int)threadIdx.x + ((u * NT) & (R1 - 1));
+          if ((u * NT) % R1 == 0) {
+            ra = f2_line(t, q0, np, R2);
+            rb = f2_line(t + np, q0, np, R2);
+          }
+          if ((u * NT) % R1 != 0 && (u & 3) != 0) W = cmul(W, wstep);
+          else W = tw2(tw2L, ((unsigned)ra + ((unsigned)k1 << logR2)) & lmask);
+          split_w(t, ra, k1, t + np, rb, R1 - 1 - k1, true, W);
+        }
+      }
+      return;
+    }
+  }
+  int u = 0, tl = -1;
 #pragma unroll 2
   for (int it = threadIdx.x; it < items; it += NT, ++u) {
     const int t = it >> LOGR1, k1 = it & (R1 - 1);
