@@ -253,11 +253,16 @@ __device__ __forceinline__ void f2_load(const float2* __restrict__ in, float2* s
   const float4* in4 = reinterpret_cast<const float4*>(in);
   constexpr int H = EPT / 2;
   float4 r[H];
+  // with R1 >= 2 NT the slot of a load is fixed by u: (2 u NT) / R1
+  auto slot_of = [&](int u, int idx) { return R1 >= 2 * NT ? (2 * u * NT) >> LOGR1 : idx >> LOGR1; };
+  int rows[H];
 #pragma unroll
   for (int u = 0; u < H; ++u) {
     const int idx = 2 * (threadIdx.x + u * NT);
+    if (R1 >= 2 * NT && u > 0 && slot_of(u, idx) == slot_of(u - 1, idx)) rows[u] = rows[u - 1];
+    else rows[u] = f2_line(slot_of(u, idx), q0, np, R2);
     if (idx < tot) {
-      const unsigned k2 = (unsigned)f2_line(idx >> LOGR1, q0, np, R2), n1 = (unsigned)(idx & (R1 - 1));
+      const unsigned k2 = (unsigned)rows[u], n1 = (unsigned)(idx & (R1 - 1));
       r[u] = __ldg(in4 + (((k2 << LOGR1) + n1) >> 1));
     }
   }
@@ -271,8 +276,8 @@ __device__ __forceinline__ void f2_load(const float2* __restrict__ in, float2* s
   for (int u = 0; u < H; ++u) {
     const int idx = 2 * (threadIdx.x + u * NT);
     if (idx < tot) {
-      const int slot = idx >> LOGR1;
-      const unsigned k2 = (unsigned)f2_line(slot, q0, np, R2), n1 = (unsigned)(idx & (R1 - 1));
+      const int slot = slot_of(u, idx);
+      const unsigned k2 = (unsigned)rows[u], n1 = (unsigned)(idx & (R1 - 1));
       float2 wb;
       if constexpr (UPS > 1) {
         if (u % UPS == 0) {
