@@ -69,8 +69,8 @@ extern "C" {
 
 /* Pass schedule of a segment (Sec. 3.7 path, same outputs either way). */
 #define POND_SCHEDULE_AUTO 0       /* single-trial FP32 plans whose sub-channel length M is
-                                      64 times the forward column length R2 (e.g. nfft 2^24
-                                      with 64 sub-channels) run three passes: the forward
+                                      64 times the forward column length R2 >= 16 (e.g. nfft
+                                      2^24 with 64 sub-channels) run three passes: the forward
                                       row pass also applies Eq. 4 and the first length-64
                                       factor of each sub-channel's inverse DFT, and one
                                       column pass finishes the inverse, detects and sums

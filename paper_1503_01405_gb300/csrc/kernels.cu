@@ -464,12 +464,12 @@ cudaError_t launch_tables(ChirpAnchor* anc, long long nanc, int clog, double du,
   return cudaGetLastError();
 }
 
-// Fused schedule: F2f for R1 = 512..4096 with J = 64, Ic for R2 = 4..2048.
+// Fused schedule: F2f for R1 = 512..4096 with J = 64, Ic for R2 = 16..2048.
 #define POND_FUSED_R1(X) X(512) X(1024) X(2048) X(4096)
-#define POND_FUSED_R2(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+#define POND_FUSED_R2(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
 
 bool fused_geometry(const Geom& g) {
-  return g.logM - g.logR2 == 6 && g.logR1 >= 9 && g.logR1 <= 12 && g.logR2 >= 2 && g.logR2 <= 11;
+  return g.logM - g.logR2 == 6 && g.logR1 >= 9 && g.logR1 <= 12 && g.logR2 >= 4 && g.logR2 <= 11;
 }
 
 namespace {

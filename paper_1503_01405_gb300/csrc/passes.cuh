@@ -731,20 +731,35 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
   __syncthreads();
   fft_lines<R2, true, false, LSTR>(sm, nl, stw, nullptr);
   const float s2 = scale * scale;
-  for (int m2 = threadIdx.x; m2 < R2; m2 += NT) {
-    const int m = m1 + (m2 << logJ);
-    const bool ok = m >= m_lo && m < m_hi;
-    float p0 = 0.f, p1 = 0.f;
-    for (int b = 0; b < nl; ++b) {
-      const float2 v = sm[pidx(b, m2, LSTR)];
-      p0 = fmaf(v.x, v.x, p0);
-      p1 = fmaf(v.y, v.y, p1);
-      if (vout && ok) vout[(size_t)((gi << lognl) + b) * vstride + vofs + (m - m_lo)] = cscale(v, scale);
-    }
-    if (logG == 0) {
-      if (ok) P[m - m_lo] = (p0 + p1) * s2;
-    } else {
-      part[((((size_t)gi << logJ) + m1) << ilog2c(R2)) + m2] = p0 + p1;
+  constexpr int NLMAX = TILE / R2 < NT ? TILE / R2 : NT;   // nl <= NLMAX
+  constexpr int MPT = (R2 + NT - 1) / NT;                 // outputs per thread
+#pragma unroll
+  for (int q = 0; q < MPT; ++q) {
+    const int m2 = (int)threadIdx.x + q * NT;
+    if (m2 < R2) {
+      const int m = m1 + (m2 << logJ);
+      const bool ok = m >= m_lo && m < m_hi;
+      float p0 = 0.f, p1 = 0.f;
+      auto acc = [&](int b) {
+        const float2 v = sm[pidx(b, m2, LSTR)];
+        p0 = fmaf(v.x, v.x, p0);
+        p1 = fmaf(v.y, v.y, p1);
+      };
+      if constexpr (NLMAX <= 16) {
+#pragma unroll
+        for (int b = 0; b < NLMAX; ++b)
+          if (b < nl) acc(b);
+      } else {
+        for (int b = 0; b < nl; ++b) acc(b);
+      }
+      if (vout && ok)
+        for (int b = 0; b < nl; ++b)
+          vout[(size_t)((gi << lognl) + b) * vstride + vofs + (m - m_lo)] = cscale(sm[pidx(b, m2, LSTR)], scale);
+      if (logG == 0) {
+        if (ok) P[m - m_lo] = (p0 + p1) * s2;
+      } else {
+        part[((((size_t)gi << logJ) + m1) << ilog2c(R2)) + m2] = p0 + p1;
+      }
     }
   }
   if (logG == 0) return;
