@@ -773,12 +773,27 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  for (int m2 = threadIdx.x; m2 < R2; m2 += NT) {
+  // the G partials of an output are loaded together, then added in group order
+  constexpr int GMAX = 16;
+  const size_t gstride = (size_t)1 << (logJ + ilog2c(R2));   // part[g + 1] - part[g]
+#pragma unroll
+  for (int q = 0; q < MPT; ++q) {
+    const int m2 = (int)threadIdx.x + q * NT;
     const int m = m1 + (m2 << logJ);
-    if (m < m_lo || m >= m_hi) continue;
-    float q = 0.f;
-    for (int g = 0; g < (1 << logG); ++g) q += __ldcg(part + ((((size_t)g << logJ) + m1) << ilog2c(R2)) + m2);
-    P[m - m_lo] = q * s2;
+    if (m2 >= R2 || m < m_lo || m >= m_hi) continue;
+    const float* src = part + (((size_t)m1) << ilog2c(R2)) + m2;
+    float acc = 0.f;
+    if (logG <= 4) {
+      float v[GMAX];
+#pragma unroll
+      for (int g = 0; g < GMAX; ++g) v[g] = g < (1 << logG) ? __ldcg(src + g * gstride) : 0.f;
+#pragma unroll
+      for (int g = 0; g < GMAX; ++g)
+        if (g < (1 << logG)) acc += v[g];
+    } else {
+      for (int g = 0; g < (1 << logG); ++g) acc += __ldcg(src + g * gstride);
+    }
+    P[m - m_lo] = acc * s2;
   }
 }
 
