@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_partial(const float* _
 
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
 
+// Series samples spanning at most DEC_SPAN channel samples load them together.
+constexpr int DEC_SPAN = 16;
+
 // Fold + decimation of one segment's valid span [g0, g0 + n) in one launch.
 // CTA b owns the series samples j in [j_lo + b jpc, j_lo + (b+1) jpc) and the
 // channel samples they cover: it folds them (its histogram is added to
@@ -302,7 +305,17 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_dec(const float* __res
     for (long long j = ja + threadIdx.x; j < jb; j += blockDim.x) {
       const long long a = max(ceil_div_ll(j * num, den), g0), e = min(ceil_div_ll((j + 1) * num, den), g0 + n);
       float s = 0.f;
-      for (long long g = a; g < e; ++g) s += __ldg(P + (g - g0));
+      if (e - a <= DEC_SPAN) {
+        // loads issued together, added in sample order
+        float v[DEC_SPAN];
+#pragma unroll
+        for (int i = 0; i < DEC_SPAN; ++i) v[i] = a + i < e ? __ldg(P + (a + i - g0)) : 0.f;
+#pragma unroll
+        for (int i = 0; i < DEC_SPAN; ++i)
+          if (a + i < e) s += v[i];
+      } else {
+        for (long long g = a; g < e; ++g) s += __ldg(P + (g - g0));
+      }
       const long long slot = j % ring;
       T[slot] += s;
       C[slot] += (int)max(e - a, 0ll);

@@ -76,6 +76,9 @@ def test_engine_limits():
     with pytest.raises(pond.PondError) as e:
         pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1, precision=7)
     assert e.value.name == "ARG"
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(326.5, 16.0, 32e6, 0.1, 1 << 16, 4, 64, 0.1, schedule=2)
+    assert e.value.name == "ARG"
 
 
 def test_null_handle_and_pointers():
