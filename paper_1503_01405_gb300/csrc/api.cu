@@ -429,6 +429,41 @@ int collect_timing(pond_t h) {
 }
 
 // Move completed time-series samples of every trial from the device rings to the host.
+// Move n completed series samples, from ts_drained on, out of the device ring
+// into row d of dst (dst(d) returns its first element) and the counts into
+// cnt, through the pinned row buffer (device-to-pageable copies are several
+// times slower), and clear the ring slots they held.
+template <class DstRow>
+int drain_ts(pond_t h, long long n, DstRow dst, int32_t* cnt) {
+  const int ntr = (int)h->trials.size();
+  if (!h->ts_pin) CK(cudaMallocHost(&h->ts_pin, (size_t)h->ring * sizeof(float)));
+  const long long slot0 = h->ts_drained % h->ring;
+  auto row = [&](auto* dev_row, auto* out) -> int {
+    using T = typename std::remove_pointer<decltype(out)>::type;
+    static_assert(sizeof(T) == sizeof(float), "4-byte ring rows");
+    long long done = 0, slot = slot0;
+    while (done < n) {
+      const long long run = std::min(n - done, h->ring - slot);
+      if (out) CK(cudaMemcpyAsync(static_cast<T*>(h->ts_pin) + done, dev_row + slot, run * sizeof(T),
+                                  cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemsetAsync(dev_row + slot, 0, run * sizeof(T), h->st));
+      done += run;
+      slot = 0;
+    }
+    if (out) {
+      CK(cudaStreamSynchronize(h->st));
+      memcpy(out, h->ts_pin, n * sizeof(T));
+    }
+    return POND_OK;
+  };
+  for (int d = 0; d < ntr; ++d) RC(row(h->ts + (size_t)d * h->ring, dst(d)));
+  // every trial's counts row is the same: the first is returned, all are cleared
+  for (int d = 0; d < ntr; ++d) RC(row(h->ts_cnt + (size_t)d * h->ring, d == 0 ? cnt : (int32_t*)nullptr));
+  CK(cudaStreamSynchronize(h->st));
+  h->ts_drained += n;
+  return POND_OK;
+}
+
 int spill_ts(pond_t h) {
   if (h->ts_first < 0 || h->ts_complete <= h->ts_drained) return POND_OK;
   RC(join_streams(h));
@@ -436,41 +471,10 @@ int spill_ts(pond_t h) {
   const long long n = h->ts_complete - h->ts_drained;
   const int ntr = (int)h->trials.size();
   if (h->ts_host[0].empty()) h->ts_host_first = h->ts_drained;
-  // each ring row (a trial's sums, then the counts) passes through a pinned
-  // buffer: device-to-pageable copies are several times slower
-  if (!h->ts_pin) CK(cudaMallocHost(&h->ts_pin, (size_t)h->ring * sizeof(float)));
-  const long long slot0 = h->ts_drained % h->ring;
-  auto drain = [&](auto* dev_row, auto& vec) -> int {
-    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
-    static_assert(sizeof(T) == sizeof(float), "4-byte ring rows");
-    long long done = 0, slot = slot0;
-    while (done < n) {
-      const long long run = std::min(n - done, h->ring - slot);
-      CK(cudaMemcpyAsync(static_cast<T*>(h->ts_pin) + done, dev_row + slot, run * sizeof(T), cudaMemcpyDeviceToHost,
-                         h->st));
-      CK(cudaMemsetAsync(dev_row + slot, 0, run * sizeof(T), h->st));
-      done += run;
-      slot = 0;
-    }
-    CK(cudaStreamSynchronize(h->st));
-    const T* p = static_cast<const T*>(h->ts_pin);
-    vec.insert(vec.end(), p, p + n);
-    return POND_OK;
-  };
-  for (int d = 0; d < ntr; ++d) RC(drain(h->ts + (size_t)d * h->ring, h->ts_host[d]));
-  RC(drain(h->ts_cnt, h->ts_host_cnt));
-  for (int d = 1; d < ntr; ++d) {   // every trial's counts row is the same: clear the others
-    long long done = 0, slot = slot0;
-    while (done < n) {
-      const long long run = std::min(n - done, h->ring - slot);
-      CK(cudaMemsetAsync(h->ts_cnt + (size_t)d * h->ring + slot, 0, run * sizeof(int), h->st));
-      done += run;
-      slot = 0;
-    }
-  }
-  CK(cudaStreamSynchronize(h->st));
-  h->ts_drained = h->ts_complete;
-  return POND_OK;
+  const size_t off = h->ts_host[0].size();
+  for (int d = 0; d < ntr; ++d) h->ts_host[d].resize(off + n);
+  h->ts_host_cnt.resize(off + n);
+  return drain_ts(h, n, [&](int d) { return h->ts_host[d].data() + off; }, h->ts_host_cnt.data() + off);
 }
 
 int spill_voltages(pond_t h) {
@@ -1175,6 +1179,22 @@ int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n
   *n_out = 0;
   *first_index = h->ts_host[0].empty() ? std::max(h->ts_drained, 0ll) : h->ts_host_first;
   if (h->ts_first < 0) return POND_OK;
+  if (h->ts_host[0].empty() && h->ts_complete > h->ts_drained) {
+    // nothing held on the host: drain the device ring straight into the caller's rows
+    RC(join_streams(h));
+    CK(cudaStreamSynchronize(h->st));
+    const long long n = std::min<long long>((long long)cap, h->ts_complete - h->ts_drained);
+    *first_index = h->ts_drained;
+    int32_t* cnt = counts;
+    std::vector<int32_t> scratch;
+    if (!cnt) {
+      scratch.resize((size_t)n);
+      cnt = scratch.data();
+    }
+    RC(drain_ts(h, n, [&](int d) { return out + (size_t)d * cap; }, cnt));
+    *n_out = (size_t)n;
+    return POND_OK;
+  }
   RC(spill_ts(h));
   const size_t n = std::min(cap, h->ts_host[0].size());
   if (n) {
