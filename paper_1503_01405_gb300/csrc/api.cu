@@ -63,7 +63,7 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 constexpr double K_DM = 1.0 / 2.41e-4;          // s MHz^2 (Eq. 1 constant)
-constexpr long long STAGE_BYTES = 256ll << 20;  // host-push staging chunk
+constexpr long long STAGE_BYTES = 128ll << 20;  // host-push staging chunk
 constexpr long long FIRST_STAGE_BYTES = 32ll << 20;  // first piece of a stream's host push
 constexpr long long TS_RING_SINGLE = 1ll << 22; // time-series samples held on the device (one trial)
 constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched plan
@@ -157,11 +157,15 @@ struct pond_s {
   // streams
   cudaStream_t st = nullptr, cst = nullptr;
   // streams of segments s with s mod NSLOT = 1 .. NSLOT-1 (slot 0 runs on st);
-  // joined into st after every push and flush
+  // joined into st by every call that reads results or hands a buffer back
   cudaStream_t sx[NSLOT] = {};
   cudaEvent_t ev_in = nullptr, ev_join[NSLOT] = {};
   cudaEvent_t ev_done = nullptr, ev_caller = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  // side-stream work of the last two ingests (carry reuse) and of the segments
+  // that read each staging buffer (staging reuse)
+  cudaEvent_t ev_side[2][NSLOT] = {}, ev_used_x[2][NSLOT] = {};
+  int ingest_par = 0;
   // fold (single-DM plans)
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
@@ -603,7 +607,8 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   return POND_OK;
 }
 
-// Ingest n samples at device pointer d into every lane (work ordered on h->st).
+// Ingest n samples at device pointer d into every lane (work ordered on h->st
+// and the side streams; callers that read results or release d join them).
 int ingest_device(pond_t h, const int8_t* d, long long n) {
   const long long end = h->total_in + n;
   RC(fork_streams(h));
@@ -626,8 +631,18 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
       RC(run_segment(h, (int)li, in, ln.seg_start / g.S, 1ll << 62));
       ln.seg_start += g.S;
     }
-    // the segment streams read the input and the carry: the carry update waits for them
-    RC(join_streams(h));
+  }
+  // Each lane's carry is double-buffered: the buffer rewritten below was last
+  // read by the previous ingest's segments, so st waits for that ingest's
+  // side-stream work (recorded then), not for this one's.
+  const int par = h->ingest_par;
+  for (int k = 1; k < NSLOT; ++k) {
+    CK(cudaEventRecord(h->ev_side[par][k], h->sx[k]));
+    CK(cudaStreamWaitEvent(h->st, h->ev_side[1 - par][k], 0));
+  }
+  h->ingest_par = 1 - par;
+  for (size_t li = 0; li < h->lanes.size(); ++li) {
+    Lane& ln = h->lanes[li];
     // keep [seg_start, end) for the lane's next segment
     int8_t* dst = ln.carry[1 - ln.carry_cur];
     if (ln.seg_start < h->total_in) {
@@ -692,6 +707,10 @@ void destroy_all(pond_t h) {
   if (h->st) cudaStreamDestroy(h->st);
   for (int k = 1; k < NSLOT; ++k) {
     if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
+    for (int i = 0; i < 2; ++i) {
+      if (h->ev_side[i][k]) cudaEventDestroy(h->ev_side[i][k]);
+      if (h->ev_used_x[i][k]) cudaEventDestroy(h->ev_used_x[i][k]);
+    }
     if (h->sx[k]) cudaStreamDestroy(h->sx[k]);
   }
   if (h->cst) cudaStreamDestroy(h->cst);
@@ -920,6 +939,10 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   for (int k = 1; k < NSLOT; ++k) {
     CKD(cudaStreamCreateWithFlags(&h->sx[k], cudaStreamNonBlocking));
     CKD(cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) {
+      CKD(cudaEventCreateWithFlags(&h->ev_side[i][k], cudaEventDisableTiming));
+      CKD(cudaEventCreateWithFlags(&h->ev_used_x[i][k], cudaEventDisableTiming));
+    }
   }
   CKD(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
@@ -1046,6 +1069,7 @@ int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream) {
   cudaStream_t cs = (cudaStream_t)cuda_stream;
   RC(caller_wait(h, cs));
   RC(ingest_device(h, d_x, (long long)n));
+  RC(join_streams(h));   // every segment that read d_x precedes the release
   return caller_release(h, cs);
 }
 
@@ -1069,11 +1093,13 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     const int i = h->stage_next;
     h->stage_next ^= 1;
     CK(cudaStreamWaitEvent(h->cst, h->ev_used[i], 0));
+    for (int k = 1; k < NSLOT; ++k) CK(cudaStreamWaitEvent(h->cst, h->ev_used_x[i][k], 0));
     CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
     CK(cudaEventRecord(h->ev_copied[i], h->cst));
     CK(cudaStreamWaitEvent(h->st, h->ev_copied[i], 0));
     RC(ingest_device(h, h->stage[i], len));
     CK(cudaEventRecord(h->ev_used[i], h->st));
+    for (int k = 1; k < NSLOT; ++k) CK(cudaEventRecord(h->ev_used_x[i][k], h->sx[k]));
     last = h->ev_copied[i];
     off += (size_t)len;
   }
@@ -1121,6 +1147,7 @@ int pond_reset(pond_t h) {
   if (!h) return fail(POND_E_ARG, "null handle");
   CK(cudaSetDevice(h->device));
   RC(collect_timing(h));
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   const int ntr = (int)h->trials.size();
   if (!h->multi) {
@@ -1156,6 +1183,7 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta) {
   if (!h) return fail(POND_E_ARG, "null handle");
   if (h->multi) return fail(POND_E_STATE, "a batched plan does not fold");
   CK(cudaSetDevice(h->device));
+  RC(join_streams(h));
   CK(launch_fold_snapshot(h->psum, h->phits, h->nbins, h->prof_sum, h->prof_hits, h->st));
   if (sum) CK(cudaMemcpyAsync(sum, h->prof_sum, h->nbins * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (hits) CK(cudaMemcpyAsync(hits, h->prof_hits, h->nbins * sizeof(long long), cudaMemcpyDeviceToHost, h->st));
@@ -1249,6 +1277,7 @@ static int candidates_impl(pond_t h, pond_cnn_t net, double threshold, pond_cand
   CK(cudaSetDevice(h->device));
   *n_found = 0;
   if (h->ts_first < 0) return POND_OK;
+  RC(join_streams(h));
   CK(cudaStreamSynchronize(h->st));
   const long long j0 = h->ts_drained, n = h->ts_complete - h->ts_drained;
   if (n <= 0) return POND_OK;
