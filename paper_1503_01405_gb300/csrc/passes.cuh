@@ -720,14 +720,35 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
   load_twiddles<R2>(stw, tw);
   const int m1 = blockIdx.x >> logG, gi = blockIdx.x & ((1 << logG) - 1);
   const float2* blk = in + (size_t)blockIdx.x * tot;   // block m1 G + g
-  const Lin<EPT> slot([&](unsigned idx) { return (unsigned)pidx((int)(idx & (nl - 1)), (int)(idx >> lognl), LSTR); });
-  float2 r[EPT];
+  if (nl >= 2) {
+    // 16-byte loads: elements 2i, 2i + 1 (sub-channels ci, ci + 1 of row k2)
+    constexpr int H = EPT / 2;
+    const float4* blk4 = reinterpret_cast<const float4*>(blk);
+    const Lin<H> slot([&](unsigned i) {
+      return (unsigned)pidx((int)((2 * i) & (nl - 1)), (int)((2 * i) >> lognl), LSTR);
+    });
+    float4 r[H];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u)
-    if ((int)threadIdx.x + u * NT < tot) r[u] = blk[threadIdx.x + u * NT];
+    for (int u = 0; u < H; ++u)
+      if (2 * ((int)threadIdx.x + u * NT) < tot) r[u] = blk4[threadIdx.x + u * NT];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u)
-    if ((int)threadIdx.x + u * NT < tot) sm[slot(u)] = r[u];
+    for (int u = 0; u < H; ++u) {
+      if (2 * ((int)threadIdx.x + u * NT) < tot) {
+        float2* p = sm + slot(u);
+        p[0] = make_float2(r[u].x, r[u].y);
+        p[LSTR] = make_float2(r[u].z, r[u].w);
+      }
+    }
+  } else {
+    const Lin<EPT> slot([&](unsigned idx) { return (unsigned)pidx(0, (int)idx, LSTR); });
+    float2 r[EPT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u)
+      if ((int)threadIdx.x + u * NT < tot) r[u] = blk[threadIdx.x + u * NT];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u)
+      if ((int)threadIdx.x + u * NT < tot) sm[slot(u)] = r[u];
+  }
   __syncthreads();
   fft_lines<R2, true, false, LSTR>(sm, nl, stw, nullptr);
   const float s2 = scale * scale;
