@@ -140,15 +140,22 @@ def test_three_pass_schedule(cfg):
     assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
 
 
-def test_streaming_invariance_bit_exact():
-    p = pcd.make_plan(326.5, 16.0, 32e6, 0.3, 1 << 16, 16, 128, 0.033)
+@pytest.mark.parametrize("plan", [(1 << 16, 16, 0.3, 128, 0.033), (1 << 21, 16, 3.0, 256, 0.07)],
+                         ids=["four_pass", "three_pass"])
+def test_streaming_invariance_bit_exact(plan):
+    """Outputs do not depend on how the stream is cut into pushes (host or device),
+    down to the bit: every reduction has a fixed order and the segment streams
+    are ordered by events wherever they share a buffer."""
+    nfft, nchan, dm, nbins, period = plan
+    p = pcd.make_plan(326.5, 16.0, 32e6, dm, nfft, nchan, nbins, period)
     x = _stream(p, seed=5, extra=999)
     ref = run_engine(x, p)
     rng = np.random.default_rng(1)
+    sizes = [0, 1, 7, 1000, 65536, 100_000, 300_001] if nfft < 1 << 20 else [0, 7, 65536, 1_000_003, 3_000_017]
     cuts = []
     left = len(x)
     while left > 0:
-        c = int(min(left, rng.choice([0, 1, 7, 1000, 65536, 100_000, 300_001])))
+        c = int(min(left, rng.choice(sizes)))
         cuts.append(c)
         left -= c
     for dev in (False, True):
