@@ -462,29 +462,44 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
     sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
   });
   __syncthreads();
-  fft_lines<J, true, false, J + J / 16>(sm, nl * NCH, stwj, nullptr);
-  // idx bits: [0,2) c, [2,4) m1, then the rest of c, the rest of m1, the slot;
-  // a half-warp reads 4 runs x 4 elements (banks 4c + m1 apart: distinct) and
-  // writes 4 x 32 contiguous bytes
-  auto cof = [](unsigned idx) { return (idx & 3u) | (((idx >> 4) & (NCH / 4 - 1)) << 2); };
-  auto mof = [](unsigned idx) { return ((idx >> 2) & 3u) | (((idx >> (LOGNCH + 2)) & (J / 4 - 1)) << 2); };
+  // Length-J inverse DFT of every (slot, c) run, four lanes of one warp per run
+  // (run = threadIdx.x / 4, lane t4): the Stockham radix-16 step (outputs of
+  // butterfly t4 to 16 t4 + k) in registers, the exchange through the run's own
+  // line with warp-level barriers, the radix-4 step (butterflies t4 + 4q, outputs
+  // to t' + 16 j), then e^{2 pi i k2 m1 / M} and the blocked store from registers.
+  static_assert(J == 64, "radix-16 x radix-4 runs");
   const int lognl = min(13 - logR2, LOGNCH);      // Ic's sub-channels per CTA (log2)
-  // block (m1 G + g) of R2 nl elements, row k2 (added per u), sub-channel ci
-  const Lin<EPT> oofs([&](unsigned idx) {
-    const unsigned c = cof(idx);
-    return ((((mof(idx) << (LOGNCH - lognl)) + (c >> lognl)) << logR2) << lognl) + (c & ((1u << lognl) - 1));
-  });
-  const Lin<EPT> sidx([&](unsigned idx) {
-    return (unsigned)pidx((int)(idx >> LOGR1), (int)((cof(idx) << LOGJ) + mof(idx)), LSTR);
-  });
-  const Lin<EPT> tidx([&](unsigned idx) { return ((idx >> LOGR1) << LOGJ) + mof(idx); });
-  const int tot = nl * R1;
+  const int run = (int)threadIdx.x >> 2, t4 = (int)threadIdx.x & 3;
+  if (run < nl * NCH) {                            // whole warps (8 runs each) in or out
+    const int slot = run >> LOGNCH, c = run & (NCH - 1);
+    float2* line = sm + slot * LSTR + c * (J + J / 16);
+    float2 v[16];
 #pragma unroll
-  for (int u = 0; u < EPT; ++u) {
-    if ((int)threadIdx.x + u * NT < tot) {
-      const int slot = (u * NT) >> LOGR1;          // NT <= R1: the slot is the u's
-      const unsigned row = (unsigned)f2_line(slot, q0, np, R2);
-      out[(row << lognl) + oofs(u)] = cmul(sm[sidx(u)], twk[tidx(u)]);
+    for (int i = 0; i < 16; ++i) v[i] = line[pidx(0, t4 + 4 * i, 0)];
+    Dft<16, true>::run(v);
+    __syncwarp();                                  // the run is read before it is overwritten
+#pragma unroll
+    for (int k = 0; k < 16; ++k) line[pidx(0, 16 * t4 + k, 0)] = v[k];
+    __syncwarp();
+    const unsigned k2 = (unsigned)f2_line(slot, q0, np, R2);
+    const unsigned g = (unsigned)c >> lognl, ci = (unsigned)c & ((1u << lognl) - 1);
+    // element (k2, m1, c) at ((m1 G + g) R2 + k2) nl + ci
+    const unsigned ofs0 = (((g << logR2) + k2) << lognl) + ci;
+    const int mstep = LOGNCH - lognl + logR2 + lognl;   // log2 of the m1 stride (G R2 nl)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = t4 + 4 * q;
+      float2 w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = line[t + 17 * j];   // element t + 16 j (t < 16)
+#pragma unroll
+      for (int j = 1; j < 4; ++j) w[j] = cmul(w[j], cconj(stwj[(j - 1) * 16 + t]));
+      Dft<4, true>::run(w);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m1 = t + 16 * j;
+        out[ofs0 + ((unsigned)m1 << mstep)] = cmul(w[j], twk[slot * J + m1]);
+      }
     }
   }
 }
