@@ -37,7 +37,8 @@ UNIT = "Msamples/s"
 F0, BW, FS = 326.5, 16.0, 32e6
 # kernel behind each stage name of pond_stats
 KERNEL_OF_STAGE = {"fwd_cols_unpack": "k_fwd_cols", "fwd_rows_split": "k_fwd_rows",
-                   "fwd_rows_chirp_inv": "k_fwd_rows_inv", "inv_cols_chirp": "k_inv_cols",
+                   "fwd_rows_chirp_inv": "k_fwd_rows_inv", "inv_rows_chirp": "k_inv_rows_chirp",
+                   "inv_cols_chirp": "k_inv_cols",
                    "inv_rows_detect": "k_inv_rows", "inv_cols_detect": "k_inv_cols_det",
                    "fold": "k_fold_dec", "decimate": "k_decimate"}
 PLAN = dict(dm=26.8, nfft=1 << 24, nchan=64, nbins=1024, period=0.7145, t_dec=61.44e-6)

@@ -141,7 +141,7 @@ typedef struct {
 } pond_cand;
 
 /* Counters and per-stage GPU time (ms; stage times only with opts.timing). */
-#define POND_NSTAGE 8
+#define POND_NSTAGE 9
 typedef struct {
   int64_t samples_in;       /* int8 samples accepted */
   int64_t segments;         /* segments processed */

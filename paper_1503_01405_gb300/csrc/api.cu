@@ -70,13 +70,13 @@ constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched pl
 constexpr int MAX_TRIALS = 4096;
 constexpr int NSLOT = 2;                       // segments in flight (streams, FFT buffer sets)
 
-// Stages in pipeline order (a segment runs F1, F2, I1, I2 or F1, F2f, Ic, then
-// fold / decimation).
-enum Stage { ST_F1 = 0, ST_F2, ST_F2F, ST_I1, ST_I2, ST_IC, ST_FOLD, ST_DEC, ST_COUNT };
+// Stages in pipeline order (a segment runs F1, F2, I1, I2; F1, F2f, Ic; or, in
+// batched plans, F1, F2 and per trial Ir, Ic; then fold / decimation).
+enum Stage { ST_F1 = 0, ST_F2, ST_F2F, ST_IR, ST_I1, ST_I2, ST_IC, ST_FOLD, ST_DEC, ST_COUNT };
 static_assert(ST_COUNT <= POND_NSTAGE, "stage slots");
 const char* kStageName[POND_NSTAGE] = {"fwd_cols_unpack", "fwd_rows_split", "fwd_rows_chirp_inv",
-                                       "inv_cols_chirp", "inv_rows_detect", "inv_cols_detect",
-                                       "fold", "decimate"};
+                                       "inv_rows_chirp", "inv_cols_chirp", "inv_rows_detect",
+                                       "inv_cols_detect", "fold", "decimate"};
 
 int ilog2ll(long long v) {
   int r = 0;
@@ -116,8 +116,9 @@ struct Lane {
   float2* bufA[NSLOT] = {};
   float2* bufB[NSLOT] = {};
   float* P[NSLOT] = {};
-  // fused schedule (F1, F2f, Ic): Ic's group partials and per-m1 tickets per slot
-  bool fused = false;
+  // fused schedule (F1, F2f, Ic; batched: F1, F2, per trial Ir, Ic): Ic's group
+  // partials and per-m1 tickets per slot
+  bool fused = false, fused_multi = false;
   float* part[NSLOT] = {};
   int* cnt[NSLOT] = {};
   // per trial of the lane and slot: after that trial's fold / decimation of a segment
@@ -321,11 +322,12 @@ int build_lane(pond_t h, Lane* ln) {
   }
   const Geom& g = ln->g;
   ln->fused = !h->multi && !h->tc_terms && h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g);
+  ln->fused_multi = h->multi && !h->tc_terms && h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g);
   for (int k = 0; k < NSLOT; ++k) {
     CK(cudaMalloc(&ln->bufA[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->bufB[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->P[k], g.M * sizeof(float)));
-    if (ln->fused && fused_groups(g) > 1) {
+    if ((ln->fused || ln->fused_multi) && fused_groups(g) > 1) {
       CK(cudaMalloc(&ln->part[k], (size_t)fused_groups(g) * g.M * sizeof(float)));
       CK(cudaMalloc(&ln->cnt[k], FUSED_J * sizeof(int)));
       CK(cudaMemsetAsync(ln->cnt[k], 0, FUSED_J * sizeof(int), h->st));
@@ -578,11 +580,20 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     for (size_t q = 0; q < ln.trials.size(); ++q) {
       const int d = ln.trials[q];
       const Trial& t = h->trials[d];
-      // every trial's chirp is applied as I1 loads the shared forward spectrum
-      CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
-      if (q == 0) RC(record(h, 1 + ST_I1, cs));
-      CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
-      if (q == 0) RC(record(h, 1 + ST_I2, cs));
+      if (ln.fused_multi) {
+        // the trial's chirp and the first inverse factor as Ir loads the shared spectrum's rows
+        CK(launch_inv_rows_chirp(g, bufB, bufA, ln.tw3L, ln.stwJ, t.anc, t.clog, cs));
+        if (q == 0) RC(record(h, 1 + ST_IR, cs));
+        CK(launch_inv_cols_det(g, bufA, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
+                               (int)m_hi, ln.stwR2, cs));
+        if (q == 0) RC(record(h, 1 + ST_IC, cs));
+      } else {
+        // every trial's chirp is applied as I1 loads the shared forward spectrum
+        CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
+        if (q == 0) RC(record(h, 1 + ST_I1, cs));
+        CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
+        if (q == 0) RC(record(h, 1 + ST_I2, cs));
+      }
       // each trial's series row (and the fold partials) is updated in segment order
       CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
       if (!h->multi) {
@@ -724,10 +735,10 @@ void destroy_all(pond_t h) {
 // ---------------------------------------------------------------------------
 
 std::mutex g_tune_mu;
-std::map<std::tuple<long long, int, int>, std::pair<double, double>> g_tune_cache;
+std::map<std::tuple<long long, int, int, int>, std::pair<double, double>> g_tune_cache;
 
 int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, double* t_inv) {
-  const auto key = std::make_tuple(nfft, o->nchan, o->device);
+  const auto key = std::make_tuple(nfft, o->nchan, o->device, o->schedule);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -780,10 +791,17 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
   if (ce == cudaSuccess) ce = cudaEventRecord(e[1], h->st);
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
     if (it == 1) ce = cudaEventRecord(e[2], h->st);
-    if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB[0], ln.bufA[0], anc, clog, ln.stwQ2, h->st);
-    if (ce == cudaSuccess)
-      ce = launch_inv_rows(g, ln.bufA[0], ln.P[0], nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.tw3M, ln.stwQ1,
-                           h->st);
+    if (ln.fused_multi) {   // the per-trial passes the plan will run
+      if (ce == cudaSuccess) ce = launch_inv_rows_chirp(g, ln.bufB[0], ln.bufA[0], ln.tw3L, ln.stwJ, anc, clog, h->st);
+      if (ce == cudaSuccess)
+        ce = launch_inv_cols_det(g, ln.bufA[0], ln.P[0], ln.part[0], ln.cnt[0], nullptr, 0, 0, (int)g.n_past,
+                                 (int)(g.n_past + nv), ln.stwR2, h->st);
+    } else {
+      if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB[0], ln.bufA[0], anc, clog, ln.stwQ2, h->st);
+      if (ce == cudaSuccess)
+        ce = launch_inv_rows(g, ln.bufA[0], ln.P[0], nullptr, 0, 0, (int)g.n_past, (int)(g.n_past + nv), ln.tw3M,
+                             ln.stwQ1, h->st);
+    }
     if (ce == cudaSuccess) ce = launch_decimate(ln.P[0], nv, 0, 8, 1, 0, nv / 8, T, C, nv / 8 + 1, h->st);
   }
   if (ce == cudaSuccess) ce = cudaEventRecord(e[3], h->st);
@@ -1400,6 +1418,7 @@ int pond_stats(pond_t h, pond_stats_t* s) {
   s->algo_bytes[ST_F1] = (double)g.N + spec;
   s->algo_bytes[ST_F2] = 2 * spec;
   s->algo_bytes[ST_F2F] = 2 * spec;
+  s->algo_bytes[ST_IR] = 2 * spec;
   s->algo_bytes[ST_I1] = 2 * spec;
   s->algo_bytes[ST_I2] = spec + nv * sizeof(float);
   s->algo_bytes[ST_IC] = spec + nv * sizeof(float);

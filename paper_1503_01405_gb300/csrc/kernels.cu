@@ -511,6 +511,27 @@ cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, co
   return cudaGetLastError();
 }
 
+namespace {
+size_t smem_inv_rows_chirp(int R1, int nl) {
+  return ((size_t)TW3_SN + stage_table_size(FUSED_J) + (size_t)nl * FUSED_J + (size_t)nl * (R1 + R1 / 16)) *
+         sizeof(float2);
+}
+}  // namespace
+
+cudaError_t launch_inv_rows_chirp(const Geom& g, const float2* in, float2* out, const float2* tw3L, const float2* twJ,
+                                  const ChirpAnchor* anc, int clog, cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R1, R2);
+  const unsigned grid = (unsigned)(R2 / nl);
+  switch (R1) {
+#define CASE(R) case R: k_inv_rows_chirp<R, FUSED_J><<<grid, NT, smem_inv_rows_chirp(R, nl), st>>>(in, out, g.logR2, tw3L, twJ, anc, clog); break;
+    POND_FUSED_R1(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 int fused_groups(const Geom& g) {
   const int nl = std::min(TILE >> g.logR2, g.nchan);
   return g.nchan / nl;
@@ -539,6 +560,10 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows_inv<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd_rows_inv(R, TILE / R));
   POND_FUSED_R1(SET_F)
 #undef SET_F
+#define SET_I(R) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows_chirp<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_rows_chirp(R, TILE / R));
+  POND_FUSED_R1(SET_I)
+#undef SET_I
 #define SET_C(R) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols_det<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_cols_det<R>(TILE / R));
   POND_FUSED_R2(SET_C)

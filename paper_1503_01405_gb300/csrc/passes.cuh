@@ -409,6 +409,56 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   });
 }
 
+// Length-J (= 64 = 16 x 4) inverse DFT of every (slot, c) run of a row tile
+// (row stride R1 + R1/16, run c at c (J + J/16)), four lanes of one warp per
+// run (run = threadIdx.x / 4, lane t4): the Stockham radix-16 step (outputs of
+// butterfly t4 to 16 t4 + k) in registers, the exchange through the run's own
+// line with warp-level barriers, the radix-4 step (butterflies t4 + 4q, outputs
+// to t' + 16 j), then twk[slot][m1] = e^{2 pi i k2 m1 / M} and the store of
+// element (k2 = row_of(slot), m1, c) at ((m1 G + g) R2 + k2) nl_c + ci,
+// c = g nl_c + ci, nl_c = min(8192 / R2, NCH) (the column pass's blocks).
+template <int R1, int J, class RowOf>
+__device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const float2* twk, float2* __restrict__ out,
+                                       int nl, int logR2, RowOf row_of) {
+  static_assert(J == 64, "radix-16 x radix-4 runs");
+  constexpr int NCH = R1 / J;
+  constexpr int LSTR = R1 + R1 / 16;
+  constexpr int LOGNCH = ilog2c(NCH);
+  const int lognl = min(13 - logR2, LOGNCH);
+  const int run = (int)threadIdx.x >> 2, t4 = (int)threadIdx.x & 3;
+  if (run < nl * NCH) {                            // whole warps (8 runs each) in or out
+    const int slot = run >> LOGNCH, c = run & (NCH - 1);
+    float2* line = sm + slot * LSTR + c * (J + J / 16);
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = line[pidx(0, t4 + 4 * i, 0)];
+    Dft<16, true>::run(v);
+    __syncwarp();                                  // the run is read before it is overwritten
+#pragma unroll
+    for (int k = 0; k < 16; ++k) line[pidx(0, 16 * t4 + k, 0)] = v[k];
+    __syncwarp();
+    const unsigned k2 = (unsigned)row_of(slot);
+    const unsigned g = (unsigned)c >> lognl, ci = (unsigned)c & ((1u << lognl) - 1);
+    const unsigned ofs0 = (((g << logR2) + k2) << lognl) + ci;
+    const int mstep = LOGNCH + logR2;              // log2 of the m1 stride (G R2 nl_c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = t4 + 4 * q;
+      float2 w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = line[t + 17 * j];   // element t + 16 j (t < 16)
+#pragma unroll
+      for (int j = 1; j < 4; ++j) w[j] = cmul(w[j], cconj(stwj[(j - 1) * 16 + t]));
+      Dft<4, true>::run(w);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m1 = t + 16 * j;
+        out[ofs0 + ((unsigned)m1 << mstep)] = cmul(w[j], twk[slot * J + m1]);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // F2f: F2 with the chirp and the first factor of every sub-channel's inverse
 // ---------------------------------------------------------------------------
@@ -462,46 +512,67 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
     sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
   });
   __syncthreads();
-  // Length-J inverse DFT of every (slot, c) run, four lanes of one warp per run
-  // (run = threadIdx.x / 4, lane t4): the Stockham radix-16 step (outputs of
-  // butterfly t4 to 16 t4 + k) in registers, the exchange through the run's own
-  // line with warp-level barriers, the radix-4 step (butterflies t4 + 4q, outputs
-  // to t' + 16 j), then e^{2 pi i k2 m1 / M} and the blocked store from registers.
-  static_assert(J == 64, "radix-16 x radix-4 runs");
-  const int lognl = min(13 - logR2, LOGNCH);      // Ic's sub-channels per CTA (log2)
-  const int run = (int)threadIdx.x >> 2, t4 = (int)threadIdx.x & 3;
-  if (run < nl * NCH) {                            // whole warps (8 runs each) in or out
-    const int slot = run >> LOGNCH, c = run & (NCH - 1);
-    float2* line = sm + slot * LSTR + c * (J + J / 16);
-    float2 v[16];
+  j_runs<R1, J>(sm, stwj, twk, out, nl, logR2, [&](int slot) { return f2_line(slot, q0, np, R2); });
+}
+
+// ---------------------------------------------------------------------------
+// Ir: per-trial row pass of batched plans with M = 64 R2
+// ---------------------------------------------------------------------------
+
+// A batched plan shares F2's spectrum X[k2 + R2 k1] (row k2, column k1) among
+// its trials, so the chirp cannot move into F2.  For each trial a CTA takes
+// nl = min(TILE/R1, R2) consecutive rows, applies the trial's chirp (Eq. 4) as
+// it loads them and runs F2f's length-64 runs and blocked store; the column
+// pass (Ic) then completes the trial's sub-channel inverses.
+template <int R1, int J>
+__global__ void __launch_bounds__(NT, 2) k_inv_rows_chirp(const float2* __restrict__ in, float2* __restrict__ out,
+                                                          int logR2, const float2* __restrict__ tw3L,
+                                                          const float2* __restrict__ twJ,
+                                                          const ChirpAnchor* __restrict__ anc, int clog) {
+  static_assert(J == 64 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
+  constexpr int NCH = R1 / J;
+  constexpr int LSTR = R1 + R1 / 16;
+  constexpr int LOGJ = ilog2c(J), LOGNCH = ilog2c(NCH), LOGR1 = ilog2c(R1);
+  extern __shared__ float2 smem[];
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stwj = st3 + TW3_SN;
+  float2* twk = stwj + stage_table_size(J);        // [nl][J]: e^{2 pi i k2 m1 / M}
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);
+  float2* sm = twk + nl * J;
+  load_tw3(st3, tw3L);
+  load_twiddles<J>(stwj, twJ);
+  const int r0 = blockIdx.x * nl;
+  const int tot = nl * R1;
+  // rows r0 .. r0 + nl - 1 are contiguous: 16-byte loads of columns k1, k1 + 1
+  const float4* in4 = reinterpret_cast<const float4*>(in) + ((size_t)r0 << (LOGR1 - 1));
+  constexpr int H = EPT / 2;
+  float4 r[H];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = line[pidx(0, t4 + 4 * i, 0)];
-    Dft<16, true>::run(v);
-    __syncwarp();                                  // the run is read before it is overwritten
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * ((int)threadIdx.x + u * NT);
+    if (idx < tot) r[u] = __ldg(in4 + (idx >> 1));
+  }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) line[pidx(0, 16 * t4 + k, 0)] = v[k];
-    __syncwarp();
-    const unsigned k2 = (unsigned)f2_line(slot, q0, np, R2);
-    const unsigned g = (unsigned)c >> lognl, ci = (unsigned)c & ((1u << lognl) - 1);
-    // element (k2, m1, c) at ((m1 G + g) R2 + k2) nl + ci
-    const unsigned ofs0 = (((g << logR2) + k2) << lognl) + ci;
-    const int mstep = LOGNCH - lognl + logR2 + lognl;   // log2 of the m1 stride (G R2 nl)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int t = t4 + 4 * q;
-      float2 w[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) w[j] = line[t + 17 * j];   // element t + 16 j (t < 16)
-#pragma unroll
-      for (int j = 1; j < 4; ++j) w[j] = cmul(w[j], cconj(stwj[(j - 1) * 16 + t]));
-      Dft<4, true>::run(w);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int m1 = t + 16 * j;
-        out[ofs0 + ((unsigned)m1 << mstep)] = cmul(w[j], twk[slot * J + m1]);
-      }
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * ((int)threadIdx.x + u * NT);
+    if (idx < tot) {
+      const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
+      const unsigned ka = (unsigned)(r0 + slot) + ((unsigned)k1 << logR2), kb = ka + (1u << logR2);
+      const ChirpAnchor a = anc[ka >> clog], b = anc[kb >> clog];
+      float2* p = sm + pidx(slot, k1, LSTR);        // k1 even: no pad between the two
+      p[0] = cmul(make_float2(r[u].x, r[u].y), chirp_from(a, clog, ka));
+      p[1] = cmul(make_float2(r[u].z, r[u].w), chirp_from(b, clog, kb));
     }
   }
+  __syncthreads();   // st3 and the tile
+  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
+  for (int i = threadIdx.x; i < nl * J; i += NT) {
+    const unsigned k2 = (unsigned)(r0 + (i >> LOGJ)), m1 = (unsigned)(i & (J - 1));
+    twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
+  }
+  __syncthreads();
+  j_runs<R1, J>(sm, stwj, twk, out, nl, logR2, [&](int slot) { return r0 + slot; });
 }
 
 // ---------------------------------------------------------------------------

@@ -103,6 +103,8 @@ int fused_groups(const Geom& g);
 cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L,
                                 const float2* tw, const float2* twJ, const ChirpAnchor* anc, int clog,
                                 cudaStream_t st);
+cudaError_t launch_inv_rows_chirp(const Geom& g, const float2* in, float2* out, const float2* tw3L, const float2* twJ,
+                                  const ChirpAnchor* anc, int clog, cudaStream_t st);
 cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
                                 long long vstride, long long vofs, int m_lo, int m_hi, const float2* tw,
                                 cudaStream_t st);

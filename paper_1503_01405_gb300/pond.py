@@ -28,7 +28,7 @@ POND_SPLIT_BF16 = 1
 POND_SPLIT_BF16_5T = 2
 POND_SCHEDULE_AUTO = 0
 POND_SCHEDULE_FOUR_PASS = 1
-POND_NSTAGE = 8
+POND_NSTAGE = 9
 POND_NOALLOC_MAX_NBINS = 1024
 
 CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", POND_E_OOM: "OOM",
