@@ -167,6 +167,11 @@ struct pond_s {
   // that read each staging buffer (staging reuse)
   cudaEvent_t ev_side[2][NSLOT] = {}, ev_used_x[2][NSLOT] = {};
   int ingest_par = 0;
+  // single-DM plans fold on their own stream: a segment's fold waits for its
+  // detection (ev_pready), the next detection into the same P for the fold
+  // (ev_pfree); the segment streams never wait for folds of other segments
+  cudaStream_t sf = nullptr;
+  cudaEvent_t ev_pready[NSLOT] = {}, ev_pfree[NSLOT] = {}, ev_fjoin = nullptr;
   // fold (single-DM plans)
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
@@ -387,6 +392,8 @@ int join_streams(pond_t h) {
     CK(cudaEventRecord(h->ev_join[k], h->sx[k]));
     CK(cudaStreamWaitEvent(h->st, h->ev_join[k], 0));
   }
+  CK(cudaEventRecord(h->ev_fjoin, h->sf));
+  CK(cudaStreamWaitEvent(h->st, h->ev_fjoin, 0));
   return POND_OK;
 }
 
@@ -394,6 +401,7 @@ int join_streams(pond_t h) {
 int fork_streams(pond_t h) {
   CK(cudaEventRecord(h->ev_in, h->st));
   for (int k = 1; k < NSLOT; ++k) CK(cudaStreamWaitEvent(h->sx[k], h->ev_in, 0));
+  CK(cudaStreamWaitEvent(h->sf, h->ev_in, 0));
   return POND_OK;
 }
 
@@ -562,16 +570,23 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     const Trial& t = h->trials[ln.trials[0]];
     CK(launch_fwd_rows_inv(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, ln.stwJ, t.anc, t.clog, cs));
     RC(record(h, 1 + ST_F2F, cs));
+    // P of this slot is free once the fold of segment s - NSLOT has read it
+    if (!h->timing) CK(cudaStreamWaitEvent(cs, h->ev_pfree[slot], 0));
     CK(launch_inv_cols_det(g, bufB, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
                            (int)m_hi, ln.stwR2, cs));
     RC(record(h, 1 + ST_IC, cs));
-    CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][0], 0));
+    // folds run in segment order on their own stream (on st with per-stage timing)
+    cudaStream_t fs = h->timing ? cs : h->sf;
+    if (!h->timing) {
+      CK(cudaEventRecord(h->ev_pready[slot], cs));
+      CK(cudaStreamWaitEvent(fs, h->ev_pready[slot], 0));
+    }
     CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
                        h->ts + (size_t)ln.trials[0] * h->ring, h->ts_cnt + (size_t)ln.trials[0] * h->ring, h->ring,
-                       h->psum, h->phits, cs));
-    RC(record(h, 1 + ST_FOLD, cs));
-    RC(record(h, 1 + ST_DEC, cs, true));
-    CK(cudaEventRecord(ln.ev_chain[slot][0], cs));
+                       h->psum, h->phits, fs));
+    RC(record(h, 1 + ST_FOLD, fs));
+    RC(record(h, 1 + ST_DEC, fs, true));
+    if (!h->timing) CK(cudaEventRecord(h->ev_pfree[slot], fs));
     h->launches += 4;
   } else {
     CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
@@ -715,6 +730,12 @@ void destroy_all(pond_t h) {
   if (h->ev_done) cudaEventDestroy(h->ev_done);
   if (h->ev_caller) cudaEventDestroy(h->ev_caller);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_fjoin) cudaEventDestroy(h->ev_fjoin);
+  for (int k = 0; k < NSLOT; ++k) {
+    if (h->ev_pready[k]) cudaEventDestroy(h->ev_pready[k]);
+    if (h->ev_pfree[k]) cudaEventDestroy(h->ev_pfree[k]);
+  }
+  if (h->sf) cudaStreamDestroy(h->sf);
   if (h->st) cudaStreamDestroy(h->st);
   for (int k = 1; k < NSLOT; ++k) {
     if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
@@ -963,6 +984,12 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     }
   }
   CKD(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  CKD(cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking));
+  CKD(cudaEventCreateWithFlags(&h->ev_fjoin, cudaEventDisableTiming));
+  for (int k = 0; k < NSLOT; ++k) {
+    CKD(cudaEventCreateWithFlags(&h->ev_pready[k], cudaEventDisableTiming));
+    CKD(cudaEventCreateWithFlags(&h->ev_pfree[k], cudaEventDisableTiming));
+  }
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_caller, cudaEventDisableTiming));
   for (int i = 0; i < 2; ++i) {
