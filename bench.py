@@ -21,6 +21,7 @@ Multi-GPU: replicas only (one independent stream per rank, no collective).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -144,6 +145,15 @@ def max_over_ranks(dist, v: float) -> float:
     return float(t.item())
 
 
+def quiet_gc():
+    """Collect once and move every live object out of the collector's scans, so
+    that a full collection of the harness's (torch / numpy) heap cannot land
+    inside a timed region; collection stays enabled."""
+    gc.collect()
+    if hasattr(gc, "freeze"):
+        gc.freeze()
+
+
 def traffic_from_profiles(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
     import hashlib
@@ -257,6 +267,7 @@ def run_batched(args, rank, ws, dist):
         step()
     st0 = eng.stats()
     torch.cuda.synchronize()
+    quiet_gc()
     barrier(dist)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -335,6 +346,7 @@ def run_precision(args, rank, ws, dist):
             step()
         st0 = eng.stats()
         torch.cuda.synchronize()
+        quiet_gc()
         barrier(dist)
         total = 0.0
         for _ in range(steps):
@@ -405,6 +417,7 @@ def run_precision(args, rank, ws, dist):
 
     for _ in range(max(1, args.warmup)):
         step_host()
+    quiet_gc()
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -565,6 +578,7 @@ def main():
     for _ in range(args.warmup):
         step_device(eng)
     torch.cuda.synchronize()
+    quiet_gc()
     barrier(dist)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -657,6 +671,7 @@ def main():
 
     for _ in range(max(1, args.warmup)):
         step_host()
+    quiet_gc()
     barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
