@@ -237,6 +237,18 @@ template <int R, int LS, bool INV, int LSTR = line_stride(R)> struct Stages {
   }
 };
 
+// The stages of R with LS < LS_STOP (all but the last when LS_STOP is the last
+// stage's LS): a pass that takes the last stage itself runs these first.
+template <int R, int LS, bool INV, int LSTR, int LS_STOP> struct StagesUntil {
+  static __device__ __forceinline__ void run(float2* s, int nl, const float2* stw) {
+    if constexpr (LS < LS_STOP) {
+      constexpr int RAD = stage_radix(R, LS);
+      stockham_stage<R, RAD, LS, INV, LSTR>(s, nl, stw);
+      StagesUntil<R, LS * RAD, INV, LSTR, LS_STOP>::run(s, nl, stw);
+    }
+  }
+};
+
 // Transform the nl lines of length R held in shared memory s (stw: stage tables).
 template <int R, bool INV>
 __device__ __forceinline__ void block_fft(float2* s, int nl, const float2* stw) {

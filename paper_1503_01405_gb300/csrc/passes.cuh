@@ -217,6 +217,32 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
     }
   }
   __syncthreads();
+  if constexpr (!TC && R2 >= 512) {
+    // the last stage (LS 256, radix RL) stores its outputs X[t + 256 j] straight
+    // to global memory: butterflies go lines first, so a warp's stores are the
+    // nl columns of consecutive rows (32-byte runs) and its loads fall in
+    // distinct banks (line stride 16 R2 / TILE mod 16)
+    constexpr int RL = R2 / 256, BPTL = 16 / RL;
+    StagesUntil<R2, 1, false, LSTR, 256>::run(sm, nl, stw);
+    const float2* tws = stw + stage_table_offset(R2, 256);
+#pragma unroll
+    for (int q = 0; q < BPTL; ++q) {
+      const int bf = (int)threadIdx.x + q * NT;
+      if (bf < nl * 256) {
+        const int b = bf & (nl - 1), t = bf >> lognl;
+        const float2* src = sm + b * LSTR + t + (t >> 4);
+        float2 u[RL];
+#pragma unroll
+        for (int j = 0; j < RL; ++j) u[j] = src[j * (256 + 16)];   // element t + 256 j
+#pragma unroll
+        for (int j = 1; j < RL; ++j) u[j] = cmul(u[j], tws[(j - 1) * 256 + t]);
+        Dft<RL, false>::run(u);
+#pragma unroll
+        for (int j = 0; j < RL; ++j) out[(unsigned)(n1_0 + b) + ((unsigned)(t + 256 * j) << logR1)] = u[j];
+      }
+    }
+    return;
+  }
   fft_lines<R2, false, TC, LSTR>(sm, nl, stw, &tcc);
   if constexpr (TC) tc::teardown(tcc);
   // neighbouring threads take the nl columns of one row, then the next rows:
