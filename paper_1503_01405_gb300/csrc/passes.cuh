@@ -524,14 +524,42 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   load_twiddles<R1>(stw, tw);
   load_twiddles<J>(stwj, twJ);
   const int q0 = blockIdx.x * np;
-  f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
-  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L (st3 is in)
+  {
+    // The first radix-16 stage straight from global memory: butterfly t of line
+    // `slot` (one per thread: nl R1 / 16 = NT) reads x[t + NB j], j < 16, which
+    // consecutive lanes load contiguously, scales element n1 = t + NB j of row k2
+    // by w^{n1 k2} (direct every fourth j, else one step by w^{NB k2}), and
+    // writes its outputs to 16 t + j as the Stockham stage would.
+    constexpr int NB = R1 / 16, LOGNB = ilog2c(NB);
+    const int slot = (int)threadIdx.x >> LOGNB, t = (int)threadIdx.x & (NB - 1);
+    const bool on = slot < nl;                         // whole warps (NB >= 32)
+    const unsigned k2 = on ? (unsigned)f2_line(slot, q0, np, R2) : 0u;
+    const float2* src = in + ((size_t)k2 << LOGR1) + t;
+    float2 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = on ? __ldg(src + j * NB) : make_float2(0.f, 0.f);
+    __syncthreads();   // st3 filled
+    if (on) {
+      const float2 ws = tw3(st3, (unsigned)NB * k2);
+      float2 w = make_float2(1.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        w = (j % 4 == 0) ? tw3(st3, (unsigned)(t + NB * j) * k2) : cmul(w, ws);
+        v[j] = cmul(v[j], w);
+      }
+      Dft<16, false>::run(v);
+      float2* dst = sm + slot * LSTR + 16 * t + t;    // element 16 t + j
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dst[j] = v[j];
+    }
+  }
+  // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
   for (int i = threadIdx.x; i < nl * J; i += NT) {
     const unsigned k2 = (unsigned)f2_line(i >> LOGJ, q0, np, R2), m1 = (unsigned)(i & (J - 1));
     twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
   }
   __syncthreads();
-  fft_lines<R1, false, false, LSTR>(sm, nl, stw, nullptr);
+  Stages<R1, 16, false, LSTR>::run(sm, nl, stw);          // the stages after the first
   f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int row, int k1, float2 X) {
     const unsigned k = (unsigned)row + ((unsigned)k1 << logR2);
     const ChirpAnchor a = anc[k >> clog];   // every row spans the band: L1/L2-resident table
@@ -832,37 +860,25 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
   load_twiddles<R2>(stw, tw);
   const int m1 = blockIdx.x >> logG, gi = blockIdx.x & ((1 << logG) - 1);
   const float2* blk = in + (size_t)blockIdx.x * tot;   // block m1 G + g
-  if (nl >= 2) {
-    // 16-byte loads: elements 2i, 2i + 1 (sub-channels ci, ci + 1 of row k2)
-    constexpr int H = EPT / 2;
-    const float4* blk4 = reinterpret_cast<const float4*>(blk);
-    const Lin<H> slot([&](unsigned i) {
-      return (unsigned)pidx((int)((2 * i) & (nl - 1)), (int)((2 * i) >> lognl), LSTR);
-    });
-    float4 r[H];
+  {
+    // The first radix-16 stage straight from global memory: butterfly t of line
+    // ci (sub-channels fastest, so consecutive lanes read consecutive elements)
+    // reads element k2 = t + NB j of the block's rows, j < 16, and writes its
+    // outputs to 16 t + j as the Stockham stage would.
+    constexpr int NB = R2 / 16;
+    const int ci = (int)threadIdx.x & (nl - 1), t = (int)threadIdx.x >> lognl;
+    if (t < NB) {
+      float2 v[16];
 #pragma unroll
-    for (int u = 0; u < H; ++u)
-      if (2 * ((int)threadIdx.x + u * NT) < tot) r[u] = blk4[threadIdx.x + u * NT];
+      for (int j = 0; j < 16; ++j) v[j] = blk[(t + NB * j) * nl + ci];
+      Dft<16, true>::run(v);
+      float2* dst = sm + ci * LSTR + pidx(0, 16 * t, 0);      // element 16 t + j
 #pragma unroll
-    for (int u = 0; u < H; ++u) {
-      if (2 * ((int)threadIdx.x + u * NT) < tot) {
-        float2* p = sm + slot(u);
-        p[0] = make_float2(r[u].x, r[u].y);
-        p[LSTR] = make_float2(r[u].z, r[u].w);
-      }
+      for (int j = 0; j < 16; ++j) dst[j] = v[j];
     }
-  } else {
-    const Lin<EPT> slot([&](unsigned idx) { return (unsigned)pidx(0, (int)idx, LSTR); });
-    float2 r[EPT];
-#pragma unroll
-    for (int u = 0; u < EPT; ++u)
-      if ((int)threadIdx.x + u * NT < tot) r[u] = blk[threadIdx.x + u * NT];
-#pragma unroll
-    for (int u = 0; u < EPT; ++u)
-      if ((int)threadIdx.x + u * NT < tot) sm[slot(u)] = r[u];
   }
   __syncthreads();
-  fft_lines<R2, true, false, LSTR>(sm, nl, stw, nullptr);
+  Stages<R2, 16, true, LSTR>::run(sm, nl, stw);            // the stages after the first
   const float s2 = scale * scale;
   constexpr int NLMAX = TILE / R2 < NT ? TILE / R2 : NT;   // nl <= NLMAX
   constexpr int MPT = (R2 + NT - 1) / NT;                 // outputs per thread
