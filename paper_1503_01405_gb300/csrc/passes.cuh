@@ -169,7 +169,30 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   if constexpr (TC) tc::setup(tcc, sm, tile_f2<R2, TC, LSTR>(nl), tca);
   const int tile = blockIdx.x;
   const int n1_0 = tile * nl;
-  if (in.vec8) {
+  // FP32 form, R2 >= 512, aligned runs: the first radix-16 stage takes its inputs
+  // straight from global memory (butterfly t of column b, columns fastest: a warp
+  // reads the nl columns of 8 rows per load) and the stages after it start from
+  // LS = 16; the unpack's shared-memory round trip and a barrier go away
+  const bool direct1 = !TC && R2 >= 512 && in.vec8;
+  if (direct1) {
+    constexpr int NB = R2 / 16;
+    const int b = (int)threadIdx.x & (nl - 1), t = (int)threadIdx.x >> lognl;
+    if (t < NB) {
+      float2 v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const long long r = 2ll * ((long long)(n1_0 + b) + ((long long)(t + NB * j) << logR1));
+        unsigned short q = 0;   // int8 pair x[2n], x[2n+1] (even offsets: no pair straddles the runs)
+        if (r < in.a_len) q = __ldg(reinterpret_cast<const unsigned short*>(in.a + r));
+        else if (r - in.a_len < in.b_len) q = __ldg(reinterpret_cast<const unsigned short*>(in.b + (r - in.a_len)));
+        v[j] = make_float2((float)(signed char)(q & 0xff), (float)(signed char)(q >> 8));
+      }
+      Dft<16, false>::run(v);
+      float2* dst = sm + b * LSTR + pidx(0, 16 * t, 0);    // element 16 t + j
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dst[j] = v[j];
+    }
+  } else if (in.vec8) {
     // 8-byte loads: 4 consecutive columns of one row per load (runs 8-aligned)
     constexpr int CPT = EPT / 4;
     const int logq = lognl - 2;            // chunks per row = nl / 4
@@ -223,7 +246,8 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
     // nl columns of consecutive rows (32-byte runs) and its loads fall in
     // distinct banks (line stride 16 R2 / TILE mod 16)
     constexpr int RL = R2 / 256, BPTL = 16 / RL;
-    StagesUntil<R2, 1, false, LSTR, 256>::run(sm, nl, stw);
+    if (direct1) StagesUntil<R2, 16, false, LSTR, 256>::run(sm, nl, stw);
+    else StagesUntil<R2, 1, false, LSTR, 256>::run(sm, nl, stw);
     const float2* tws = stw + stage_table_offset(R2, 256);
 #pragma unroll
     for (int q = 0; q < BPTL; ++q) {
