@@ -349,6 +349,40 @@ __device__ __forceinline__ void f2_load(const float2* __restrict__ in, float2* s
   }
 }
 
+// F2's first radix-16 stage straight from global memory: butterfly t of line
+// `slot` (one per thread: nl R1 / 16 <= NT) reads x[t + NB j], j < 16, which
+// consecutive lanes load contiguously, scales element n1 = t + NB j of row k2 by
+// w^{n1 k2} (direct every fourth j, else one step by w^{NB k2}), and writes its
+// outputs to 16 t + j as the Stockham stage would.  Waits for st3 (being filled
+// by the caller); R1 >= 256.
+template <int R1, int LSTR>
+__device__ __forceinline__ void f2_stage1(const float2* __restrict__ in, float2* sm, const float2* st3, int q0,
+                                          int np, int R2, int nl) {
+  static_assert(R1 >= 256, "radix-16 first stage with at least 16 butterflies per line");
+  constexpr int NB = R1 / 16, LOGNB = ilog2c(NB), LOGR1 = ilog2c(R1);
+  const int slot = (int)threadIdx.x >> LOGNB, t = (int)threadIdx.x & (NB - 1);
+  const bool on = slot < nl;
+  const unsigned k2 = on ? (unsigned)f2_line(slot, q0, np, R2) : 0u;
+  const float2* src = in + ((size_t)k2 << LOGR1) + t;
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = on ? __ldg(src + j * NB) : make_float2(0.f, 0.f);
+  __syncthreads();   // st3 filled
+  if (on) {
+    const float2 ws = tw3(st3, (unsigned)NB * k2);
+    float2 w = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      w = (j % 4 == 0) ? tw3(st3, (unsigned)(t + NB * j) * k2) : cmul(w, ws);
+      v[j] = cmul(v[j], w);
+    }
+    Dft<16, false>::run(v);
+    float2* dst = sm + slot * LSTR + 16 * t + t;    // element 16 t + j
+#pragma unroll
+    for (int j = 0; j < 16; ++j) dst[j] = v[j];
+  }
+}
+
 // Real-input split by conjugate pairs after the row FFTs: with A = Z[k],
 // B = conj(Z[L-k]), E = (A + B)/2, O = (A - B)/2 and W = exp(-i pi k / L),
 //   X[k] = E - i W O   and   X[L-k] = conj(E) - i conj(W O),
@@ -450,10 +484,16 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   tc::Ctx tcc;
   if constexpr (TC) tc::setup(tcc, sm, tile_f2<R1, TC>(nl), tca);
   const int q0 = blockIdx.x * np;
-  f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
-  __syncthreads();
-  fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
-  if constexpr (TC) tc::teardown(tcc);
+  if constexpr (!TC && R1 >= 256) {
+    f2_stage1<R1, LSTR>(in, sm, st3, q0, np, R2, nl);
+    __syncthreads();
+    Stages<R1, 16, false, LSTR>::run(sm, nl, stw);        // the stages after the first
+  } else {
+    f2_load<R1, LSTR>(in, sm, st3, q0, np, R2, nl * R1);
+    __syncthreads();
+    fft_lines<R1, false, TC>(sm, nl, stw, &tcc);
+    if constexpr (TC) tc::teardown(tcc);
+  }
   f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int, int row, int k1, float2 X) {
     out[((unsigned)row << LOGR1) + (unsigned)k1] = X;
   });
@@ -548,35 +588,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   load_twiddles<R1>(stw, tw);
   load_twiddles<J>(stwj, twJ);
   const int q0 = blockIdx.x * np;
-  {
-    // The first radix-16 stage straight from global memory: butterfly t of line
-    // `slot` (one per thread: nl R1 / 16 = NT) reads x[t + NB j], j < 16, which
-    // consecutive lanes load contiguously, scales element n1 = t + NB j of row k2
-    // by w^{n1 k2} (direct every fourth j, else one step by w^{NB k2}), and
-    // writes its outputs to 16 t + j as the Stockham stage would.
-    constexpr int NB = R1 / 16, LOGNB = ilog2c(NB);
-    const int slot = (int)threadIdx.x >> LOGNB, t = (int)threadIdx.x & (NB - 1);
-    const bool on = slot < nl;                         // whole warps (NB >= 32)
-    const unsigned k2 = on ? (unsigned)f2_line(slot, q0, np, R2) : 0u;
-    const float2* src = in + ((size_t)k2 << LOGR1) + t;
-    float2 v[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = on ? __ldg(src + j * NB) : make_float2(0.f, 0.f);
-    __syncthreads();   // st3 filled
-    if (on) {
-      const float2 ws = tw3(st3, (unsigned)NB * k2);
-      float2 w = make_float2(1.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        w = (j % 4 == 0) ? tw3(st3, (unsigned)(t + NB * j) * k2) : cmul(w, ws);
-        v[j] = cmul(v[j], w);
-      }
-      Dft<16, false>::run(v);
-      float2* dst = sm + slot * LSTR + 16 * t + t;    // element 16 t + j
-#pragma unroll
-      for (int j = 0; j < 16; ++j) dst[j] = v[j];
-    }
-  }
+  f2_stage1<R1, LSTR>(in, sm, st3, q0, np, R2, nl);
   // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
   for (int i = threadIdx.x; i < nl * J; i += NT) {
     const unsigned k2 = (unsigned)f2_line(i >> LOGJ, q0, np, R2), m1 = (unsigned)(i & (J - 1));
