@@ -114,7 +114,12 @@ typedef struct {
                            input sample predicted from timed launches of each length
                            (cached per nfft, nchan and device); zero: every trial uses nfft */
   int32_t schedule;     /* POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS (below) */
-  int32_t reserved[6];
+  int32_t input_channels; /* 0 or 1: one int8 sample per byte; 2: the two halves' int8
+                             samples interleaved (N0 S0 N1 S1 ...) and added in phase,
+                             x[m] = N[m] + S[m] (PONDER's AIP; -256..254): pushes then
+                             take whole pairs (an even byte count, POND_E_ARG otherwise)
+                             and stats count pairs */
+  int32_t reserved[5];
 } pond_opts;
 
 /* Fold metadata returned with a profile snapshot. */

@@ -76,6 +76,16 @@ class Plan:
     dec: Fraction = Fraction(1)   # channel samples per time-series sample
 
 
+def adding_in_phase(raw: np.ndarray) -> np.ndarray:
+    """Adding in phase (Sec. 3.4.1; the first kernel of the GPU flow in Sec. 3.7):
+    the two halves' int8 samples arrive interleaved, N0 S0 N1 S1 ..., and the
+    real sample the path transforms is their sum, x[m] = N[m] + S[m]."""
+    raw = np.asarray(raw, dtype=np.int8)
+    if raw.size % 2:
+        raise ValueError("interleaved N / S stream of odd length")
+    return raw[0::2].astype(np.float64) + raw[1::2].astype(np.float64)
+
+
 def overlap(f0: float, bw: float, dm: float, dtc: float) -> tuple[int, int]:
     """(n_past, n_fut) in channel samples, rounded up per side.
 

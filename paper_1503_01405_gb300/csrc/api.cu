@@ -148,6 +148,7 @@ struct pond_s {
   int want_voltages, timing, device;
   bool multi = false;
   int schedule = POND_SCHEDULE_AUTO;
+  int ch = 1;                               // bytes per real sample (2: N / S added in phase)
   double dtc = 0, inc = 0;
   long long dec_num = 1, dec_den = 1;
   int sgn = 1;
@@ -246,6 +247,8 @@ int validate(const pond_opts* o) {
     return fail(POND_E_ARG, "precision must be POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T");
   if (o->schedule != POND_SCHEDULE_AUTO && o->schedule != POND_SCHEDULE_FOUR_PASS)
     return fail(POND_E_ARG, "schedule must be POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS");
+  if (o->input_channels < 0 || o->input_channels > 2)
+    return fail(POND_E_ARG, "input_channels must be 0 or 1 (one int8 stream) or 2 (N / S pairs added in phase)");
   return POND_OK;
 }
 
@@ -355,8 +358,8 @@ int build_lane(pond_t h, Lane* ln) {
   ln->tw3M = p + 768;
   p += 2 * 768;
   ln->tw2L = {p, p + TW2_LO};
-  CK(cudaMalloc(&ln->carry[0], g.N));
-  CK(cudaMalloc(&ln->carry[1], g.N));
+  CK(cudaMalloc(&ln->carry[0], g.N * h->ch));
+  CK(cudaMalloc(&ln->carry[1], g.N * h->ch));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwR1), 1 << g.logR1, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwR2), 1 << g.logR2, h->st));
   CK(launch_stage_tw(const_cast<float2*>(ln->stwQ1), 1 << g.logQ1, h->st));
@@ -550,7 +553,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   }
   {  // F1 may load 8 bytes (4 columns of a row) at a time when both runs allow it
     const int nl1 = std::min(TILE >> g.logR2, 1 << g.logR1);
-    in.vec8 = (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
+    in.vec8 = in.ch == 1 && (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
               (in.b_len == 0 || (uintptr_t)in.b % 8 == 0);
   }
   // consecutive segments alternate buffer slots and streams, so one segment's
@@ -633,24 +636,26 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   return POND_OK;
 }
 
-// Ingest n samples at device pointer d into every lane (work ordered on h->st
+// Ingest n samples (n ch bytes) at device pointer d into every lane (work ordered on h->st
 // and the side streams; callers that read results or release d join them).
 int ingest_device(pond_t h, const int8_t* d, long long n) {
   const long long end = h->total_in + n;
+  const long long ch = h->ch;                // bytes per sample at d and in the carry
   RC(fork_streams(h));
   for (size_t li = 0; li < h->lanes.size(); ++li) {
     Lane& ln = h->lanes[li];
     const Geom& g = ln.g;
     while (ln.seg_start + g.N <= end) {
       SegIn in;
+      in.ch = ch;
       if (ln.seg_start < h->total_in) {
-        in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos);
-        in.a_len = h->total_in - ln.seg_start;
+        in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos) * ch;
+        in.a_len = (h->total_in - ln.seg_start) * ch;
         in.b = d;
-        in.b_len = g.N - in.a_len;
+        in.b_len = g.N * ch - in.a_len;
       } else {
-        in.a = d + (ln.seg_start - h->total_in);
-        in.a_len = g.N;
+        in.a = d + (ln.seg_start - h->total_in) * ch;
+        in.a_len = g.N * ch;
         in.b = nullptr;
         in.b_len = 0;
       }
@@ -673,12 +678,12 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
     int8_t* dst = ln.carry[1 - ln.carry_cur];
     if (ln.seg_start < h->total_in) {
       const long long old = h->total_in - ln.seg_start;
-      CK(cudaMemcpyAsync(dst, ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos), old,
+      CK(cudaMemcpyAsync(dst, ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos) * ch, old * ch,
                          cudaMemcpyDeviceToDevice, h->st));
-      if (n > 0) CK(cudaMemcpyAsync(dst + old, d, n, cudaMemcpyDeviceToDevice, h->st));
+      if (n > 0) CK(cudaMemcpyAsync(dst + old * ch, d, n * ch, cudaMemcpyDeviceToDevice, h->st));
     } else if (end > ln.seg_start) {
-      CK(cudaMemcpyAsync(dst, d + (ln.seg_start - h->total_in), end - ln.seg_start, cudaMemcpyDeviceToDevice,
-                         h->st));
+      CK(cudaMemcpyAsync(dst, d + (ln.seg_start - h->total_in) * ch, (end - ln.seg_start) * ch,
+                         cudaMemcpyDeviceToDevice, h->st));
     }
     ln.carry_cur = 1 - ln.carry_cur;
     ln.carry_pos = ln.seg_start;
@@ -798,12 +803,12 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
   if (ce == cudaSuccess) ce = cudaMalloc(&C, (size_t)(nv / 8 + 1) * sizeof(int));
   for (auto& x : e)
     if (ce == cudaSuccess) ce = cudaEventCreate(&x);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(ln.carry[0], 0, g.N, h->st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(ln.carry[0], 0, g.N * h->ch, h->st);
   if (ce == cudaSuccess)
     ce = launch_tables(anc, nanc, clog, o->fs_hz / (double)nfft * 1e-6, std::fabs(o->bw_mhz) / 2, o->f0_mhz, 0.0,
                        h->sgn, h->st);
   const int reps = 3;
-  SegIn in{ln.carry[0], g.N, nullptr, 0, 0};
+  SegIn in{ln.carry[0], g.N * h->ch, nullptr, 0, 0, h->ch};
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {      // first pass warms up
     if (it == 1) ce = cudaEventRecord(e[0], h->st);
     if (ce == cudaSuccess) ce = launch_fwd_cols(g, in, ln.bufA[0], ln.stwR2, h->st);
@@ -915,6 +920,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   h->sgn = o->bw_mhz > 0 ? 1 : -1;
   h->multi = multi;
   h->schedule = o->schedule;
+  h->ch = o->input_channels == 2 ? 2 : 1;
   h->dtc = 2.0 * o->nchan / o->fs_hz;
   h->inc = multi ? 0.0 : h->dtc / o->period_s;
   const double tdec = o->t_dec_s > 0 ? o->t_dec_s : 61.44e-6;
@@ -1110,10 +1116,11 @@ int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream) {
   if (h->flushed) return fail(POND_E_STATE, "push after flush");
   if (n == 0) return POND_OK;
   if (!d_x) return fail(POND_E_ARG, "null data");
+  if (n % h->ch) return fail(POND_E_ARG, "push of %zu bytes splits an N / S sample pair", n);
   CK(cudaSetDevice(h->device));
   cudaStream_t cs = (cudaStream_t)cuda_stream;
   RC(caller_wait(h, cs));
-  RC(ingest_device(h, d_x, (long long)n));
+  RC(ingest_device(h, d_x, (long long)(n / h->ch)));
   RC(join_streams(h));   // every segment that read d_x precedes the release
   return caller_release(h, cs);
 }
@@ -1123,6 +1130,7 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
   if (h->flushed) return fail(POND_E_STATE, "push after flush");
   if (n == 0) return POND_OK;
   if (!x) return fail(POND_E_ARG, "null data");
+  if (n % h->ch) return fail(POND_E_ARG, "push of %zu bytes splits an N / S sample pair", n);
   CK(cudaSetDevice(h->device));
   if (!h->stage[0]) {
     CK(cudaMalloc(&h->stage[0], STAGE_BYTES));
@@ -1142,7 +1150,7 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
     CK(cudaEventRecord(h->ev_copied[i], h->cst));
     CK(cudaStreamWaitEvent(h->st, h->ev_copied[i], 0));
-    RC(ingest_device(h, h->stage[i], len));
+    RC(ingest_device(h, h->stage[i], len / h->ch));
     CK(cudaEventRecord(h->ev_used[i], h->st));
     for (int k = 1; k < NSLOT; ++k) CK(cudaEventRecord(h->ev_used_x[i][k], h->sx[k]));
     last = h->ev_copied[i];
@@ -1165,8 +1173,9 @@ int pond_flush(pond_t h) {
     const Geom& g = ln.g;
     while ((ln.seg_start / g.S) * g.S_c + g.n_past < g_end) {
       SegIn in;
-      in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos);
-      in.a_len = std::max(0ll, h->total_in - ln.seg_start);
+      in.ch = h->ch;
+      in.a = ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos) * h->ch;
+      in.a_len = std::max(0ll, h->total_in - ln.seg_start) * h->ch;
       in.b = nullptr;
       in.b_len = 0;
       RC(run_segment(h, (int)li, in, ln.seg_start / g.S, g_end));

@@ -144,11 +144,27 @@ __host__ __device__ constexpr int col_stride() {
 // F1: unpack + column FFTs of the forward transform
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float sample_at(const SegIn& in, long long r) {
-  if (r < in.a_len) return (float)in.a[r];
-  r -= in.a_len;
-  if (r < in.b_len) return (float)in.b[r];
-  return 0.f;
+// Real sample m of the segment (one byte, or the sum of an N / S pair).
+__device__ __forceinline__ float sample_at(const SegIn& in, long long m) {
+  long long r = m * in.ch;
+  float x = 0.f;
+  for (int c = 0; c < in.ch; ++c, ++r) {
+    if (r < in.a_len) x += (float)in.a[r];
+    else if (r - in.a_len < in.b_len) x += (float)in.b[r - in.a_len];
+  }
+  return x;
+}
+
+// Unaligned runs or N / S pairs: element (b, n2) of the tile sample by sample
+// (rare; out of line so that the aligned load paths keep their registers).
+template <int LSTR>
+__device__ __noinline__ void f1_load_any(const SegIn in, float2* sm, int n1_0, int nl, int lognl, int logR1,
+                                         int tot) {
+  for (int idx = threadIdx.x; idx < tot; idx += NT) {
+    const int n2 = idx >> lognl, b = idx & (nl - 1);
+    const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
+    sm[pidx(b, n2, LSTR)] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
+  }
 }
 
 // z viewed as [R2][R1] (z[n1 + R1 n2]); a CTA transforms nl adjacent columns n1
@@ -223,21 +239,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
       }
     }
   } else {
-    float2 r[EPT];
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const int idx = threadIdx.x + u * NT;
-      if (idx < tot) {
-        const int n2 = idx >> lognl, b = idx & (nl - 1);
-        const long long q = (long long)(n1_0 + b) + ((long long)n2 << logR1);
-        r[u] = make_float2(sample_at(in, 2 * q), sample_at(in, 2 * q + 1));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < EPT; ++u) {
-      const int idx = threadIdx.x + u * NT;
-      if (idx < tot) sm[pidx(idx & (nl - 1), idx >> lognl, LSTR)] = r[u];
-    }
+    f1_load_any<LSTR>(in, sm, n1_0, nl, lognl, logR1, tot);
   }
   __syncthreads();
   if constexpr (!TC && R2 >= 512) {

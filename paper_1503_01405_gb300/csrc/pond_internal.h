@@ -35,12 +35,17 @@ struct Tw2 {
 
 // A segment's int8 input as up to two runs: samples [0, a_len) from a,
 // [a_len, a_len + b_len) from b, zeros beyond.
+// One segment's input: bytes [0, a_len) of run a, then [0, b_len) of run b, then
+// zeros.  Real sample m is byte m (ch = 1) or the sum of bytes 2m, 2m + 1 (ch = 2:
+// the two halves' interleaved int8 samples, added in phase); a_len is a whole
+// number of samples.
 struct SegIn {
   const int8_t* a;
   long long a_len;
   const int8_t* b;
   long long b_len;
-  int vec8;   // both runs 8-byte aligned with a_len % 8 == 0: F1 may load 8 bytes at a time
+  int vec8;   // ch 1, both runs 8-byte aligned with a_len % 8 == 0: F1 may load 8 bytes at a time
+  int ch = 1;
 };
 
 constexpr int TC_W_BYTES = 3 * 32 * 32 * 2;   // W16 hi, mid, lo parts of one direction

@@ -60,7 +60,8 @@ class pond_opts(ctypes.Structure):
                 ("timing", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("ndm", ctypes.c_int32), ("dm_list", ctypes.POINTER(ctypes.c_double)),
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("schedule", ctypes.c_int32), ("input_channels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class pond_meta(ctypes.Structure):
@@ -177,7 +178,7 @@ class Engine:
                  period: float, t_dec: float = 61.44e-6, want_voltages: bool = False,
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
                  precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
-                 schedule: int = POND_SCHEDULE_AUTO):
+                 schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1):
         """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
@@ -189,6 +190,7 @@ class Engine:
         o.timing = int(bool(timing))
         o.device = device
         o.schedule = schedule
+        o.input_channels = input_channels
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])

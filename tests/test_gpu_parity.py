@@ -33,9 +33,9 @@ def rel(a, b):
 
 
 def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6,
-               schedule=pond.POND_SCHEDULE_AUTO):
+               schedule=pond.POND_SCHEDULE_AUTO, input_channels=1):
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
-                     want_voltages=want_voltages, schedule=schedule) as e:
+                     want_voltages=want_voltages, schedule=schedule, input_channels=input_channels) as e:
         if device_push:
             import torch
             t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -138,6 +138,29 @@ def test_three_pass_schedule(cfg):
     segs = three["stats"]["segments"]
     assert segs == four["stats"]["segments"] and segs >= 2
     assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
+
+
+@pytest.mark.parametrize("cfg", [(1 << 16, 16, 0.3, 16.0, 128, 0.033), (1 << 18, 8, 1.0, 16.0, 128, 0.03)],
+                         ids=["four_pass", "three_pass"])
+def test_adding_in_phase_matches_oracle(cfg):
+    """Interleaved N / S int8 input (input_channels = 2) is added in phase by the
+    unpack: the engine matches the oracle on x = N + S, for host and device
+    pushes cut into uneven whole pairs; a push that splits a pair is refused."""
+    nfft, nchan, dm, bw, nbins, period = cfg
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
+    n, s_ = _stream(p, seed=41, extra=11), _stream(p, seed=42, extra=11)
+    inter = np.empty(2 * len(n), np.int8)
+    inter[0::2], inter[1::2] = n, s_
+    r = pcd.run(p, pcd.adding_in_phase(inter), want_voltages=True)
+    cuts = [2 * 12345, 2 * 500_001, len(inter) - 2 * (12345 + 500_001)]
+    for dev in (False, True):
+        out = run_engine(inter, p, chunks=cuts, device_push=dev, input_channels=2)
+        check(out, r)
+        assert out["stats"]["samples_in"] == len(n)
+    with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, input_channels=2) as e:
+        with pytest.raises(pond.PondError) as ei:
+            e.push(inter[:3])
+        assert ei.value.name == "ARG"
 
 
 @pytest.mark.parametrize("plan", [(1 << 16, 16, 0.3, 128, 0.033), (1 << 21, 16, 3.0, 256, 0.07)],

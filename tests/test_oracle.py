@@ -381,3 +381,36 @@ def test_batched_trials_tone_closed_form(dms):
         want = A * 4 * np.exp(1j * theta) * np.exp(-2j * np.pi * (c - round(c))) \
             * np.exp(2j * np.pi * ((j0 * g) % base.M) / base.M)
         assert np.max(np.abs(r.voltages[c0, complete] - want[complete])) < 1e-9 * A * 4
+
+
+def test_adding_in_phase_special_cases():
+    """AIP (Sec. 3.4.1, Sec. 3.7): a silent second half leaves the first, equal
+    halves double it, opposite halves cancel, and the int8 extremes add without
+    wrapping (-256 .. 254)."""
+    rng = np.random.default_rng(7)
+    n = rng.integers(-128, 128, 1000).astype(np.int8)
+    inter = np.empty(2 * n.size, np.int8)
+    inter[0::2], inter[1::2] = n, 0
+    assert np.array_equal(pcd.adding_in_phase(inter), n.astype(np.float64))
+    inter[1::2] = n
+    assert np.array_equal(pcd.adding_in_phase(inter), 2.0 * n)
+    inter[1::2] = -np.maximum(n, -127)
+    assert np.array_equal(pcd.adding_in_phase(inter), n.astype(np.float64) - np.maximum(n, -127))
+    ext = np.array([127, 127, -128, -128, 127, -128], np.int8)
+    assert np.array_equal(pcd.adding_in_phase(ext), [254.0, -256.0, -1.0])
+    with pytest.raises(ValueError):
+        pcd.adding_in_phase(ext[:5])
+
+
+def test_adding_in_phase_dedisperses_linearly():
+    """Up to detection the path is linear, so the voltages of the added stream are
+    the sum of each half's voltages (brute force over one segment)."""
+    p = pcd.make_plan(**ORT, dm=0.05, nfft=1 << 14, nchan=4, nbins=16, period=0.01)
+    rng = np.random.default_rng(8)
+    n = rng.integers(-128, 128, p.nfft).astype(np.int8)
+    s_ = rng.integers(-128, 128, p.nfft).astype(np.int8)
+    inter = np.empty(2 * p.nfft, np.int8)
+    inter[0::2], inter[1::2] = n, s_
+    v = pcd.dedisperse_segment(p, pcd.adding_in_phase(inter))
+    vn, vs = pcd.dedisperse_segment(p, n), pcd.dedisperse_segment(p, s_)
+    assert np.allclose(v, vn + vs, rtol=0, atol=1e-9 * np.abs(v).max())
