@@ -551,10 +551,12 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     if (h->v_len + nv > h->v_cap) RC(spill_voltages(h));
     vout = h->vbuf;
   }
-  {  // F1 may load 8 bytes (4 columns of a row) at a time when both runs allow it
+  {  // F1 may load 8 bytes (4 columns of a row), or one sample's N / S pairs, at a time when both runs allow it
     const int nl1 = std::min(TILE >> g.logR2, 1 << g.logR1);
     in.vec8 = in.ch == 1 && (nl1 % 4 == 0) && ((uintptr_t)in.a % 8 == 0) && (in.a_len % 8 == 0) &&
               (in.b_len == 0 || (uintptr_t)in.b % 8 == 0);
+    in.pair4 = in.ch == 2 && ((uintptr_t)in.a % 4 == 0) && (in.a_len % 4 == 0) && (in.b_len % 4 == 0) &&
+               (in.b_len == 0 || (uintptr_t)in.b % 4 == 0);
   }
   // consecutive segments alternate buffer slots and streams, so one segment's
   // passes fill the other's tail waves; fold / decimation stay in segment order.
@@ -1451,7 +1453,7 @@ int pond_stats(pond_t h, pond_stats_t* s) {
   s->flushed = h->flushed;
   const double spec = (double)g.L * sizeof(float2);
   const double nv = (double)g.S_c;
-  s->algo_bytes[ST_F1] = (double)g.N + spec;
+  s->algo_bytes[ST_F1] = (double)g.N * h->ch + spec;  // int8 in (pairs for AIP input)
   s->algo_bytes[ST_F2] = 2 * spec;
   s->algo_bytes[ST_F2F] = 2 * spec;
   s->algo_bytes[ST_IR] = 2 * spec;

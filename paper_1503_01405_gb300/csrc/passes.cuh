@@ -167,6 +167,28 @@ __device__ __noinline__ void f1_load_any(const SegIn in, float2* sm, int n1_0, i
   }
 }
 
+// Complex sample q = n1 + R1 n2 of z straight from global memory: one int8 pair
+// x[2q], x[2q + 1] (CH 1, 2-byte load), or the two halves' pairs of both real
+// samples added in phase (CH 2, 4-byte load N S N S).  Offsets are multiples of
+// 2 CH and both runs' lengths multiples of 2 CH, so no load straddles a run or
+// passes its end; past both runs the sample is zero.
+template <int CH>
+__device__ __forceinline__ float2 f1_pair(const SegIn& in, long long q) {
+  const long long r = 2ll * CH * q;
+  if constexpr (CH == 1) {
+    unsigned short w = 0;
+    if (r < in.a_len) w = __ldg(reinterpret_cast<const unsigned short*>(in.a + r));
+    else if (r - in.a_len < in.b_len) w = __ldg(reinterpret_cast<const unsigned short*>(in.b + (r - in.a_len)));
+    return make_float2((float)(signed char)(w & 0xff), (float)(signed char)(w >> 8));
+  } else {
+    unsigned w = 0;
+    if (r < in.a_len) w = __ldg(reinterpret_cast<const unsigned*>(in.a + r));
+    else if (r - in.a_len < in.b_len) w = __ldg(reinterpret_cast<const unsigned*>(in.b + (r - in.a_len)));
+    return make_float2((float)((int)(signed char)(w & 0xff) + (int)(signed char)((w >> 8) & 0xff)),
+                       (float)((int)(signed char)((w >> 16) & 0xff) + (int)(signed char)(w >> 24)));
+  }
+}
+
 // z viewed as [R2][R1] (z[n1 + R1 n2]); a CTA transforms nl adjacent columns n1
 // and stores them in place (the twiddle exp(-2 pi i n1 k2 / L) is F2's).
 template <int R2, bool TC>
@@ -189,19 +211,19 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   // straight from global memory (butterfly t of column b, columns fastest: a warp
   // reads the nl columns of 8 rows per load) and the stages after it start from
   // LS = 16; the unpack's shared-memory round trip and a barrier go away
-  const bool direct1 = !TC && R2 >= 512 && in.vec8;
+  const bool direct1 = !TC && R2 >= 512 && (in.vec8 || in.pair4);
   if (direct1) {
     constexpr int NB = R2 / 16;
     const int b = (int)threadIdx.x & (nl - 1), t = (int)threadIdx.x >> lognl;
     if (t < NB) {
       float2 v[16];
+      const long long q0 = (long long)(n1_0 + b) + ((long long)t << logR1);
+      if (in.ch == 1) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const long long r = 2ll * ((long long)(n1_0 + b) + ((long long)(t + NB * j) << logR1));
-        unsigned short q = 0;   // int8 pair x[2n], x[2n+1] (even offsets: no pair straddles the runs)
-        if (r < in.a_len) q = __ldg(reinterpret_cast<const unsigned short*>(in.a + r));
-        else if (r - in.a_len < in.b_len) q = __ldg(reinterpret_cast<const unsigned short*>(in.b + (r - in.a_len)));
-        v[j] = make_float2((float)(signed char)(q & 0xff), (float)(signed char)(q >> 8));
+        for (int j = 0; j < 16; ++j) v[j] = f1_pair<1>(in, q0 + ((long long)(NB * j) << logR1));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = f1_pair<2>(in, q0 + ((long long)(NB * j) << logR1));
       }
       Dft<16, false>::run(v);
       float2* dst = sm + b * LSTR + pidx(0, 16 * t, 0);    // element 16 t + j

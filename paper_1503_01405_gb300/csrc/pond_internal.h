@@ -46,6 +46,8 @@ struct SegIn {
   long long b_len;
   int vec8;   // ch 1, both runs 8-byte aligned with a_len % 8 == 0: F1 may load 8 bytes at a time
   int ch = 1;
+  int pair4 = 0;  // ch 2, both runs 4-byte aligned with a_len, b_len % 4 == 0: F1 may load
+                  // one complex sample's two N / S pairs (4 bytes) at a time
 };
 
 constexpr int TC_W_BYTES = 3 * 32 * 32 * 2;   // W16 hi, mid, lo parts of one direction

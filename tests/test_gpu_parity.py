@@ -140,12 +140,14 @@ def test_three_pass_schedule(cfg):
     assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
 
 
-@pytest.mark.parametrize("cfg", [(1 << 16, 16, 0.3, 16.0, 128, 0.033), (1 << 18, 8, 1.0, 16.0, 128, 0.03)],
-                         ids=["four_pass", "three_pass"])
+@pytest.mark.parametrize("cfg", [(1 << 16, 16, 0.3, 16.0, 128, 0.033), (1 << 18, 8, 1.0, 16.0, 128, 0.03),
+                                 (1 << 20, 16, 1.0, 16.0, 128, 0.03)],
+                         ids=["four_pass", "three_pass", "three_pass_direct"])
 def test_adding_in_phase_matches_oracle(cfg):
     """Interleaved N / S int8 input (input_channels = 2) is added in phase by the
     unpack: the engine matches the oracle on x = N + S, for host and device
-    pushes cut into uneven whole pairs; a push that splits a pair is refused."""
+    pushes cut into uneven whole pairs and for one whole device push; a push that
+    splits a pair is refused."""
     nfft, nchan, dm, bw, nbins, period = cfg
     p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
     n, s_ = _stream(p, seed=41, extra=11), _stream(p, seed=42, extra=11)
@@ -153,10 +155,17 @@ def test_adding_in_phase_matches_oracle(cfg):
     inter[0::2], inter[1::2] = n, s_
     r = pcd.run(p, pcd.adding_in_phase(inter), want_voltages=True)
     cuts = [2 * 12345, 2 * 500_001, len(inter) - 2 * (12345 + 500_001)]
-    for dev in (False, True):
-        out = run_engine(inter, p, chunks=cuts, device_push=dev, input_channels=2)
+    outs = []
+    for chunks, dev in ((cuts, False), (cuts, True), (None, True)):
+        out = run_engine(inter, p, chunks=chunks, device_push=dev, input_channels=2)
         check(out, r)
         assert out["stats"]["samples_in"] == len(n)
+        outs.append(out)
+    # one whole device push keeps every segment's run 4-byte aligned (4-byte loads of
+    # N S N S in the first pass where its columns allow); the cuts of 2 * 12345 bytes
+    # leave some segments unaligned (element-wise loads): the results agree to the bit
+    for key in ("s", "T", "V"):
+        assert np.array_equal(outs[2][key], outs[1][key])
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, input_channels=2) as e:
         with pytest.raises(pond.PondError) as ei:
             e.push(inter[:3])
