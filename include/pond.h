@@ -404,6 +404,103 @@ const char* pond_last_error(void);
  * NULL is accepted. */
 int pond_destroy(pond_t h);
 
+/*
+ * Incoherent dedispersion modes (PONDER Sec. 3.4, sub-modes AID of Sec. 3.4.1
+ * and CID of Sec. 3.4.2): an FFT filterbank over the same band, detected,
+ * integrated, shifted per channel by the dispersive delay of Eq. 3, summed over
+ * channels and folded.  One call processes one whole device buffer.
+ *
+ *  - Filterbank: the stream is cut into consecutive blocks of 2 nchan real
+ *    samples (no overlap, no window); X[k] = sum_n x[n] exp(-2 pi i k n /
+ *    (2 nchan)), k = 0 .. nchan-1 (DC kept, Nyquist dropped).  Channel k sits
+ *    at the sky frequency f_k = f0 - |bw|/2 + k |bw|/nchan (bw > 0) or
+ *    f0 + |bw|/2 - k |bw|/nchan (bw < 0).
+ *  - Detection: AID takes |X[k]|^2 of the single stream (input_channels 1) or
+ *    of the two halves added in phase, x = N + S (input_channels 2, bytes
+ *    N0 S0 N1 S1 ...); CID takes the cross-power Re(X_N[k] conj(X_S[k])) of
+ *    the two halves (input_channels 2).
+ *  - Integration: output sample t (t_s = 2 nchan nint / fs seconds) sums the
+ *    spectra t nint .. t nint + nint - 1, in that order; T = floor(samples /
+ *    (2 nchan nint)) output samples, trailing input is not used.
+ *  - Dedispersion: channel k is read d_k samples later, d_k = floor(K DM
+ *    (f_k^-2 - f0^-2) / t_s + 1/2) in FP64 (K as for the coherent mode,
+ *    delays referred to the band centre); D[t] = sum_k F[t + d_k][k] for
+ *    t = t_first .. t_first + n - 1 with t_first = max(0, -min d) and
+ *    n = max(0, T - max(0, max d) - t_first).
+ *  - Fold: D[t] goes to bin min(floor(frac(t * (t_s / period)) * nbins),
+ *    nbins - 1), FP64 phase, epoch at the first input sample.
+ * Results are FP32 (filterbank, series) and FP64 / int64 (profile); repeated
+ * runs give bit-identical results.
+ */
+#define POND_INCOH_AID 0   /* adding (in phase) and incoherent dedispersion */
+#define POND_INCOH_CID 1   /* correlation and incoherent dedispersion */
+typedef struct pond_incoh_s* pond_incoh_t;
+typedef struct {
+  double f0_mhz, bw_mhz, fs_hz;  /* the band, as for pond_plan (fs = 2 |bw| 1e6) */
+  double dm;                     /* >= 0 */
+  double period_s;               /* fold period, > 0 */
+  int32_t nchan;                 /* filterbank channels: power of two, 64 .. 2048 */
+  int32_t nint;                  /* spectra per output sample: power of two, 1 .. 65536 */
+  int32_t mode;                  /* POND_INCOH_AID or POND_INCOH_CID */
+  int32_t input_channels;        /* AID: 1 or 2; CID: 2 */
+  int32_t nbins;                 /* fold bins, 1 .. 4096 */
+  int32_t device;                /* CUDA device ordinal */
+  int32_t reserved[6];           /* zero */
+} pond_incoh_opts;
+
+/* Counts and device times of the last run (times from CUDA events around each
+ * stage, on the run's stream). */
+typedef struct {
+  int64_t T;             /* filterbank samples */
+  int64_t t_first;       /* first dedispersed sample */
+  int64_t n_out;         /* dedispersed samples */
+  int32_t d_min, d_max;  /* channel delays, output samples */
+  double ts;             /* output sample time, s */
+  double ms_filterbank, ms_dedisperse, ms_fold;
+  double algo_bytes_filterbank;  /* input bytes read + filterbank bytes written */
+  double algo_bytes_dedisperse;  /* filterbank bytes read + series bytes written */
+  int32_t launches;      /* kernel launches of the run */
+  int32_t reserved[3];
+} pond_incoh_info;
+
+/* pond_incoh_create: validate opts and allocate the tables.  Errors:
+ * POND_E_ARG (band, DM, period, nbins, mode / input_channels, reserved not
+ * zero, nint), POND_E_NCHAN (nchan), POND_E_OOM, POND_E_CUDA. */
+int pond_incoh_create(pond_incoh_t* out, const pond_incoh_opts* opts);
+
+/* pond_incoh_run: enqueue the whole mode on cuda_stream (a cudaStream_t of the
+ * handle's device, NULL = legacy default stream) over nbytes bytes of int8 at
+ * d_x (device memory, 16-byte aligned, caller-owned and unchanged until the
+ * run completes).  Replaces the previous run's results.  Grows the handle's
+ * device buffers (cudaMalloc, which may synchronise) when the input is longer
+ * than any before.  Errors: POND_E_ARG (null or misaligned d_x with nbytes >
+ * 0, nbytes not a multiple of input_channels), POND_E_OOM, POND_E_CUDA. */
+int pond_incoh_run(pond_incoh_t h, const int8_t* d_x, size_t nbytes, void* cuda_stream);
+
+/* pond_incoh_info_get: counts and stage times of the last run (waits for it). */
+int pond_incoh_info_get(pond_incoh_t h, pond_incoh_info* info);
+
+/* pond_incoh_filterbank: copy the last run's integrated filterbank to host
+ * out[T][nchan] (time-major: one spectrum of nchan channels per output sample,
+ * FP32); *T receives the sample count.  Errors: POND_E_OVERRUN if cap (floats)
+ * < T nchan (nothing copied, *T still set), POND_E_ARG. */
+int pond_incoh_filterbank(pond_incoh_t h, float* out, size_t cap, int64_t* T);
+
+/* pond_incoh_series: copy the dedispersed series to host out[n_out];
+ * *n_out and *t_first receive its length and first sample index.  Errors:
+ * POND_E_OVERRUN (cap < n_out, nothing copied), POND_E_ARG. */
+int pond_incoh_series(pond_incoh_t h, float* out, size_t cap, int64_t* n_out, int64_t* t_first);
+
+/* pond_incoh_profile: copy the folded profile of the last run to host sum[nbins]
+ * (FP64) and hits[nbins] (int64). */
+int pond_incoh_profile(pond_incoh_t h, double* sum, int64_t* hits);
+
+/* pond_incoh_delays: copy the channel delays d_k (output samples) to out[nchan]. */
+int pond_incoh_delays(pond_incoh_t h, int32_t* out);
+
+/* pond_incoh_destroy: wait for the device and release the handle (NULL accepted). */
+int pond_incoh_destroy(pond_incoh_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,8 @@ POND_SCHEDULE_AUTO = 0
 POND_SCHEDULE_FOUR_PASS = 1
 POND_NSTAGE = 9
 POND_NOALLOC_MAX_NBINS = 1024
+POND_INCOH_AID = 0
+POND_INCOH_CID = 1
 
 CODE_NAMES = {POND_E_ARG: "ARG", POND_E_NFFT: "NFFT", POND_E_NCHAN: "NCHAN", POND_E_OOM: "OOM",
               POND_E_CUDA: "CUDA", POND_E_STATE: "STATE", POND_E_OVERRUN: "OVERRUN",
@@ -41,7 +43,9 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_profile", "pond_timeseries", "pond_voltages", "pond_stats", "pond_strerror",
            "pond_last_error", "pond_destroy", "pond_fold_noalloc", "pond_trials",
            "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_check_bounded_wait", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
-           "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches"]
+           "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches",
+           "pond_incoh_create", "pond_incoh_run", "pond_incoh_info_get", "pond_incoh_filterbank",
+           "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy"]
 
 
 class PondError(RuntimeError):
@@ -89,6 +93,22 @@ class pond_stats_t(ctypes.Structure):
 _lib = None
 
 
+class pond_incoh_opts(ctypes.Structure):
+    _fields_ = [("f0_mhz", ctypes.c_double), ("bw_mhz", ctypes.c_double), ("fs_hz", ctypes.c_double),
+                ("dm", ctypes.c_double), ("period_s", ctypes.c_double), ("nchan", ctypes.c_int32),
+                ("nint", ctypes.c_int32), ("mode", ctypes.c_int32), ("input_channels", ctypes.c_int32),
+                ("nbins", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class pond_incoh_info(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int64), ("t_first", ctypes.c_int64), ("n_out", ctypes.c_int64),
+                ("d_min", ctypes.c_int32), ("d_max", ctypes.c_int32), ("ts", ctypes.c_double),
+                ("ms_filterbank", ctypes.c_double), ("ms_dedisperse", ctypes.c_double),
+                ("ms_fold", ctypes.c_double), ("algo_bytes_filterbank", ctypes.c_double),
+                ("algo_bytes_dedisperse", ctypes.c_double), ("launches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
 def lib() -> ctypes.CDLL:
     """Load libpond.so (built by ``__graft_entry__.build()``); raise if absent."""
     global _lib
@@ -131,6 +151,14 @@ def lib() -> ctypes.CDLL:
         "pond_cnn_train_step": [vp, vp, vp, ctypes.c_int32, ctypes.c_float, vp, vp],
         "pond_cnn_destroy": [vp],
         "pond_patches": [vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_int32, vp, vp],
+        "pond_incoh_create": [P(vp), P(pond_incoh_opts)],
+        "pond_incoh_run": [vp, vp, ctypes.c_size_t, vp],
+        "pond_incoh_info_get": [vp, P(pond_incoh_info)],
+        "pond_incoh_filterbank": [vp, vp, ctypes.c_size_t, P(ctypes.c_int64)],
+        "pond_incoh_series": [vp, vp, ctypes.c_size_t, P(ctypes.c_int64), P(ctypes.c_int64)],
+        "pond_incoh_profile": [vp, vp, vp],
+        "pond_incoh_delays": [vp, vp],
+        "pond_incoh_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -408,3 +436,99 @@ def patches(series, corners, stream: int = 0):
     _check(lib().pond_patches(series.data_ptr(), series.shape[0], series.shape[1], series.stride(0),
                               corners.data_ptr(), corners.shape[0], out.data_ptr(), stream))
     return out
+
+
+class Incoherent:
+    """Incoherent dedispersion (PONDER Sec. 3.4): FFT filterbank, AID or CID
+    detection, integration, Eq. 3 channel shifts with the channel sum, fold.
+    One ``run`` processes one whole buffer of int8 input."""
+
+    def __init__(self, f0: float, bw: float, fs: float, dm: float, nchan: int, nint: int, nbins: int,
+                 period: float, mode: int = POND_INCOH_AID, input_channels: int = 1, device: int = 0):
+        o = pond_incoh_opts()
+        o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm, o.period_s = f0, bw, fs, dm, period
+        o.nchan, o.nint, o.mode, o.input_channels, o.nbins, o.device = nchan, nint, mode, input_channels, nbins, device
+        h = ctypes.c_void_p()
+        _check(lib().pond_incoh_create(ctypes.byref(h), ctypes.byref(o)))
+        self._h = h
+        self.nchan, self.nbins, self.channels = nchan, nbins, input_channels
+
+    def run_device(self, ptr: int, nbytes: int, stream: int = 0) -> None:
+        """Enqueue the mode over nbytes of int8 at device address ptr on ``stream``."""
+        _check(lib().pond_incoh_run(self._h, ptr, nbytes, stream))
+
+    def run_tensor(self, t, stream=None) -> None:
+        """Enqueue the mode over a CUDA int8 tensor (default: torch's current stream)."""
+        import torch
+        assert t.is_cuda and t.dtype == torch.int8 and t.is_contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(t.device)
+        self.run_device(t.data_ptr(), t.numel(), s.cuda_stream)
+
+    def run(self, x: np.ndarray, stream=None) -> None:
+        """Copy host int8 input to the device (through pinned memory) and run."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        src = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int8))
+        if not src.is_pinned():
+            src = src.pin_memory()
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        d = torch.empty(src.numel(), dtype=torch.int8, device=dev)
+        with torch.cuda.stream(s):
+            d.copy_(src, non_blocking=True)
+        self.run_tensor(d, s)
+        self._keep = (src, d)      # alive until the next run or a result read
+
+    def info(self) -> dict:
+        i = pond_incoh_info()
+        _check(lib().pond_incoh_info_get(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in pond_incoh_info._fields_ if f != "reserved"}
+
+    def filterbank(self) -> np.ndarray:
+        """The integrated filterbank of the last run, [T][nchan] (time-major)."""
+        T = ctypes.c_int64()
+        rc = lib().pond_incoh_filterbank(self._h, None, 0, ctypes.byref(T))
+        if rc not in (POND_OK, POND_E_OVERRUN):
+            _check(rc)
+        out = np.empty((T.value, self.nchan), np.float32)
+        _check(lib().pond_incoh_filterbank(self._h, _ptr(out) if out.size else None, out.size, ctypes.byref(T)))
+        return out
+
+    def series(self):
+        """(D, t_first): the dedispersed series of the last run and its first sample index."""
+        n, t0 = ctypes.c_int64(), ctypes.c_int64()
+        rc = lib().pond_incoh_series(self._h, None, 0, ctypes.byref(n), ctypes.byref(t0))
+        if rc not in (POND_OK, POND_E_OVERRUN):
+            _check(rc)
+        out = np.empty(n.value, np.float32)
+        _check(lib().pond_incoh_series(self._h, _ptr(out) if out.size else None, out.size, ctypes.byref(n),
+                                       ctypes.byref(t0)))
+        return out, t0.value
+
+    def profile(self):
+        s = np.empty(self.nbins, np.float64)
+        h = np.empty(self.nbins, np.int64)
+        _check(lib().pond_incoh_profile(self._h, _ptr(s), _ptr(h)))
+        return s, h
+
+    def delays(self) -> np.ndarray:
+        d = np.empty(self.nchan, np.int32)
+        _check(lib().pond_incoh_delays(self._h, _ptr(d)))
+        return d
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().pond_incoh_destroy(self._h)
+            self._h = None
+        self._keep = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -114,3 +114,43 @@ def test_batched_plan_validation():
     with pytest.raises(pond.PondError) as e:        # the fixed nfft cannot carry DM 30
         pond.Engine(**base, dms=[0.1, 30.0])
     assert e.value.name == "NFFT"
+
+
+INCOH_CASES = [  # (options changed from a valid incoherent plan, expected code)
+    (dict(mode=pond.POND_INCOH_CID, input_channels=1), "ARG"),
+    (dict(input_channels=3), "ARG"),
+    (dict(mode=2), "ARG"),
+    (dict(nchan=32), "NCHAN"),
+    (dict(nchan=4096), "NCHAN"),
+    (dict(nchan=96), "NCHAN"),
+    (dict(nint=3), "ARG"),
+    (dict(nint=1 << 17), "ARG"),
+    (dict(nbins=0), "ARG"),
+    (dict(nbins=4097), "ARG"),
+    (dict(dm=-1.0), "ARG"),
+    (dict(period=0.0), "ARG"),
+    (dict(fs=31e6), "ARG"),
+    (dict(bw=0.0), "ARG"),
+]
+
+
+@pytest.mark.parametrize("kw,code", INCOH_CASES)
+def test_incoherent_plan_errors(kw, code):
+    """Incoherent-mode options are checked on the host before any CUDA call."""
+    a = dict(f0=326.5, bw=16.0, fs=32e6, dm=1.0, nchan=1024, nint=1, nbins=64, period=0.5,
+             mode=pond.POND_INCOH_AID, input_channels=1)
+    a.update(kw)
+    with pytest.raises(pond.PondError) as ei:
+        pond.Incoherent(**a)
+    assert ei.value.name == code
+
+
+def test_incoherent_reserved_fields_rejected():
+    o = pond.pond_incoh_opts()
+    o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm, o.period_s = 326.5, 16.0, 32e6, 1.0, 0.5
+    o.nchan, o.nint, o.mode, o.input_channels, o.nbins = 1024, 1, 0, 1, 64
+    o.reserved[2] = 1
+    h = ctypes.c_void_p()
+    assert pond.lib().pond_incoh_create(ctypes.byref(h), ctypes.byref(o)) == pond.POND_E_ARG
+    assert pond.lib().pond_incoh_create(None, ctypes.byref(o)) == pond.POND_E_ARG
+    assert pond.lib().pond_incoh_destroy(None) == pond.POND_OK
