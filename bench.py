@@ -303,6 +303,138 @@ def run_batched(args, rank, ws, dist):
 PREC_PLAN = dict(dm=3.0, nfft=1 << 21, nchan=1, nbins=256, period=0.253, t_dec=61.44e-6)
 
 
+INCOH_PLAN = {"nchan": 1024, "nint": 1, "dm": 26.8, "nbins": 1024, "period": 0.7145}
+
+
+def run_incoherent(args, rank, ws, dist):
+    """Incoherent modes (Sec. 3.4) on the full-rate band: the two halves' 60 s
+    streams (1.92e9 samples each, the second an independent stream of the same
+    recipe) interleaved N / S (3.84 GB), through a 1024-channel FFT filterbank
+    (64 us spectra, nint 1), detected as AID (added in phase) or CID (cross-power),
+    shifted by the Eq. 3 delays at DM 26.8, summed and folded into 1024 bins.
+    The input and the 3.84 GB filterbank are larger than L2."""
+    import numpy as np
+    import torch
+
+    from oracle import incoherent as inc
+    from paper_1503_01405_gb300 import build as pbuild
+    from paper_1503_01405_gb300 import pond, synth
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pbuild.build()
+    P = INCOH_PLAN
+    cid = args.incoh_mode == "cid"
+    spec = synth.replace(synth.FULL_RATE, seed=synth.FULL_RATE.seed + rank)
+    if args.samples:
+        spec = synth.replace(spec, n=args.samples)
+    n = spec.n
+    a = synth.make_stream_torch(spec, dev)
+    b = synth.make_stream_torch(synth.replace(spec, seed=spec.seed + 1000), dev)
+    x_dev = torch.stack([a, b], dim=1).reshape(-1)
+    del a, b
+    torch.cuda.synchronize()
+    eng = pond.Incoherent(F0, BW, FS, P["dm"], P["nchan"], P["nint"], P["nbins"], P["period"],
+                          mode=pond.POND_INCOH_CID if cid else pond.POND_INCOH_AID, input_channels=2, device=local)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        eng.run_tensor(x_dev, stream)
+    torch.cuda.synchronize()
+    quiet_gc()
+    barrier(dist)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            eng.run_tensor(x_dev, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
+    value = ws * n * args.steps / (ms / 1e3) / 1e6
+    info = eng.info()   # the last timed run: CUDA events around each stage on its stream
+    peaks = measured_peaks()
+    stages = {"filterbank": (info["ms_filterbank"], info["algo_bytes_filterbank"], "k_fb_power"),
+              "dedisperse": (info["ms_dedisperse"], info["algo_bytes_dedisperse"], "k_incoh_sum")}
+    dom = max(stages, key=lambda k: stages[k][0])
+    t_ms, nbytes, kname = stages[dom]
+    achieved = nbytes / (t_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname, "peak_src": peaks["src"],
+            "stage_ms_per_step": {"filterbank": info["ms_filterbank"], "dedisperse": info["ms_dedisperse"],
+                                  "fold": info["ms_fold"]},
+            "stage_gbs": {k: v[1] / (v[0] / 1e3) / 1e9 for k, v in stages.items() if v[0] > 0}}
+
+    # end to end: host int8 pairs in pinned memory through the binding's host call,
+    # series and profile read back
+    x_host = torch.empty(2 * n, dtype=torch.int8, pin_memory=True)
+    x_host.copy_(x_dev)
+    xh = x_host.numpy()
+    del x_dev
+    torch.cuda.synchronize()
+    out = {}
+
+    def step_host():
+        eng.run(xh)
+        D, _ = eng.series()
+        s_, h_ = eng.profile()
+        out["bytes"] = D.nbytes + s_.nbytes + h_.nbytes
+
+    for _ in range(max(1, args.warmup)):
+        step_host()
+    quiet_gc()
+    barrier(dist)
+    e2e_steps = max(args.steps, 10)
+    t0 = time.perf_counter()
+    marks = [t0]
+    for _ in range(e2e_steps):
+        step_host()
+        marks.append(time.perf_counter())
+    e2e_s = max_over_ranks(dist, marks[-1] - t0)
+    step_ms = sorted(1e3 * (b_ - a_) for a_, b_ in zip(marks, marks[1:]))
+    e2e = {"value": ws * n * e2e_steps / e2e_s / 1e6, "unit": UNIT, "steps": e2e_steps,
+           "h2d_bytes_per_step": 2 * n, "d2h_bytes_per_step": out["bytes"],
+           "step_ms_min_median_max": [step_ms[0], statistics.median(step_ms), step_ms[-1]]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        p = inc.make_plan(F0, BW, FS, P["dm"], P["nchan"], P["nint"], inc.CID if cid else inc.AID, 2,
+                          P["nbins"], P["period"])
+        m = 1 << 22
+        while True:
+            t0 = time.perf_counter()
+            inc.run(p, xh[:2 * m])
+            dt = time.perf_counter() - t0
+            if dt > 5.0 or 2 * m > len(xh) // 2:
+                break
+            m *= 2
+        cpu = {"value": m / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {m} pairs of the same input, {dt:.1f} s of FP64 numpy on 1 host thread"}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": "Msamples/s incoherent " + ("CID" if cid else "AID") +
+                          " (1024-channel filterbank, Eq. 3 shifts, fold)",
+                "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "incoherent " + ("CID" if cid else "AID") + " on the full-rate band: "
+                                       "1.92e9 interleaved N / S int8 pairs (3.84 GB), 1024 channels, 64 us "
+                                       "spectra, DM 26.8, 1024-bin fold",
+                           "samples_per_step": n, "nchan": P["nchan"], "nint": P["nint"], "dm": P["dm"],
+                           "nbins": P["nbins"], "period_s": P["period"],
+                           "l2": "inputs larger than L2 (3.84 GB input, 3.84 GB filterbank)",
+                           "parallelism": "replicas"},
+                "realtime_factor": value / REALTIME_MSPS, "e2e": e2e,
+                "gpu_launches": int(info["launches"]) * args.steps, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_precision(args, rank, ws, dist):
     """Precision form: the 2^23-sample stream (DM 3, P 0.253 s, S/N 50 per fold;
     nfft 2^21, one channel, 256-bin fold) with every radix-16 FFT stage computed
@@ -524,13 +656,15 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft-baseline", action="store_true")
-    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned", "precision", "aip"],
+    ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned", "precision", "aip", "incoherent"],
                     help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks; "
                          "learned: classifier training and evaluation beside the boxcar detector; "
                          "precision: split-BF16 tensor-core FFT stages vs the FP32 path and the oracle")
     ap.add_argument("--chunks", type=int, default=40, help="learned: 8 s training chunks")
     ap.add_argument("--shifts", type=int, default=16, help="learned: time-shifted patches per event")
     ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")
+    ap.add_argument("--incoh-mode", default="aid", choices=["aid", "cid"],
+                    help="incoherent: adding in phase (AID) or correlation (CID)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x5"],
                     help="full-rate: arithmetic of the radix-16 FFT stages (FP32, or split-BF16 tensor-core "
                          "DFT products with three or five terms)")
@@ -547,6 +681,9 @@ def main():
         return
     if args.workload == "precision":
         run_precision(args, rank, ws, dist)
+        return
+    if args.workload == "incoherent":
+        run_incoherent(args, rank, ws, dist)
         return
     import numpy as np
     import torch
