@@ -445,7 +445,9 @@ typedef struct {
   int32_t input_channels;        /* AID: 1 or 2; CID: 2 */
   int32_t nbins;                 /* fold bins, 1 .. 4096 */
   int32_t device;                /* CUDA device ordinal */
-  int32_t reserved[6];           /* zero */
+  int32_t ips_len;               /* 0, or the chunk length L of the fluctuation spectrum
+                                    (power of two, 64 .. 4096): see pond_incoh_ips */
+  int32_t reserved[5];           /* zero */
 } pond_incoh_opts;
 
 /* Counts and device times of the last run (times from CUDA events around each
@@ -454,9 +456,10 @@ typedef struct {
   int64_t T;             /* filterbank samples */
   int64_t t_first;       /* first dedispersed sample */
   int64_t n_out;         /* dedispersed samples */
+  int64_t ips_chunks;    /* complete chunks in the fluctuation spectrum (0 without ips_len) */
   int32_t d_min, d_max;  /* channel delays, output samples */
   double ts;             /* output sample time, s */
-  double ms_filterbank, ms_dedisperse, ms_fold;
+  double ms_filterbank, ms_dedisperse, ms_fold, ms_ips;
   double algo_bytes_filterbank;  /* input bytes read + filterbank bytes written */
   double algo_bytes_dedisperse;  /* filterbank bytes read + series bytes written */
   int32_t launches;      /* kernel launches of the run */
@@ -494,6 +497,16 @@ int pond_incoh_series(pond_incoh_t h, float* out, size_t cap, int64_t* n_out, in
 /* pond_incoh_profile: copy the folded profile of the last run to host sum[nbins]
  * (FP64) and hits[nbins] (int64). */
 int pond_incoh_profile(pond_incoh_t h, double* sum, int64_t* hits);
+
+/* pond_incoh_ips: the fluctuation spectrum of the interplanetary scintillation
+ * mode (PONDER Sec. 3.5), computed by every run of a handle created with
+ * ips_len = L > 0: the series D is cut into its J = floor(n_out / L) complete
+ * chunks of L samples and out[f] = sum_j |sum_u D[j L + u] exp(-2 pi i f u / L)|^2
+ * for f = 0 .. L/2 (L/2 + 1 FP64 values; no window, no mean removed; zero when
+ * J = 0); *chunks receives J.  With mode CID and dm 0 every channel delay is
+ * zero and D is the band-collapsed cross-power series of Sec. 3.5 (its further
+ * integration is nint).  Errors: POND_E_STATE (ips_len was 0), POND_E_ARG. */
+int pond_incoh_ips(pond_incoh_t h, double* out, int64_t* chunks);
 
 /* pond_incoh_delays: copy the channel delays d_k (output samples) to out[nchan]. */
 int pond_incoh_delays(pond_incoh_t h, int32_t* out);

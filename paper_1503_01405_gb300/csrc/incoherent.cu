@@ -197,6 +197,71 @@ __global__ void __launch_bounds__(DD_WARPS * 32) k_incoh_sum(const float* __rest
   }
 }
 
+// Fluctuation spectrum of the series (Sec. 3.5): chunks of L samples, two per
+// complex line (z = c_j + i c_{j+1}), A[f] = sum_j |X_j[f]|^2 for f = 0 .. L/2,
+// j over the J complete chunks.  One CTA: each thread owns bins f and adds the
+// chunks in order in FP64, so the result needs no merge and is deterministic.
+template <int L>
+__global__ void __launch_bounds__(NT, 1) k_ips_spectrum(const float* __restrict__ c, long long J,
+                                                        const float2* __restrict__ tw, double* __restrict__ out) {
+  constexpr int NL = TILE / L;                 // lines per pass (2 chunks each)
+  constexpr int LSTR = line_stride(L);
+  constexpr int QPL = L / 4;
+  constexpr int QPT = TILE / 4 / NT;
+  constexpr int NF = L / 2 + 1;                // bins 0 .. L/2
+  constexpr int FPT = (NF + NT - 1) / NT;
+  extern __shared__ float2 smem[];
+  float2* stw = smem;
+  float2* sm = smem + stage_table_size(L);
+  load_twiddles<L>(stw, tw);
+  double acc[FPT];
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) acc[u] = 0.0;
+  for (long long p = 0; p < J; p += 2 * NL) {
+#pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+      const int q = (int)threadIdx.x + u * NT;
+      const int l = q / QPL, n0 = 4 * (q % QPL);
+      const long long ja = p + 2 * l;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (ja < J) a = __ldg(reinterpret_cast<const float4*>(c + ja * L + n0));
+      if (ja + 1 < J) b = __ldg(reinterpret_cast<const float4*>(c + (ja + 1) * L + n0));
+      sm[pidx(l, n0, LSTR)] = make_float2(a.x, b.x);
+      sm[pidx(l, n0 + 1, LSTR)] = make_float2(a.y, b.y);
+      sm[pidx(l, n0 + 2, LSTR)] = make_float2(a.z, b.z);
+      sm[pidx(l, n0 + 3, LSTR)] = make_float2(a.w, b.w);
+    }
+    __syncthreads();
+    Stages<L, 1, false, LSTR>::run(sm, NL, stw);
+#pragma unroll
+    for (int u = 0; u < FPT; ++u) {
+      const int f = (int)threadIdx.x + u * NT;
+      if (f < NF) {
+        for (int l = 0; l < NL; ++l) {
+          const long long ja = p + 2 * l;
+          if (ja >= J) break;
+          const float2 A = sm[pidx(l, f, LSTR)];
+          const float2 C = sm[pidx(l, (L - f) & (L - 1), LSTR)];
+          const float ar = A.x + C.x, ai = A.y - C.y, br = A.x - C.x, bi = A.y + C.y;
+          acc[u] += (double)(0.25f * (ar * ar + ai * ai));
+          if (ja + 1 < J) acc[u] += (double)(0.25f * (br * br + bi * bi));
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < FPT; ++u) {
+    const int f = (int)threadIdx.x + u * NT;
+    if (f < NF) out[f] = acc[u];
+  }
+}
+
+template <int L>
+size_t ips_smem_bytes() {
+  return ((size_t)stage_table_size(L) + (size_t)(TILE / L) * line_stride(L)) * sizeof(float2);
+}
+
 template <int R>
 size_t fb_smem_bytes() {
   return ((size_t)stage_table_size(R) + (size_t)(TILE / R) * line_stride(R)) * sizeof(float2) +
@@ -219,6 +284,9 @@ struct pond_incoh_s {
   int dmin = 0, dmax = 0;
   int* d_delay = nullptr;
   float2* stw = nullptr;
+  float2* stwL = nullptr;    // stage tables of the fluctuation FFT (ips_len)
+  double* ips = nullptr;     // accumulated fluctuation spectrum [ips_len / 2 + 1]
+  long long ips_chunks = 0;
   float* F = nullptr;
   size_t F_cap = 0;          // floats
   float* D = nullptr;
@@ -227,7 +295,7 @@ struct pond_incoh_s {
   int* phits = nullptr;
   double* prof_sum = nullptr;
   long long* prof_hits = nullptr;
-  cudaEvent_t ev[4] = {};
+  cudaEvent_t ev[5] = {};
   cudaStream_t st = nullptr; // stream of the last run
   bool ran = false;
   long long T = 0, t_first = 0, n_out = 0;
@@ -276,6 +344,29 @@ cudaError_t fb_launch(const FbArgs& a, const float2* tw, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int L>
+cudaError_t ips_attr() {
+  return cudaFuncSetAttribute(pond::k_ips_spectrum<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)pond::ips_smem_bytes<L>());
+}
+
+template <int L>
+cudaError_t ips_launch(const float* c, long long J, const float2* tw, double* out, cudaStream_t st) {
+  pond::k_ips_spectrum<L><<<1, pond::NT, pond::ips_smem_bytes<L>(), st>>>(c, J, tw, out);
+  return cudaGetLastError();
+}
+
+cudaError_t ips_dispatch(int logL, bool attr, const float* c, long long J, const float2* tw, double* out,
+                         cudaStream_t st) {
+  switch (logL) {
+#define IPS_CASE(K) \
+  case K: return attr ? ips_attr<1 << K>() : ips_launch<1 << K>(c, J, tw, out, st);
+    IPS_CASE(6) IPS_CASE(7) IPS_CASE(8) IPS_CASE(9) IPS_CASE(10) IPS_CASE(11) IPS_CASE(12)
+#undef IPS_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t fb_dispatch(int logR, bool attr, const FbArgs& a, const float2* tw, cudaStream_t st) {
   switch (logR) {
 #define FB_CASE(L) \
@@ -296,6 +387,8 @@ int ilog2(long long v) {
 void release(pond_incoh_t h) {
   cudaFree(h->d_delay);
   cudaFree(h->stw);
+  cudaFree(h->stwL);
+  cudaFree(h->ips);
   cudaFree(h->F);
   cudaFree(h->D);
   cudaFree(h->psum);
@@ -335,6 +428,8 @@ extern "C" int pond_incoh_create(pond_incoh_t* out, const pond_incoh_opts* o) {
                pond::FB_MAX_NCH);
   if (!pow2(o->nint) || o->nint > (1 << pond::FB_MAX_LOGNINT))
     return err(POND_E_ARG, "pond_incoh_create: nint must be a power of two in 1..%d", 1 << pond::FB_MAX_LOGNINT);
+  if (o->ips_len != 0 && (!pow2(o->ips_len) || o->ips_len < 64 || o->ips_len > 4096))
+    return err(POND_E_ARG, "pond_incoh_create: ips_len must be 0 or a power of two in 64..4096");
   pond_incoh_t h = new pond_incoh_s;
   h->device = o->device;
   h->o = *o;
@@ -366,6 +461,15 @@ extern "C" int pond_incoh_create(pond_incoh_t* out, const pond_incoh_opts* o) {
   cudaError_t e = cudaSetDevice(o->device);
   if (e == cudaSuccess) e = pond::set_kernel_attributes();
   if (e == cudaSuccess) e = fb_dispatch(h->logR, true, FbArgs{}, nullptr, nullptr);
+  if (e == cudaSuccess && o->ips_len) {
+    const int logL = ilog2(o->ips_len);
+    e = ips_dispatch(logL, true, nullptr, 0, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess)
+      e = cudaMalloc(&h->stwL, std::max(1, pond::stage_tw_entries(o->ips_len)) * sizeof(float2));
+    if (e == cudaSuccess) e = pond::launch_stage_tw(h->stwL, o->ips_len, nullptr);
+    if (e == cudaSuccess) e = cudaMalloc(&h->ips, (o->ips_len / 2 + 1) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(h->ips, 0, (o->ips_len / 2 + 1) * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaMalloc(&h->d_delay, o->nchan * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->stw, std::max(1, pond::stage_tw_entries(1 << h->logR)) * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&h->psum, (size_t)pond::MAX_FOLD_PARTS * o->nbins * sizeof(double));
@@ -450,6 +554,18 @@ extern "C" int pond_incoh_run(pond_incoh_t h, const int8_t* d_x, size_t nbytes, 
     launches += 2;
   }
   ICK(cudaEventRecord(h->ev[3], st));
+  long long ips_chunks = 0;
+  if (h->o.ips_len) {
+    ips_chunks = n_out / h->o.ips_len;
+    if (ips_chunks > 0) {
+      ICK(ips_dispatch(ilog2(h->o.ips_len), false, h->D, ips_chunks, h->stwL, h->ips, st));
+      ++launches;
+    } else {
+      ICK(cudaMemsetAsync(h->ips, 0, (h->o.ips_len / 2 + 1) * sizeof(double), st));
+    }
+  }
+  ICK(cudaEventRecord(h->ev[4], st));
+  h->ips_chunks = ips_chunks;
   h->st = st;
   h->ran = true;
   h->T = T;
@@ -467,6 +583,7 @@ extern "C" int pond_incoh_info_get(pond_incoh_t h, pond_incoh_info* info) {
   info->T = h->T;
   info->t_first = h->t_first;
   info->n_out = h->n_out;
+  info->ips_chunks = h->ips_chunks;
   info->d_min = h->dmin;
   info->d_max = h->dmax;
   info->ts = h->ts;
@@ -474,11 +591,12 @@ extern "C" int pond_incoh_info_get(pond_incoh_t h, pond_incoh_info* info) {
   info->algo_bytes_filterbank = h->in_bytes + (double)h->T * h->nch * sizeof(float);
   info->algo_bytes_dedisperse = (double)h->n_out * h->nch * sizeof(float) + (double)h->n_out * sizeof(float);
   if (h->ran) {
-    float ms[3] = {0.f, 0.f, 0.f};
-    for (int i = 0; i < 3; ++i) ICK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    float ms[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = 0; i < 4; ++i) ICK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
     info->ms_filterbank = ms[0];
     info->ms_dedisperse = ms[1];
     info->ms_fold = ms[2];
+    info->ms_ips = ms[3];
   }
   return POND_OK;
 }
@@ -515,6 +633,15 @@ extern "C" int pond_incoh_profile(pond_incoh_t h, double* sum, int64_t* hits) {
   if (int rc = wait_last(h)) return rc;
   ICK(cudaMemcpy(sum, h->prof_sum, h->o.nbins * sizeof(double), cudaMemcpyDeviceToHost));
   ICK(cudaMemcpy(hits, h->prof_hits, h->o.nbins * sizeof(long long), cudaMemcpyDeviceToHost));
+  return POND_OK;
+}
+
+extern "C" int pond_incoh_ips(pond_incoh_t h, double* out, int64_t* chunks) {
+  if (!h || !out || !chunks) return err(POND_E_ARG, "pond_incoh_ips: null pointer");
+  if (!h->o.ips_len) return err(POND_E_STATE, "pond_incoh_ips: the handle was created with ips_len = 0");
+  if (int rc = wait_last(h)) return rc;
+  *chunks = h->ips_chunks;
+  ICK(cudaMemcpy(out, h->ips, (h->o.ips_len / 2 + 1) * sizeof(double), cudaMemcpyDeviceToHost));
   return POND_OK;
 }
 

@@ -45,7 +45,7 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_check_bounded_wait", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches",
            "pond_incoh_create", "pond_incoh_run", "pond_incoh_info_get", "pond_incoh_filterbank",
-           "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy"]
+           "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy", "pond_incoh_ips"]
 
 
 class PondError(RuntimeError):
@@ -97,14 +97,15 @@ class pond_incoh_opts(ctypes.Structure):
     _fields_ = [("f0_mhz", ctypes.c_double), ("bw_mhz", ctypes.c_double), ("fs_hz", ctypes.c_double),
                 ("dm", ctypes.c_double), ("period_s", ctypes.c_double), ("nchan", ctypes.c_int32),
                 ("nint", ctypes.c_int32), ("mode", ctypes.c_int32), ("input_channels", ctypes.c_int32),
-                ("nbins", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("nbins", ctypes.c_int32), ("device", ctypes.c_int32), ("ips_len", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class pond_incoh_info(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int64), ("t_first", ctypes.c_int64), ("n_out", ctypes.c_int64),
-                ("d_min", ctypes.c_int32), ("d_max", ctypes.c_int32), ("ts", ctypes.c_double),
-                ("ms_filterbank", ctypes.c_double), ("ms_dedisperse", ctypes.c_double),
-                ("ms_fold", ctypes.c_double), ("algo_bytes_filterbank", ctypes.c_double),
+                ("ips_chunks", ctypes.c_int64), ("d_min", ctypes.c_int32), ("d_max", ctypes.c_int32),
+                ("ts", ctypes.c_double), ("ms_filterbank", ctypes.c_double), ("ms_dedisperse", ctypes.c_double),
+                ("ms_fold", ctypes.c_double), ("ms_ips", ctypes.c_double), ("algo_bytes_filterbank", ctypes.c_double),
                 ("algo_bytes_dedisperse", ctypes.c_double), ("launches", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 3)]
 
@@ -158,6 +159,7 @@ def lib() -> ctypes.CDLL:
         "pond_incoh_series": [vp, vp, ctypes.c_size_t, P(ctypes.c_int64), P(ctypes.c_int64)],
         "pond_incoh_profile": [vp, vp, vp],
         "pond_incoh_delays": [vp, vp],
+        "pond_incoh_ips": [vp, vp, P(ctypes.c_int64)],
         "pond_incoh_destroy": [vp],
     }
     for name, args in sig.items():
@@ -444,14 +446,16 @@ class Incoherent:
     One ``run`` processes one whole buffer of int8 input."""
 
     def __init__(self, f0: float, bw: float, fs: float, dm: float, nchan: int, nint: int, nbins: int,
-                 period: float, mode: int = POND_INCOH_AID, input_channels: int = 1, device: int = 0):
+                 period: float, mode: int = POND_INCOH_AID, input_channels: int = 1, device: int = 0,
+                 ips_len: int = 0):
         o = pond_incoh_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm, o.period_s = f0, bw, fs, dm, period
         o.nchan, o.nint, o.mode, o.input_channels, o.nbins, o.device = nchan, nint, mode, input_channels, nbins, device
+        o.ips_len = ips_len
         h = ctypes.c_void_p()
         _check(lib().pond_incoh_create(ctypes.byref(h), ctypes.byref(o)))
         self._h = h
-        self.nchan, self.nbins, self.channels = nchan, nbins, input_channels
+        self.nchan, self.nbins, self.channels, self.ips_len = nchan, nbins, input_channels, ips_len
 
     def run_device(self, ptr: int, nbytes: int, stream: int = 0) -> None:
         """Enqueue the mode over nbytes of int8 at device address ptr on ``stream``."""
@@ -509,6 +513,14 @@ class Incoherent:
         h = np.empty(self.nbins, np.int64)
         _check(lib().pond_incoh_profile(self._h, _ptr(s), _ptr(h)))
         return s, h
+
+    def ips(self):
+        """(A, J): the accumulated fluctuation spectrum (ips_len / 2 + 1 bins) of the
+        last run's series and the number of chunks in it (Sec. 3.5)."""
+        out = np.empty(max(self.ips_len, 2) // 2 + 1, np.float64)
+        j = ctypes.c_int64()
+        _check(lib().pond_incoh_ips(self._h, _ptr(out), ctypes.byref(j)))
+        return out, j.value
 
     def delays(self) -> np.ndarray:
         d = np.empty(self.nchan, np.int32)

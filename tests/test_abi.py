@@ -131,6 +131,9 @@ INCOH_CASES = [  # (options changed from a valid incoherent plan, expected code)
     (dict(period=0.0), "ARG"),
     (dict(fs=31e6), "ARG"),
     (dict(bw=0.0), "ARG"),
+    (dict(ips_len=32), "ARG"),
+    (dict(ips_len=8192), "ARG"),
+    (dict(ips_len=100), "ARG"),
 ]
 
 
