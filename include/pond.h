@@ -395,6 +395,46 @@ int pond_stats(pond_t h, pond_stats_t* s);
 int pond_fold_noalloc(const float* d_power, int64_t n, int64_t g0, double dtc_s, double period_s,
                       int32_t nbins, double* d_sum, int64_t* d_hits, void* cuda_stream);
 
+/*
+ * Fold with a polynomial phase model into a pulse stack (the fold of Sec. 3.4
+ * with the period of a timing model, as PONDER takes it from TEMPO2 predictors;
+ * the single-pulse stack of Sec. 4).  Series sample i is sample g = g0 + i of
+ * spacing dt_s from the first stream sample; its phase is
+ *   phi = sum_{k < ncoef} coef[k] tau^k,  tau = g dt_s - t_ref_s  (cycles),
+ * evaluated by Horner's rule with every multiply and add rounded on its own in
+ * FP64 (a spin-down model: coef = {phase0, 1/P, -Pdot/(2 P^2)}).  Rotation
+ * q = floor(phi), bin b = min(floor((phi - q) nbins), nbins - 1): with coef
+ * {0, 1/P} the bins are the constant-period fold's when g dt / P rounds as g
+ * (dt / P) does.  Rows: POND_STACK_ROTATION, one per rotation from the first
+ * sample's (row = q - first_rotation); POND_STACK_SUBINT, one per n_sub samples
+ * (row = i / n_sub).  Cell (row, b) receives the FP64 sum of its samples, added
+ * in sample order, and their count.
+ */
+#define POND_STACK_ROTATION 0
+#define POND_STACK_SUBINT 1
+
+/* pond_stack_rows: the number of rows pond_fold_stack fills for these arguments
+ * and the first sample's rotation (host arithmetic only).  Errors: POND_E_ARG
+ * (n or g0 < 0, dt_s <= 0, ncoef outside 1..8, nbins outside 1..4096, bad mode,
+ * n_sub < 1 for SUBINT, a non-finite coefficient, null pointer). */
+int pond_stack_rows(int64_t n, int64_t g0, double dt_s, const double* coef, int32_t ncoef, double t_ref_s,
+                    int32_t nbins, int32_t mode, int64_t n_sub, int64_t* rows, int64_t* first_rotation);
+
+/* pond_fold_stack: fold d_series[0..n) (device, FP32) into the caller-owned
+ * stack d_sum[rows][nbins] (device, FP64) and d_hits[rows][nbins] (device,
+ * int64), every cell written (rows as pond_stack_rows returns them, at most
+ * rows_cap); *rows and *first_rotation as from pond_stack_rows.  Work is
+ * enqueued on cuda_stream (NULL = legacy default stream); the call waits for a
+ * check that the phase model runs forwards over the whole series (a
+ * non-decreasing (rotation, bin) key, which the stack relies on).  Calls that
+ * overlap on the GPU share that check's flag and must be serialised.  Errors:
+ * as pond_stack_rows, POND_E_OVERRUN (rows > rows_cap; nothing written),
+ * POND_E_ARG (the phase model runs backwards; null device pointer with n > 0),
+ * POND_E_CUDA. */
+int pond_fold_stack(const float* d_series, int64_t n, int64_t g0, double dt_s, const double* coef, int32_t ncoef,
+                    double t_ref_s, int32_t nbins, int32_t mode, int64_t n_sub, double* d_sum, int64_t* d_hits,
+                    int64_t rows_cap, int64_t* rows, int64_t* first_rotation, void* cuda_stream);
+
 /* pond_strerror: static text for a return code.  pond_last_error: message of the
  * calling thread's last failure (empty if none). */
 const char* pond_strerror(int code);

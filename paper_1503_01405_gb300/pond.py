@@ -30,6 +30,8 @@ POND_SCHEDULE_AUTO = 0
 POND_SCHEDULE_FOUR_PASS = 1
 POND_NSTAGE = 9
 POND_NOALLOC_MAX_NBINS = 1024
+POND_STACK_ROTATION = 0
+POND_STACK_SUBINT = 1
 POND_INCOH_AID = 0
 POND_INCOH_CID = 1
 
@@ -45,7 +47,8 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_boxcar", "pond_candidates", "pond_candidates_scored", "pond_check_bounded_wait", "pond_cnn_create", "pond_cnn_set_params", "pond_cnn_params",
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches",
            "pond_incoh_create", "pond_incoh_run", "pond_incoh_info_get", "pond_incoh_filterbank",
-           "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy", "pond_incoh_ips"]
+           "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy", "pond_incoh_ips",
+           "pond_stack_rows", "pond_fold_stack"]
 
 
 class PondError(RuntimeError):
@@ -160,6 +163,11 @@ def lib() -> ctypes.CDLL:
         "pond_incoh_profile": [vp, vp, vp],
         "pond_incoh_delays": [vp, vp],
         "pond_incoh_ips": [vp, vp, P(ctypes.c_int64)],
+        "pond_stack_rows": [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp, ctypes.c_int32, ctypes.c_double,
+                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64)],
+        "pond_fold_stack": [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp, ctypes.c_int32, ctypes.c_double,
+                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, vp, ctypes.c_int64,
+                            P(ctypes.c_int64), P(ctypes.c_int64), vp],
         "pond_incoh_destroy": [vp],
     }
     for name, args in sig.items():
@@ -544,3 +552,32 @@ class Incoherent:
             self.close()
         except Exception:
             pass
+
+
+def stack_rows(n: int, g0: int, dt: float, coef, t_ref: float, nbins: int, mode: int = POND_STACK_ROTATION,
+               n_sub: int = 0):
+    """(rows, first rotation) of the stack pond_fold_stack fills (host arithmetic only)."""
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    rows, q0 = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pond_stack_rows(n, g0, dt, _ptr(c), c.size, t_ref, nbins, mode, n_sub, ctypes.byref(rows),
+                                 ctypes.byref(q0)))
+    return rows.value, q0.value
+
+
+def fold_stack(series, g0: int, dt: float, coef, t_ref: float, nbins: int, mode: int = POND_STACK_ROTATION,
+               n_sub: int = 0, stream=None):
+    """Fold a CUDA FP32 series with a polynomial phase model into a pulse stack:
+    (S [rows][nbins] FP64, H [rows][nbins] int64, first rotation), on the host."""
+    import torch
+    assert series.is_cuda and series.dtype == torch.float32 and series.is_contiguous()
+    n = series.numel()
+    rows, _ = stack_rows(n, g0, dt, coef, t_ref, nbins, mode, n_sub)
+    S = torch.empty((max(rows, 1), nbins), dtype=torch.float64, device=series.device)
+    H = torch.empty((max(rows, 1), nbins), dtype=torch.int64, device=series.device)
+    c = np.ascontiguousarray(coef, dtype=np.float64)
+    s = stream if stream is not None else torch.cuda.current_stream(series.device)
+    r, q0 = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pond_fold_stack(series.data_ptr(), n, g0, dt, _ptr(c), c.size, t_ref, nbins, mode, n_sub,
+                                 S.data_ptr(), H.data_ptr(), rows, ctypes.byref(r), ctypes.byref(q0), s.cuda_stream))
+    s.synchronize()
+    return S[:r.value].cpu().numpy(), H[:r.value].cpu().numpy(), q0.value

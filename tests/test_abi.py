@@ -157,3 +157,29 @@ def test_incoherent_reserved_fields_rejected():
     assert pond.lib().pond_incoh_create(ctypes.byref(h), ctypes.byref(o)) == pond.POND_E_ARG
     assert pond.lib().pond_incoh_create(None, ctypes.byref(o)) == pond.POND_E_ARG
     assert pond.lib().pond_incoh_destroy(None) == pond.POND_OK
+
+
+def test_stack_rows_match_the_oracle():
+    """The host's row count and first rotation are the oracle's, bit for bit, for
+    spin-down and cubic models, both row modes (pond_stack_rows needs no GPU)."""
+    import numpy as np
+    from oracle import stack as st
+    y = np.zeros(200_001)
+    for (t_ref, c), dt, g0 in (((0.0123, st.spin_model(0.7145, 4e-6, 0.0123, 0.3)[1]), 61.44e-6, 12345),
+                               ((2.5, np.array([0.3, 7.0, -0.02, 1e-4])), 1e-4, 0),
+                               ((-1.0, np.array([-5.2, 1.0 / 0.0331])), 4e-6, 777)):
+        for mode, n_sub in ((st.ROTATION, 0), (st.SUBINT, 4097)):
+            S, _, q0 = st.stack(y, g0, dt, c, t_ref, 64, mode, n_sub)
+            rows, first = pond.stack_rows(len(y), g0, dt, c, t_ref, 64, mode, n_sub)
+            assert rows == S.shape[0]
+            assert first == q0
+
+
+@pytest.mark.parametrize("kw", [dict(dt=0.0), dict(coef=[]), dict(coef=[0.0] * 9), dict(nbins=0),
+                                dict(mode=1, n_sub=0), dict(mode=5), dict(n=-1), dict(coef=[float("nan"), 1.0])])
+def test_stack_argument_errors(kw):
+    a = dict(n=1000, g0=0, dt=1e-3, coef=[0.0, 2.0], t_ref=0.0, nbins=16, mode=0, n_sub=0)
+    a.update(kw)
+    with pytest.raises(pond.PondError) as ei:
+        pond.stack_rows(**a)
+    assert ei.value.name == "ARG"
