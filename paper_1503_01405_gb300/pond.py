@@ -464,6 +464,7 @@ class Incoherent:
         _check(lib().pond_incoh_create(ctypes.byref(h), ctypes.byref(o)))
         self._h = h
         self.nchan, self.nbins, self.channels, self.ips_len = nchan, nbins, input_channels, ips_len
+        self.device = device
 
     def run_device(self, ptr: int, nbytes: int, stream: int = 0) -> None:
         """Enqueue the mode over nbytes of int8 at device address ptr on ``stream``."""
@@ -479,13 +480,13 @@ class Incoherent:
     def run(self, x: np.ndarray, stream=None) -> None:
         """Copy host int8 input to the device (through pinned memory) and run."""
         import torch
-        dev = torch.device("cuda", torch.cuda.current_device())
+        dev = torch.device("cuda", self.device)
         src = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int8))
         if not src.is_pinned():
             src = src.pin_memory()
         s = stream if stream is not None else torch.cuda.current_stream(dev)
-        d = torch.empty(src.numel(), dtype=torch.int8, device=dev)
-        with torch.cuda.stream(s):
+        with torch.cuda.stream(s):      # the buffer belongs to the stream that copies and reads it
+            d = torch.empty(src.numel(), dtype=torch.int8, device=dev)
             d.copy_(src, non_blocking=True)
         self.run_tensor(d, s)
         self._keep = (src, d)      # alive until the next run or a result read
