@@ -184,3 +184,19 @@ def test_generator_pulsar_recovered_at_its_phase():
     e0, _ = excess(r0)
     assert peak in range(30, 34)                # phase 0.5 of 64 bins
     assert e.max() > 4 * e0.max()
+
+
+def test_eq2_smear_of_the_1024_channel_filterbank():
+    """Eq. 2 for the filterbank's own channels (1024 over 16 MHz, per unit DM):
+    the channel at the band centre and the lowest channel bracket the 3.8 us the
+    paper quotes, and the smear falls with frequency across the band."""
+    import os
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_numbers.txt")
+    quoted = None
+    for line in open(golden):
+        if line.startswith("eq2_smear_1024ch_per_dm"):
+            quoted = float(line.split()[1])
+    p = _plan(dm=1.0, nchan=1024)
+    smear_us = np.array([inc.residual_smear_ms(p, k) for k in range(1024)]) * 1e3
+    assert smear_us[512] < quoted < smear_us[0]
+    assert np.all(np.diff(smear_us) < 0)
