@@ -377,7 +377,7 @@ def run_incoherent(args, rank, ws, dist):
     out = {}
 
     def step_host():
-        eng.run(xh)
+        eng.run(x_host)
         D, _ = eng.series()
         s_, h_ = eng.profile()
         out["bytes"] = D.nbytes + s_.nbytes + h_.nbytes

@@ -477,11 +477,16 @@ class Incoherent:
         s = stream if stream is not None else torch.cuda.current_stream(t.device)
         self.run_device(t.data_ptr(), t.numel(), s.cuda_stream)
 
-    def run(self, x: np.ndarray, stream=None) -> None:
-        """Copy host int8 input to the device (through pinned memory) and run."""
+    def run(self, x, stream=None) -> None:
+        """Copy host int8 input (a numpy array, or a CPU int8 tensor, ideally in pinned
+        memory) to the device and run."""
         import torch
         dev = torch.device("cuda", self.device)
-        src = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int8))
+        if isinstance(x, torch.Tensor):
+            assert x.device.type == "cpu" and x.dtype == torch.int8
+            src = x.contiguous()
+        else:
+            src = torch.from_numpy(np.ascontiguousarray(x, dtype=np.int8))
         if not src.is_pinned():
             src = src.pin_memory()
         s = stream if stream is not None else torch.cuda.current_stream(dev)
