@@ -9,6 +9,11 @@
  * the interstellar-medium transfer function H of Eq. 4, inverse transformed
  * into sub-channels, detected (|v|^2, summed over sub-channels), folded at the
  * pulsar period (the fold of Sec. 3.4) and decimated to a time series.
+ * Around it: batched DM trials with an FFT-length autotuner, a boxcar
+ * single-pulse detector and a small CNN classifier (pond_candidates*,
+ * pond_cnn_*), the incoherent AID / CID modes of Sec. 3.4 and the
+ * scintillation mode of Sec. 3.5 (pond_incoh_*), and folding with a phase
+ * model into pulse stacks (pond_fold_stack).
  *
  * Conventions shared by every entry point:
  *  - Units: frequencies in MHz, the sampling rate fs in real samples per second

@@ -183,3 +183,32 @@ def test_stack_argument_errors(kw):
     with pytest.raises(pond.PondError) as ei:
         pond.stack_rows(**a)
     assert ei.value.name == "ARG"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the C header's field offsets and
+    size (a C program compiled against include/pond.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pond_opts": pond.pond_opts, "pond_meta": pond.pond_meta, "pond_cand": pond.pond_cand,
+               "pond_stats_t": pond.pond_stats_t, "pond_incoh_opts": pond.pond_incoh_opts,
+               "pond_incoh_info": pond.pond_incoh_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pond.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} . %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (l.split() for l in out if l.strip())}
+    for cname, cls in structs.items():
+        assert got[(cname, ".")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
