@@ -1,0 +1,59 @@
+"""Host-side helpers of bench.py that shape its JSON line (no GPU): the clock
+record, the DRAM-traffic lookup keyed by the kernel sources, the workload
+description and the peak denominators."""
+import os
+import shutil
+
+import bench
+
+
+def test_clock_summary_median_max_and_reasons():
+    c = bench.Clocks(0)
+    c.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "1995", "2070", "1390", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "2055", "2070", "1200", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["garbage"], ["0", "[N/A]", "2070"]]
+    s = c.summary()
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.Clocks(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_traffic_lookup_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The committed counters are returned while the pass sources are the ones they
+    were taken with, and null for a kernel without counters or changed sources."""
+    rows = {}
+    for line in open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, h, v = line.split()[:3]
+            rows[k] = float(v)
+    assert rows
+    for k, v in rows.items():
+        assert bench.traffic_from_profiles(k) == v
+    assert bench.traffic_from_profiles("k_not_a_kernel") is None
+    # a copy of the tree whose pass sources differ by one byte
+    root = tmp_path / "r"
+    csrc = root / "paper_1503_01405_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (root / "profiles").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "ncu_traffic.txt"), root / "profiles")
+    for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_1503_01405_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    k = next(iter(rows))
+    assert bench.traffic_from_profiles(k) == rows[k]
+    with open(csrc / "passes.cuh", "a") as f:
+        f.write("\n")
+    assert bench.traffic_from_profiles(k) is None
+
+
+def test_workload_description_and_peaks():
+    one = bench.workload_config(1_920_000_000)
+    two = bench.workload_config(1_920_000_000, 2)
+    assert one["samples_per_step"] == two["samples_per_step"] == 1_920_000_000
+    assert "1.92e9 int8 samples" in one["workload"] and "interleaved N / S" in two["workload"]
+    assert one["nfft"] == 1 << 24 and one["nchan"] == 64
+    p = bench.measured_peaks()
+    assert p["hbm_gbs"] > 1000 and p["src"] in ("measured", "fallback")
+    if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
+        assert p["src"] == "measured"
