@@ -189,7 +189,10 @@ int pond_plan(pond_t* out, double f0_mhz, double bw_mhz, double fs_hz, double dm
 int pond_plan_ex(pond_t* out, const pond_opts* opts);
 
 /*
- * pond_push: append n int8 samples from HOST memory x (any n >= 0).  The data
+ * pond_push: append n int8 samples from HOST memory x (any n >= 0).  This is
+ *   the input of the paper's GPU flow (Sec. 3.7, Fig. "gpuflow": the digitised
+ *   voltages held on the host are sent to the device's global memory; Sec. 3.1:
+ *   the ADC delivers 8-bit real samples of each half of the band).  The data
  *   are copied to the device before the call returns (pinned memory copies
  *   asynchronously, pageable memory through the driver's staging), so x may be
  *   reused at once; processing of complete segments continues asynchronously.
@@ -199,7 +202,9 @@ int pond_plan_ex(pond_t* out, const pond_opts* opts);
 int pond_push(pond_t h, const int8_t* x, size_t n);
 
 /*
- * pond_push_device: append n int8 samples already in DEVICE memory d_x.  All
+ * pond_push_device: append n int8 samples already in DEVICE memory d_x (the
+ *   same input as pond_push, Sec. 3.7, for a caller whose samples are already
+ *   in global memory, skipping the host-to-device copy of the flow).  All
  *   work is enqueued on cuda_stream (a cudaStream_t; NULL = the handle's own
  *   stream, which then waits for the legacy default stream), in stream order,
  *   and reads d_x directly for segments that lie inside it.  d_x must stay
@@ -210,7 +215,9 @@ int pond_push(pond_t h, const int8_t* x, size_t n);
 int pond_push_device(pond_t h, const int8_t* d_x, size_t n, void* cuda_stream);
 
 /*
- * pond_flush: end of stream.  Processes the zero-padded tail and emits every
+ * pond_flush: end of stream (Sec. 3.7: the overlap-save segmentation keeps
+ *   only outputs whose filter support lies inside the data, so the last
+ *   segment is completed here).  Processes the zero-padded tail and emits every
  *   output whose support lies inside the stream (g < floor(n_total/(2 nchan))
  *   - n_fut), then waits for the device.  Further pushes return POND_E_STATE.
  *   Errors: POND_E_CUDA; POND_E_TIMEOUT when a tensor-core stage's bounded wait
@@ -232,9 +239,12 @@ int pond_sync(pond_t h);
 int pond_reset(pond_t h);
 
 /*
- * pond_profile: snapshot of the folded profile (non-destructive; waits for the
- *   device; POND_E_STATE for a batched plan, which does not fold).
- *   device).  sum[b] (FP64) is the sum of detected power P[g] over the channel
+ * pond_profile: snapshot of the folded profile (Sec. 3.7: the last thread of
+ *   the GPU flow folds the dedispersed series to the required number of bins;
+ *   the fold thread of Sec. 3.4 folds at the period from the timing model, here
+ *   a constant period with the epoch at the first stream sample).
+ *   Non-destructive; waits for the device; POND_E_STATE for a batched plan,
+ *   which does not fold.  sum[b] (FP64) is the sum of detected power P[g] over the channel
  *   samples folded into bin b = min(floor(frac(g dtc / P) nbins), nbins-1)
  *   (phase in FP64, epoch = first stream sample), hits[b] their count; the
  *   mean profile is sum/hits.  sum and hits hold nbins entries; either may be
@@ -250,7 +260,9 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta);
 int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntrials);
 
 /*
- * pond_timeseries: drain completed samples of the decimated time series.
+ * pond_timeseries: drain completed samples of the decimated time series
+ *   (Sec. 3.7: the dedispersed series is the output of the flow; Sec. 3.4:
+ *   detected power is added to reach the desired time resolution).
  *   Sample j sums P[g] over the emitted g with floor(g / D) = j, where
  *   D = t_dec fs / (2 nchan) channel samples (an exact rational; with 4 us
  *   channel samples and t_dec = 61.44 us, bins hold 15 or 16 samples).
@@ -266,7 +278,9 @@ int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n
 
 /*
  * pond_voltages: drain dedispersed sub-channel voltages v_c[g] (complex, FP32
- *   re/im pairs) of the emitted channel samples; only with opts.want_voltages.
+ *   re/im pairs) of the emitted channel samples: the output of the inverse FFT
+ *   after multiplication by the inverse of H (Sec. 3.7, Eq. 4), before the
+ *   power detection of Sec. 3.4; only with opts.want_voltages (tests).
  *   out_c is laid out [nchan][cap][2]; at most cap samples per channel are
  *   copied; *n_out receives the number per channel, *first_g the g of the first.
  *   Errors: POND_E_STATE when the plan was made without want_voltages.
@@ -297,7 +311,10 @@ int pond_boxcar(const float* d_series, int32_t ndm, int64_t n, int64_t stride, d
  * pond_candidates: pond_boxcar over the handle's completed series samples that
  *   have not been drained yet (all trials of a batched plan), with index = the
  *   series sample index j and dm = the trial's DM.  Call it before
- *   pond_timeseries drains the samples.
+ *   pond_timeseries drains the samples.  Sec. 5 names automatic detection of
+ *   transients as the paper's plan; the detector is this library's.  Besides
+ *   the handle and the output array it takes the S/N threshold (the boxcar's
+ *   detection level, 6 in the learned form), so callers choose it per call.
  */
 int pond_candidates(pond_t h, double threshold, pond_cand* out, size_t cap, size_t* n_found);
 
@@ -371,7 +388,10 @@ int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand
  */
 int pond_check_bounded_wait(double limit_s, int32_t device, double* waited_s);
 
-/* pond_stats: counters and per-stage GPU times (waits for the device). */
+/* pond_stats: counters and per-stage GPU times (waits for the device).  The
+ * stage times give the paper's measure of real-time capability, the compute
+ * to observed ratio (Sec. 3.4: processing time over digitisation time, which
+ * must stay below 1), as stage time over samples_in / fs. */
 int pond_stats(pond_t h, pond_stats_t* s);
 
 /*
@@ -390,13 +410,25 @@ int pond_stats(pond_t h, pond_stats_t* s);
  *   process exits, so nbins is limited to POND_NOALLOC_MAX_NBINS.  The work
  *   is enqueued on cuda_stream (a cudaStream_t of the current device, NULL =
  *   legacy default stream).  The first call on a device looks up the array's
- *   device address; make that first call before any stream capture.  All
- *   calls share the one array: calls that overlap on the GPU (other streams,
- *   other threads) race and must be serialised by the caller.
+ *   device address; make that first call before any stream capture.  That
+ *   address is cached per device for the life of the process: after a
+ *   cudaDeviceReset it is stale, so do not call this entry point again in
+ *   that process.  All calls share the one array: calls that overlap on the
+ *   GPU (other streams, other threads) race and must be serialised by the
+ *   caller.  Each call overwrites the partial rows it reads, so nothing in
+ *   the array needs clearing between calls.
+ *   Accumulation: a call never overwrites d_sum / d_hits; it adds its n
+ *   samples to them, so a profile can be built over many calls.
+ *   Limit per call: a CTA counts its hits in int32 over about n / 304
+ *   samples, so n may not exceed POND_NOALLOC_MAX_SAMPLES (2^39, about
+ *   5.5e11, 4.8 hours of 32 MS/s channel samples); split longer series over
+ *   several calls.
  *   Errors: POND_E_ARG (nbins > POND_NOALLOC_MAX_NBINS or < 1, n < 0,
- *   g0 < 0, dtc_s or period_s <= 0, null pointer with n > 0), POND_E_CUDA.
+ *   n > POND_NOALLOC_MAX_SAMPLES, g0 < 0, dtc_s or period_s <= 0, null
+ *   pointer with n > 0), POND_E_CUDA.
  */
 #define POND_NOALLOC_MAX_NBINS 1024
+#define POND_NOALLOC_MAX_SAMPLES (1LL << 39)
 int pond_fold_noalloc(const float* d_power, int64_t n, int64_t g0, double dtc_s, double period_s,
                       int32_t nbins, double* d_sum, int64_t* d_hits, void* cuda_stream);
 
@@ -445,7 +477,8 @@ int pond_fold_stack(const float* d_series, int64_t n, int64_t g0, double dt_s, c
 const char* pond_strerror(int code);
 const char* pond_last_error(void);
 
-/* pond_destroy: wait for the device, release everything the handle owns.
+/* pond_destroy: wait for the device, release everything the handle owns
+ * (the end of an observation; the paper has no passage for it).
  * NULL is accepted. */
 int pond_destroy(pond_t h);
 

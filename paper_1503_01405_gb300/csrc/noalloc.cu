@@ -62,6 +62,10 @@ extern "C" int pond_fold_noalloc(const float* d_power, int64_t n, int64_t g0, do
     snprintf(msg, sizeof msg, "pond_fold_noalloc: nbins %d exceeds the limit of %d", nbins, POND_NOALLOC_MAX_NBINS);
     return pond::set_error(POND_E_ARG, msg);
   }
+  // per-CTA hits are int32 over ceil(n / kParts) samples (rounded up to 128)
+  static_assert(POND_NOALLOC_MAX_SAMPLES / kParts + 128 < (1LL << 31), "per-CTA hit count must fit in int32");
+  if (n > POND_NOALLOC_MAX_SAMPLES)
+    return pond::set_error(POND_E_ARG, "pond_fold_noalloc: n exceeds the per-call limit POND_NOALLOC_MAX_SAMPLES");
   if (n == 0) return POND_OK;
   if (!d_power || !d_sum || !d_hits) return pond::set_error(POND_E_ARG, "pond_fold_noalloc: null pointer");
   int dev = 0;

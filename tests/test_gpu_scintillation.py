@@ -61,7 +61,7 @@ def test_scintillation_spectrum_matches_oracle(case):
     assert rel(A, A_ref) <= 1e-5
     assert rel(A[1:], A_ref[1:]) <= 1e-3
     f_mod = int(round(fmod * L * p.ts))
-    assert int(np.argmax(A[1:])) + 1 == int(np.argmax(A_ref[1:])) == f_mod
+    assert int(np.argmax(A[1:])) + 1 == int(np.argmax(A_ref[1:])) + 1 == f_mod
     assert info["launches"] == 5
 
 

@@ -4,9 +4,10 @@ Some callers may not call cudaMalloc: a real-time acquisition thread that must
 never stall (allocation and release can synchronise the whole device), or a
 host application whose memory manager owns every device allocation.  They fold
 detected power with pond_fold_noalloc, which uses a fixed device array as its
-scratch instead of allocating.  Here its profile is checked against the
-engine's own fold (pond_push + pond_profile) over two calls in a row that
-share that array, with the same tolerances as the other GPU tests.
+scratch instead of allocating.  Its profile, built over two calls in a row that
+share that array, is checked against the FP64 oracle's fold of the same power
+series (hits exactly, sums to the profile tolerance of the other GPU tests) and
+against the engine's own fold (pond_push + pond_profile) of the same stream.
 """
 import ctypes
 
@@ -30,18 +31,23 @@ def built():
     pbuild.build()
 
 
-def test_noalloc_fold_matches_engine_fold():
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_noalloc_fold_matches_oracle_and_engine():
     import torch
     p = pcd.make_plan(326.5, 16.0, 32e6, 0.3, 1 << 16, 16, 128, 0.033)
-    x = synth.make_stream(synth.StreamSpec(n=5 * p.S + 4321, seed=21, dm=p.dm, period=p.period,
+    x = synth.make_stream(synth.StreamSpec(n=60 * p.S + 4321, seed=21, dm=p.dm, period=p.period,
                                            snr=60.0, duty=0.05))
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, want_voltages=True) as e:
         e.push(x)
         e.flush()
-        s_ref, h_ref, _ = e.profile()
+        s_eng, h_eng, _ = e.profile()
         V, g0 = e.voltages()
     # detected power of the emitted channel samples, summed over sub-channels
     P = (V.real.astype(np.float64) ** 2 + V.imag.astype(np.float64) ** 2).sum(axis=0).astype(np.float32)
+    s_ora, h_ora = pcd.fold(p, P.astype(np.float64), g0)
     dP = torch.from_numpy(P).cuda()
     d_sum = torch.zeros(p.nbins, dtype=torch.float64, device="cuda")
     d_hits = torch.zeros(p.nbins, dtype=torch.int64, device="cuda")
@@ -55,8 +61,15 @@ def test_noalloc_fold_matches_engine_fold():
     torch.cuda.synchronize()
     s = d_sum.cpu().numpy()
     h = d_hits.cpu().numpy()
-    assert np.array_equal(h, h_ref)
-    assert np.linalg.norm(s - s_ref) / np.linalg.norm(s_ref) <= TOL_P
+    assert np.array_equal(h, h_ora)
+    assert rel(s, s_ora) <= TOL_P
+    # the engine's fold of the same stream: same bins, same sums
+    assert np.array_equal(h, h_eng)
+    assert rel(s, s_eng) <= TOL_P
+    # and the whole FP64 path from the int8 stream: the bins, and the profile within tolerance
+    r = pcd.run(p, x)
+    assert np.array_equal(h, r.prof_hits)
+    assert rel(s, r.prof_sum) <= TOL_P
 
 
 def test_noalloc_fold_rejects_too_many_bins():
