@@ -616,7 +616,6 @@ def run_learned(args, rank):
     import numpy as np
     import torch
 
-    from oracle import cnn as _cnn_init   # parameter initialisation only (uniforms -> He bounds)
     from paper_1503_01405_gb300 import build as pbuild
     from paper_1503_01405_gb300 import learn, pond, synth
 
@@ -625,7 +624,7 @@ def run_learned(args, rank):
     Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000, shifts=args.shifts)
     Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000, shifts=args.shifts)
     gen_s = time.perf_counter() - t0
-    theta = _cnn_init.init_params(synth.uniform(99, 0, 0, _cnn_init.n_params())).astype(np.float32)
+    theta = learn.init_params(99)
     clf = pond.Classifier(theta, max_batch=512)
     torch.cuda.synchronize()
     t1 = time.perf_counter()

@@ -22,6 +22,31 @@ ROWS, COLS = 32, 256          # patch: DM trials x series samples
 F0, BW, FS = 326.5, 16.0, 32e6
 
 
+CONV_C, CONV_K, NCLASS = 32, 7, 4   # the network's width, kernel length and classes (pond.h)
+
+
+def init_params(seed: int) -> np.ndarray:
+    """Seeded starting parameters in the flat layout of pond_cnn_create.
+
+    Conv weights w[co][ci][k] uniform in +-sqrt(6 / fan_in) with fan_in =
+    CONV_C * CONV_K (He et al. 2015, uniform form, for ReLU layers); conv
+    biases zero; the final linear layer's weights uniform in
+    +-0.5 sqrt(6 / CONV_C) and its biases zero.  The uniforms are the
+    counter-based generator's words of stream 0 of ``seed``."""
+    n_conv = CONV_C * CONV_C * CONV_K
+    theta = np.zeros(pond.CNN_NPARAM, np.float64)
+    u = synth.uniform(seed, 0, 0, pond.CNN_NPARAM)
+    lim = math.sqrt(6.0 / (CONV_C * CONV_K))
+    off = 0
+    for _layer in range(3):
+        theta[off:off + n_conv] = lim * (2.0 * u[off:off + n_conv] - 1.0)
+        off += n_conv + CONV_C
+    n_fc = NCLASS * CONV_C
+    theta[off:off + n_fc] = 0.5 * math.sqrt(6.0 / CONV_C) * (2.0 * u[off:off + n_fc] - 1.0)
+    assert off + n_fc + NCLASS == pond.CNN_NPARAM
+    return theta.astype(np.float32)
+
+
 def trial_grid(ndm: int = 128, dm_max: float = 60.0) -> list[float]:
     return [dm_max * d / (ndm - 1) for d in range(ndm)]
 
