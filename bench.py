@@ -10,12 +10,17 @@ and flushes; the stream (1.92 GB) is larger than L2, so no flush is needed.
 JSON line fields: value = Msamples/s with the stream resident in HBM
 (device push); e2e = the same through pond_push from pinned host memory (H2D
 inside the timed region) plus the D2H read of the profile and series;
-roofline = the dominant kernel's algorithmic bytes / its CUDA-event time
-against measured HBM bandwidth; cpu_baseline = the FP64 oracle on a bounded
-slice on the host cores.
+roofline = the dominant kernel's algorithmic FP32 operations / its CUDA-event
+time against the FP32 ceiling (nominal, and measured by the library's FMA
+probe), with the method's algorithmic bytes and the pass's own bytes against
+measured HBM beside it, and the same for the whole path; cpu_baseline = the
+FP64 oracle on the host cores (all of them, one process each, and one
+thread); precision / batched = the split-BF16 tensor-core form beside the
+FP32 path (speed and error against the oracle) and the 128-trial batched
+form on one 8 s chunk.
 
 ``--impl reference`` times the FP64 CPU oracle (the only reference there is:
-the paper publishes no code) on host cores over a bounded slice per step.
+the paper publishes no code) on every host core over a bounded slice per step.
 Multi-GPU: replicas only (one independent stream per rank, no collective).
 """
 from __future__ import annotations
@@ -64,6 +69,135 @@ def measured_peaks() -> dict:
             d = json.load(f)
         return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
     return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+# FP32 lanes per SM of the Blackwell SM and the GB300's SM count and maximum SM
+# clock: the nominal FP32 ceiling 152 x 128 x 2 x 2.07e9 = 80.5 TFLOP/s
+FP32_LANES_PER_SM, N_SM, SM_MAX_HZ = 128, 152, 2.07e9
+FP32_NOMINAL_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_HZ / 1e12
+
+
+def host_cpu() -> dict:
+    """Host core count and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"nproc": cores, "model": model}
+
+
+def fp32_peak(pond, torch, dev, stream) -> dict:
+    """FP32 FMA ceiling of this GPU, measured with the library's probe kernel
+    (4 CTAs of 512 threads per SM, 8 independent chains per thread), best of 5
+    launches of about 50 ms each, CUDA events on the launching stream."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 4 * sms
+    out = torch.empty(blocks * 512, dtype=torch.float32, device=dev)
+    iters = 40000
+    pond.probe_fp32_fma(out.data_ptr(), blocks, 100, stream.cuda_stream)     # warm-up
+    best = None
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = pond.probe_fp32_fma(out.data_ptr(), blocks, iters, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+        best = t if best is None else max(best, t)
+    assert torch.isfinite(out).all()
+    return {"tflops": best, "sms": sms, "kernel": "k_fma_probe (pond_probe_fp32_fma)",
+            "nominal_tflops": FP32_NOMINAL_TFLOPS}
+
+
+def _oracle_worker_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from oracle import pcd  # noqa: F401  (import once per worker, outside the timed work)
+
+
+def _oracle_worker(job):
+    """Dedisperse whole segments of the shared stream with the FP64 oracle."""
+    import numpy as np
+
+    from oracle import pcd
+    path, n, segs = job
+    x = np.memmap(path, dtype=np.int8, mode="r", shape=(n,))
+    p = pcd.make_plan(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                      PLAN["t_dec"])
+    t0 = time.perf_counter()
+    for s in segs:
+        pcd.dedisperse_segment(p, np.asarray(x[s * p.S:s * p.S + p.nfft]))
+    dt = time.perf_counter() - t0
+    del x
+    return len(segs), dt
+
+
+class OraclePool:
+    """The FP64 oracle on all host cores: worker processes (started with spawn,
+    before any work is timed) each dedisperse whole segments of one stream,
+    shared through a read-only file mapping.  Throughput = samples advanced /
+    wall time of the round."""
+
+    def __init__(self, x_host, workers: int | None = None):
+        import concurrent.futures
+        import multiprocessing as mp
+        import tempfile
+
+        import numpy as np
+        self.cpu = host_cpu()
+        self.workers = max(1, min(workers or self.cpu["nproc"], 64))
+        self.S = int(x_host_seg_step())
+        self.n = len(x_host)
+        fd, self.path = tempfile.mkstemp(prefix="pond_oracle_", suffix=".i8")
+        os.close(fd)
+        self.ex = None
+        try:
+            np.asarray(x_host, dtype=np.int8).tofile(self.path)
+            self.ex = concurrent.futures.ProcessPoolExecutor(self.workers, mp_context=mp.get_context("spawn"),
+                                                             initializer=_oracle_worker_init)
+            # start every worker (one short job each) before anything is timed
+            list(self.ex.map(_oracle_worker, [(self.path, self.n, [])] * self.workers))
+        except BaseException:
+            self.close()
+            raise
+        self.max_seg = (self.n - PLAN["nfft"]) // self.S + 1
+
+    def round(self, segs_per_worker: int, first: int = 0):
+        """One timed round: worker w takes segments first + w, first + w + W, ...
+        (modulo the segments the stream holds); returns (samples advanced, wall
+        seconds, segments)."""
+        total = self.workers * segs_per_worker
+        segs = [(first + i) % self.max_seg for i in range(total)]
+        jobs = [(self.path, self.n, segs[w::self.workers]) for w in range(self.workers)]
+        t0 = time.perf_counter()
+        done = list(self.ex.map(_oracle_worker, jobs))
+        wall = time.perf_counter() - t0
+        nseg = sum(d[0] for d in done)
+        return nseg * self.S, wall, nseg
+
+    def close(self):
+        if self.ex is not None:
+            self.ex.shutdown()
+            self.ex = None
+        if self.path and os.path.exists(self.path):
+            os.unlink(self.path)
+        self.path = None
+
+
+def x_host_seg_step() -> int:
+    """Real samples between segment starts of the full-rate plan (the oracle's geometry)."""
+    from oracle import pcd
+    return pcd.make_plan(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
+                         PLAN["t_dec"]).S
 
 
 class Clocks:
@@ -209,46 +343,45 @@ def oracle_rate(x_host, seconds_budget: float = 20.0):
 
 
 def run_reference(args, rank, ws, dist):
+    """The FP64 oracle on every host core (one process per core, whole segments
+    of the full-rate plan); each step is one round of one segment per core."""
     if rank != 0:
         return
-    import numpy as np
     from paper_1503_01405_gb300 import synth
     spec = synth.replace(synth.FULL_RATE, n=3 * (1 << 24))
     x = synth.make_stream(spec)
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, nseg, samples, dt = oracle_rate(x, seconds_budget=10.0)
-        if i >= args.warmup:
-            vals.append((v, samples, dt))
-    v = sum(s for _, s, _ in vals) / sum(d for _, _, d in vals) / 1e6
+    pool = OraclePool(x)
+    try:
+        vals = []
+        for i in range(args.warmup + args.steps):
+            samples, wall, nseg = pool.round(1, first=i)
+            if i >= args.warmup:
+                vals.append((samples, wall))
+    finally:
+        pool.close()
+    v = sum(a for a, _ in vals) / sum(d for _, d in vals) / 1e6
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, _, d in vals) / len(vals),
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(d for _, d in vals) / len(vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": workload_config(int(vals[0][1])),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(vals)} steps x whole segments of a {spec.n}-sample slice "
-                                       "of the full-rate workload (FP64 numpy, single thread)"},
+            "config": workload_config(int(vals[0][0])),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                             "host": pool.cpu,
+                             "sample": f"{len(vals)} steps x {pool.workers} whole nfft-2^24 segments (one per "
+                                       f"core, {pool.workers} processes) of a {spec.n}-sample slice of the "
+                                       "full-rate workload, FP64 numpy"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args, rank, ws, dist):
-    """Batched DM trials: an 8 s chunk (2.56e8 samples) with 10 injected single
-    pulses, 128 trials DM_d = 60 d / 127, 64 sub-channels, 32 us series, FFT
-    length per trial group chosen by the autotuner from {2^22, 2^23, 2^24}."""
+def batched_core(dev, local, stream, steps, warmup, seed_offset=0, samples=0, dist=None):
+    """Batched DM trials on one 8 s chunk: returns the timing and the plan's choices."""
     import torch
 
-    from paper_1503_01405_gb300 import build as pbuild
     from paper_1503_01405_gb300 import pond, synth
-
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pbuild.build()
-    spec = synth.replace(synth.BATCH_CHUNK, seed=synth.BATCH_CHUNK.seed + rank)
-    if args.samples:
-        spec = synth.replace(spec, n=args.samples)
+    spec = synth.replace(synth.BATCH_CHUNK, seed=synth.BATCH_CHUNK.seed + seed_offset)
+    if samples:
+        spec = synth.replace(spec, n=samples)
     pulses = synth.draw_pulses(spec.seed, 10, spec.n / spec.fs)
     x_dev = synth.make_chunk_torch(spec, pulses, dev)
     torch.cuda.synchronize()
@@ -258,16 +391,14 @@ def run_batched(args, rank, ws, dist):
     plan_s = time.perf_counter() - t0
     _, nf = eng.trials()
     groups = {int(n): int((nf == n).sum()) for n in sorted(set(nf.tolist()))}
-    stream = torch.cuda.current_stream(dev)
 
     def step():
         eng.reset()
         eng.push_tensor(x_dev, stream)
         eng.flush()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    st0 = eng.stats()
     torch.cuda.synchronize()
     quiet_gc()
     barrier(dist)
@@ -275,7 +406,7 @@ def run_batched(args, rank, ws, dist):
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -283,24 +414,127 @@ def run_batched(args, rank, ws, dist):
     ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
     st1 = eng.stats()
     T, C, j0 = eng.timeseries()
-    value = ws * spec.n * args.steps / (ms / 1e3) / 1e6
+    tuned = eng.tuning() if hasattr(eng, "tuning") else None
+    eng.close()
+    del x_dev
+    return {"ms": ms, "n": spec.n, "groups": groups, "plan_s": plan_s, "series_shape": list(T.shape),
+            "launches_per_step": int(st1["kernel_launches"]), "clocks": clk.summary(), "tuning": tuned}
+
+
+def run_batched(args, rank, ws, dist):
+    """Batched DM trials: an 8 s chunk (2.56e8 samples) with 10 injected single
+    pulses, 128 trials DM_d = 60 d / 127, 64 sub-channels, 32 us series, FFT
+    length per trial group chosen by the autotuner from {2^22, 2^23, 2^24}."""
+    import torch
+
+    from paper_1503_01405_gb300 import build as pbuild
+    from paper_1503_01405_gb300 import synth
+
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pbuild.build()
+    stream = torch.cuda.current_stream(dev)
+    r = batched_core(dev, local, stream, args.steps, args.warmup, seed_offset=rank, samples=args.samples, dist=dist)
+    value = ws * r["n"] * args.steps / (r["ms"] / 1e3) / 1e6
     if rank == 0:
         line = {"metric": METRIC + " [batched DM trials]", "value": value, "unit": UNIT, "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "realtime_factor": value / REALTIME_MSPS,
                 "trial_samples_per_s": value * 1e6 * len(synth.BATCH_DMS),
-                "config": {"workload": "batched: 8 s chunk (2.56e8 int8 samples, 10 injected pulses), "
-                                       "128 DM trials 0..60, 64 sub-channels, 32 us series, autotuned nfft",
-                           "samples_per_step": spec.n, "trials": len(synth.BATCH_DMS), "nfft_groups": groups,
-                           "plan_s_incl_autotune": plan_s, "series_shape": list(T.shape),
-                           "l2": "inputs larger than L2"},
-                "gpu_launches": int(st1["kernel_launches"]) * args.steps,
-                "clocks": clk.summary()}
+                "config": {"workload": BATCHED_WORKLOAD, "samples_per_step": r["n"],
+                           "trials": len(synth.BATCH_DMS), "nfft_groups": r["groups"],
+                           "plan_s_incl_autotune": r["plan_s"], "series_shape": r["series_shape"],
+                           "tuning": r["tuning"], "l2": "inputs larger than L2"},
+                "gpu_launches": r["launches_per_step"] * args.steps,
+                "clocks": r["clocks"]}
         print(json.dumps(line), flush=True)
-    eng.close()
+
+
+BATCHED_WORKLOAD = ("batched: 8 s chunk (2.56e8 int8 samples, 10 injected pulses), 128 DM trials 0..60, "
+                    "64 sub-channels, 32 us series, autotuned nfft")
+
 
 PREC_PLAN = dict(dm=3.0, nfft=1 << 21, nchan=1, nbins=256, period=0.253, t_dec=61.44e-6)
+
+
+def precision_brief(dev, local, stream, steps=3, warmup=2):
+    """The precision form beside the FP32 path, for the headline line: the
+    2^23-sample stream (nfft 2^21, one channel; L2 flushed before each timed
+    step) and the full-rate geometry on a 2^28-sample slice, in FP32 and with
+    split-BF16 tensor-core radix-16 stages (three and five terms), plus the
+    error of every output of each form against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import pcd
+    from paper_1503_01405_gb300 import pond, synth
+    P = PREC_PLAN
+    xh = synth.make_stream(synth.SMALL)
+    n = len(xh)
+    x_dev = torch.from_numpy(xh).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    precs = {"fp32": pond.POND_FP32, "bf16x3": pond.POND_SPLIT_BF16, "bf16x5": pond.POND_SPLIT_BF16_5T}
+
+    def engine(prec, plan, want_voltages=False):
+        return pond.Engine(F0, BW, FS, plan["dm"], plan["nfft"], plan["nchan"], plan["nbins"], plan["period"],
+                           t_dec=plan["t_dec"], want_voltages=want_voltages, device=local, precision=prec)
+
+    def timed(eng, x, k, w, flush_l2):
+        def step():
+            eng.reset()
+            eng.push_tensor(x, stream)
+            eng.flush()
+        for _ in range(w):
+            step()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(k):
+            if flush_l2:
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total
+
+    small, full = {}, {}
+    for name, prec in precs.items():
+        with engine(prec, P) as e:
+            small[name] = n * steps / (timed(e, x_dev, steps, warmup, True) / 1e3) / 1e6
+    fspec = synth.replace(synth.FULL_RATE, n=1 << 28)
+    xf = synth.make_stream_torch(fspec, dev)
+    for name, prec in precs.items():
+        with engine(prec, PLAN) as e:
+            full[name] = fspec.n * 2 / (timed(e, xf, 2, 1, False) / 1e3) / 1e6
+    del xf, flush
+    p = pcd.make_plan(F0, BW, FS, P["dm"], P["nfft"], P["nchan"], P["nbins"], P["period"], P["t_dec"])
+    r = pcd.run(p, xh, want_voltages=True)
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+    err = {}
+    for name, prec in precs.items():
+        with engine(prec, P, want_voltages=True) as e:
+            e.push(xh)
+            e.flush()
+            s_, h_, _ = e.profile()
+            T_, C_, _ = e.timeseries()
+            V_, _ = e.voltages()
+        err[name] = {"voltage": rel(V_, r.voltages), "profile": rel(s_, r.prof_sum), "series": rel(T_, r.ts),
+                     "hits_exact": bool(np.array_equal(h_, r.prof_hits)),
+                     "counts_exact": bool(np.array_equal(C_, r.ts_counts))}
+    return {"workload": "2^23 int8 samples, DM 3, P 0.253 s, nfft 2^21, 1 channel, 256-bin fold (L2 flushed "
+                        "before each step); full-rate geometry: 2^28 samples, nfft 2^24, 64 channels",
+            "msps": small, "speedup_vs_fp32": {k: small[k] / small["fp32"] for k in ("bf16x3", "bf16x5")},
+            "full_rate_geometry_msps": full,
+            "full_rate_speedup_vs_fp32": {k: full[k] / full["fp32"] for k in ("bf16x3", "bf16x5")},
+            "error_vs_oracle": err, "tolerance": {"voltage": 1e-5, "profile": 1e-4, "series": 1e-4}}
 
 
 INCOH_PLAN = {"nchan": 1024, "nint": 1, "dm": 26.8, "nbins": 1024, "period": 0.7145}
@@ -508,20 +742,11 @@ def run_precision(args, rank, ws, dist):
     eng = engine(pond.POND_SPLIT_BF16, timing=True)
     _, tst0, tst1 = timed(eng, x_dev, max(1, min(args.steps, 2)), 1, True)
     eng.close()
-    stages = {}
-    for name, d in tst1["stages"].items():
-        d0 = tst0["stages"].get(name, {"ms": 0.0, "launches": 0})
-        dl = d["launches"] - d0["launches"]
-        if dl > 0:
-            stages[name] = {"ms": d["ms"] - d0["ms"], "launches": dl, "algo_bytes": d["algo_bytes"]}
-    dom = max(stages, key=lambda k: stages[k]["ms"])
-    peaks = measured_peaks()
-    achieved = stages[dom]["algo_bytes"] / (stages[dom]["ms"] / stages[dom]["launches"] / 1e3) / 1e9
-    kname = KERNEL_OF_STAGE[dom]
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": kname + " (tensor-core form)",
-            "peak_src": peaks["src"],
-            "stage_ms_per_step_serialized": {k: v["ms"] / max(1, min(args.steps, 2)) for k, v in stages.items()}}
+    stages = stage_deltas(tst0, tst1)
+    roof = roofline(stages, max(1, min(args.steps, 2)), main["ms"] / args.steps, n, 1, main["st1"],
+                    fp32_peak(pond, torch, dev, stream), measured_peaks())
+    roof["kernel"] += " (tensor-core form)"
+    roof["traffic"] = None
 
     # full-rate geometry on a 2^28-sample slice (larger than L2)
     full = {}
@@ -646,6 +871,72 @@ def run_learned(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def stage_deltas(st0: dict, st1: dict) -> dict:
+    """Per-stage time, launches, pass bytes and algorithmic flops between two pond_stats."""
+    out = {}
+    for name, d in st1["stages"].items():
+        d0 = st0["stages"].get(name, {"ms": 0.0, "launches": 0})
+        dl = d["launches"] - d0["launches"]
+        if dl > 0:
+            out[name] = {"ms": d["ms"] - d0["ms"], "launches": dl, "pass_bytes": d["pass_bytes"],
+                         "algo_flops": d["algo_flops"]}
+    return out
+
+
+def algo_bytes_per_segment(st: dict, ch: int) -> float:
+    """The method's algorithmic DRAM bytes per segment: the int8 input of one
+    overlap-save segment read once (nfft bytes per channel of input, i.e. the
+    1 B/sample input re-read over the overlap) plus the outputs (detected,
+    folded and decimated power: 4 B per emitted channel sample, an upper bound)."""
+    return float(st["nfft"]) * ch + 4.0 * (st["seg_step"] // (2 * st["nchan"]))
+
+
+def roofline(stages: dict, t_steps: int, ms_step: float, n: int, ch: int, st: dict, fp32: dict,
+             peaks: dict) -> dict:
+    """Roofline of the dominant kernel (largest serialized time per step).
+
+    The path's algorithmic arithmetic intensity is about 110 flop per DRAM byte,
+    far above the GPU's balance (about 80 TFLOP/s / 6.8 TB/s = 12), so at its
+    algorithmic minimum it is bound by the FP32 pipes: `achieved` is the
+    kernel's algorithmic FP32 operations per launch over its mean CUDA-event
+    duration, `peak` the nominal FP32 ceiling (152 SMs x 128 lanes x 2 x
+    2.07 GHz) with the probe's measured ceiling beside it.  `algo_hbm_frac` is
+    the same launch's share of the method's algorithmic bytes (one segment's
+    input, one launch per segment) over its duration against measured HBM,
+    `pass_bytes_frac` the bytes the pass itself must move (its input and output
+    once) against measured HBM."""
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    d = stages[dom]
+    avg_s = d["ms"] / d["launches"] / 1e3
+    kname = KERNEL_OF_STAGE[dom]
+    achieved = d["algo_flops"] / avg_s / 1e12
+    seg_bytes = algo_bytes_per_segment(st, ch)
+    segs_per_step = n / st["seg_step"]
+    path_flops = sum(v["algo_flops"] * v["launches"] for v in stages.values()) / t_steps
+    path_tflops = path_flops / (ms_step / 1e3) / 1e12
+    path_gbs = seg_bytes * segs_per_step / (ms_step / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_NOMINAL_TFLOPS,
+            "peak_src": "nominal FP32 (152 SMs x 128 lanes x 2 flop x 2.07 GHz)",
+            "peak_measured": fp32["tflops"], "frac_of_measured": achieved / fp32["tflops"],
+            # the committed counters are of the single-channel launches
+            "traffic": traffic_from_profiles(kname) if ch == 1 else None,
+            "kernel": kname, "algo_flops_per_launch": d["algo_flops"], "launch_us": avg_s * 1e6,
+            "algo_hbm_gbs": seg_bytes / avg_s / 1e9, "algo_hbm_frac": seg_bytes / avg_s / 1e9 / peaks["hbm_gbs"],
+            "pass_bytes_gbs": d["pass_bytes"] / avg_s / 1e9,
+            "pass_bytes_frac": d["pass_bytes"] / avg_s / 1e9 / peaks["hbm_gbs"],
+            "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_src": peaks["src"],
+            "stage_ms_per_step_serialized": {k: v["ms"] / t_steps for k, v in stages.items()},
+            "path": {"algo_flops_per_sample": path_flops / n, "tflops": path_tflops,
+                     "alu_frac": path_tflops / FP32_NOMINAL_TFLOPS,
+                     "alu_frac_of_measured": path_tflops / fp32["tflops"],
+                     "algo_bytes_per_sample": seg_bytes / st["seg_step"], "algo_hbm_gbs": path_gbs,
+                     "algo_hbm_frac": path_gbs / peaks["hbm_gbs"],
+                     "pass_bytes_gbs": sum(v["pass_bytes"] * v["launches"] for v in stages.values()) / t_steps /
+                                       (ms_step / 1e3) / 1e9},
+            "fp32_probe": fp32}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -655,6 +946,8 @@ def main():
     ap.add_argument("--samples", type=int, default=0, help="override stream length (testing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cufft-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="full-rate: skip the precision-form and batched-trials sub-measurements")
     ap.add_argument("--workload", default="full-rate", choices=["full-rate", "batched", "learned", "precision", "aip", "incoherent"],
                     help="full-rate: the headline stream; batched: 128 DM trials on 8 s chunks; "
                          "learned: classifier training and evaluation beside the boxcar detector; "
@@ -751,25 +1044,9 @@ def main():
         step_device(eng_t)
     tst1 = eng_t.stats()
     eng_t.close()
-    stages = {}
-    for name, d in tst1["stages"].items():
-        d0 = tst0["stages"].get(name, {"ms": 0.0, "launches": 0})
-        dl = d["launches"] - d0["launches"]
-        if dl > 0:
-            stages[name] = {"ms": d["ms"] - d0["ms"], "launches": dl, "algo_bytes": d["algo_bytes"]}
-    dom = max(stages, key=lambda k: stages[k]["ms"])
-    peaks = measured_peaks()
-    avg_s = stages[dom]["ms"] / stages[dom]["launches"] / 1e3
-    achieved = stages[dom]["algo_bytes"] / avg_s / 1e9
-    kname = KERNEL_OF_STAGE[dom]
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"],
-            # the committed counters are of the single-channel launches
-            "traffic": traffic_from_profiles(kname) if ch == 1 else None,
-            "kernel": kname, "peak_src": peaks["src"],
-            "stage_ms_per_step_serialized": {k: v["ms"] / t_steps for k, v in stages.items()},
-            "path_effective_gbs": sum(v["algo_bytes"] * v["launches"] / t_steps for k, v in stages.items()
-                                      if k != "decimate") / (ms / args.steps / 1e3) / 1e9}
+    stages = stage_deltas(tst0, tst1)
+    fp32 = fp32_peak(pond, torch, dev, stream)
+    roof = roofline(stages, t_steps, ms / args.steps, n, ch, st1, fp32, measured_peaks())
 
     # the cuFFT comparison path on the same device-resident stream (one warm-up, one timed step)
     cufft = None
@@ -809,23 +1086,31 @@ def main():
     eng_h = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
                         t_dec=PLAN["t_dec"], device=local, precision=prec, input_channels=ch)
     prof = {}
+    phases = []
 
     def step_host():
+        a = time.perf_counter()
         eng_h.reset()
+        b = time.perf_counter()
         eng_h.push(xh)
+        c = time.perf_counter()
         eng_h.flush()
+        d = time.perf_counter()
         s, h, _ = eng_h.profile()
         T, C, _ = eng_h.timeseries()
+        e = time.perf_counter()
         prof["bytes"] = s.nbytes + h.nbytes + T.nbytes + C.nbytes
+        phases.append((b - a, c - b, d - c, e - d))
 
     for _ in range(max(1, args.warmup)):
         step_host()
     quiet_gc()
     barrier(dist)
     torch.cuda.synchronize()
+    phases.clear()
     # at least 20 steps (about 0.4 s): a single host-side stall of tens of ms (thread
     # scheduling, memory contention from other processes) stays in the figure but
-    # weighs less; the step spread below shows it
+    # weighs less; the step spread and the slowest step's phases below show it
     e2e_steps = max(args.steps, 20)
     t0 = time.perf_counter()
     marks = [t0]
@@ -834,18 +1119,49 @@ def main():
         marks.append(time.perf_counter())
     t1 = marks[-1]
     e2e_s = max_over_ranks(dist, t1 - t0)
-    step_ms = sorted(1e3 * (b - a) for a, b in zip(marks, marks[1:]))
+    steps_ms = [1e3 * (b - a) for a, b in zip(marks, marks[1:])]
+    step_ms = sorted(steps_ms)
+    slow = max(range(len(steps_ms)), key=lambda k: steps_ms[k])
     e2e = {"value": ws * n * e2e_steps / e2e_s / 1e6, "unit": UNIT, "steps": e2e_steps, "h2d_bytes_per_step": n * ch,
            "d2h_bytes_per_step": prof["bytes"], "h2d_copy_gbs": h2d_gbs,
            "copy_bound_below_gbs": n * ch / (ms / args.steps / 1e3) / 1e9,
-           "step_ms_min_median_max": [step_ms[0], statistics.median(step_ms), step_ms[-1]]}
+           "step_ms_min_median_max": [step_ms[0], statistics.median(step_ms), step_ms[-1]],
+           "slowest_step": {"index": slow, "ms": steps_ms[slow],
+                            "reset_push_flush_read_ms": [1e3 * v for v in phases[slow]]}}
 
+    # the FP64 oracle on the host cores: one thread, then every core (one process per core)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ch == 1:
-        v, nseg, samples, dt = oracle_rate(xh[:64 * (1 << 24)], seconds_budget=20.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nseg} whole nfft-2^24 segments ({samples} samples advanced) of the same stream, "
-                         f"{dt:.1f} s of FP64 numpy on 1 host thread"}
+        host = host_cpu()
+        v1, nseg1, samples1, dt1 = oracle_rate(xh[:16 * (1 << 24)], seconds_budget=10.0)
+        pool = OraclePool(xh[:8 * x_host_seg_step() + PLAN["nfft"]])
+        samples_all, wall_all, nseg_all = pool.round(2)
+        pool.close()
+        v_all = samples_all / wall_all / 1e6
+        cpu = {"value": v_all, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "host": host,
+               "sample": f"{nseg_all} whole nfft-2^24 segments ({samples_all} samples advanced) of the same stream "
+                         f"on {pool.workers} processes (two each), {wall_all:.1f} s wall, FP64 numpy",
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{nseg1} whole segments ({samples1} samples advanced), "
+                                           f"{dt1:.1f} s on 1 host thread"}}
+
+    # the precision form and the batched trials on the same GPU, one short run each
+    extra = {}
+    if rank == 0 and not args.no_forms and ch == 1 and prec == pond.POND_FP32:
+        eng.close()
+        eng_h.close()
+        eng = eng_h = None
+        torch.cuda.empty_cache()
+        extra["precision"] = precision_brief(dev, local, stream)
+        del x_dev
+        torch.cuda.empty_cache()
+        b = batched_core(dev, local, stream, steps=2, warmup=1)
+        bval = b["n"] * 2 / (b["ms"] / 1e3) / 1e6
+        extra["batched"] = {"workload": BATCHED_WORKLOAD, "value": bval, "unit": UNIT,
+                            "realtime_factor": bval / REALTIME_MSPS, "ms_per_step": b["ms"] / 2,
+                            "trial_samples_per_s": bval * 1e6 * 128, "nfft_groups": b["groups"],
+                            "plan_s_incl_autotune": b["plan_s"], "tuning": b["tuning"],
+                            "gpu_launches_per_step": b["launches_per_step"], "clocks": b["clocks"]}
     clocks = clk.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -856,9 +1172,12 @@ def main():
                 "realtime_factor": value / REALTIME_MSPS,
                 "e2e": e2e, "gpu_launches": int(st1["kernel_launches"]) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "cufft_baseline": cufft, "clocks": clocks}
+        line.update(extra)
         print(json.dumps(line), flush=True)
-    eng.close()
-    eng_h.close()
+    if eng is not None:
+        eng.close()
+    if eng_h is not None:
+        eng_h.close()
     if dist is not None:
         dist.destroy_process_group()
 

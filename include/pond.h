@@ -163,8 +163,17 @@ typedef struct {
   int32_t flushed;
   double stage_ms[POND_NSTAGE];   /* accumulated GPU time per stage */
   int64_t stage_launches[POND_NSTAGE];
-  double algo_bytes[POND_NSTAGE]; /* algorithmic DRAM bytes per launch of each stage */
+  double pass_bytes[POND_NSTAGE]; /* DRAM bytes one launch of each stage moves at its own
+                                     minimum (its input once and its output once); the
+                                     method's own minimum is the int8 input, 1 byte per
+                                     sample read, plus the small outputs */
   const char* stage_name[POND_NSTAGE];
+  double algo_flops[POND_NSTAGE]; /* algorithmic FP32 operations per launch of each stage:
+                                     5 n log2 n per length-n complex FFT factor, 10 per bin
+                                     for the real-input split, 6 per bin for the chirp
+                                     multiply (Eq. 4), 4 per detected channel sample
+                                     (|v|^2 and the sub-channel sum), 1 per sample for the
+                                     in-phase sum of two halves, fold and decimation */
 } pond_stats_t;
 
 /*
@@ -387,6 +396,20 @@ int pond_candidates_scored(pond_t h, pond_cnn_t net, double threshold, pond_cand
  *   POND_E_ARG or POND_E_CUDA otherwise.
  */
 int pond_check_bounded_wait(double limit_s, int32_t device, double* waited_s);
+
+/*
+ * pond_probe_fp32_fma: measure the FP32 arithmetic ceiling of the current
+ *   device.  The FFT butterflies of Sec. 3.7's forward and inverse transforms
+ *   are FP32 multiply-adds, so this is the roofline that bounds the path at
+ *   its algorithmic minimum of DRAM traffic.  Enqueues one kernel on
+ *   cuda_stream (NULL = legacy default stream): `blocks` CTAs of 512 threads,
+ *   each thread running 8 independent FMA chains for iters x 16 steps, and
+ *   writes one float per thread to d_out (DEVICE, blocks x 512 floats, caller
+ *   owned).  *flops (host) receives the FP32 operations enqueued (2 per FMA);
+ *   time the launch with events on cuda_stream.  Returns at once.
+ *   Errors: POND_E_ARG (null pointer, blocks or iters < 1), POND_E_CUDA.
+ */
+int pond_probe_fp32_fma(float* d_out, int32_t blocks, int32_t iters, void* cuda_stream, double* flops);
 
 /* pond_stats: counters and per-stage GPU times (waits for the device).  The
  * stage times give the paper's measure of real-time capability, the compute

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpond.so")
-SOURCES = ["kernels.cu", "kernels_tc.cu", "api.cu", "noalloc.cu", "boxcar.cu", "cnn.cu", "incoherent.cu", "stack.cu"]
+SOURCES = ["kernels.cu", "kernels_tc.cu", "api.cu", "noalloc.cu", "boxcar.cu", "cnn.cu", "incoherent.cu", "stack.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 

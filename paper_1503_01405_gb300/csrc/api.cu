@@ -1453,15 +1453,28 @@ int pond_stats(pond_t h, pond_stats_t* s) {
   s->flushed = h->flushed;
   const double spec = (double)g.L * sizeof(float2);
   const double nv = (double)g.S_c;
-  s->algo_bytes[ST_F1] = (double)g.N * h->ch + spec;  // int8 in (pairs for AIP input)
-  s->algo_bytes[ST_F2] = 2 * spec;
-  s->algo_bytes[ST_F2F] = 2 * spec;
-  s->algo_bytes[ST_IR] = 2 * spec;
-  s->algo_bytes[ST_I1] = 2 * spec;
-  s->algo_bytes[ST_I2] = spec + nv * sizeof(float);
-  s->algo_bytes[ST_IC] = spec + nv * sizeof(float);
-  s->algo_bytes[ST_FOLD] = nv * sizeof(float);
-  s->algo_bytes[ST_DEC] = nv * sizeof(float);
+  s->pass_bytes[ST_F1] = (double)g.N * h->ch + spec;  // int8 in (pairs for AIP input)
+  s->pass_bytes[ST_F2] = 2 * spec;
+  s->pass_bytes[ST_F2F] = 2 * spec;
+  s->pass_bytes[ST_IR] = 2 * spec;
+  s->pass_bytes[ST_I1] = 2 * spec;
+  s->pass_bytes[ST_I2] = spec + nv * sizeof(float);
+  s->pass_bytes[ST_IC] = spec + nv * sizeof(float);
+  s->pass_bytes[ST_FOLD] = nv * sizeof(float);
+  s->pass_bytes[ST_DEC] = nv * sizeof(float);
+  // algorithmic FP32 work: 5 n log2 n per length-n FFT factor over all L bins
+  const double L = (double)g.L;
+  const int logJ = g.logM - g.logR2;   // first inverse factor of the three-pass schedule
+  const double detect = 4.0 * g.nchan * nv;
+  s->algo_flops[ST_F1] = 5 * L * g.logR2 + (h->ch > 1 ? (double)g.N : 0.0);
+  s->algo_flops[ST_F2] = 5 * L * g.logR1 + 10 * L;
+  s->algo_flops[ST_F2F] = 5 * L * g.logR1 + 10 * L + 6 * L + 5 * L * logJ;
+  s->algo_flops[ST_IR] = 6 * L + 5 * L * logJ;
+  s->algo_flops[ST_I1] = 6 * L + 5 * L * g.logQ2;
+  s->algo_flops[ST_I2] = 5 * L * g.logQ1 + detect;
+  s->algo_flops[ST_IC] = 5 * L * g.logR2 + detect;
+  s->algo_flops[ST_FOLD] = nv;
+  s->algo_flops[ST_DEC] = nv;
   for (int i = 0; i < POND_NSTAGE; ++i) {
     s->stage_ms[i] = h->stage_ms[i];
     s->stage_launches[i] = h->stage_launches[i];

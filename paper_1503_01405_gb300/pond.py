@@ -48,7 +48,7 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches",
            "pond_incoh_create", "pond_incoh_run", "pond_incoh_info_get", "pond_incoh_filterbank",
            "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy", "pond_incoh_ips",
-           "pond_stack_rows", "pond_fold_stack"]
+           "pond_stack_rows", "pond_fold_stack", "pond_probe_fp32_fma"]
 
 
 class PondError(RuntimeError):
@@ -89,8 +89,9 @@ class pond_stats_t(ctypes.Structure):
                 ("nfft", ctypes.c_int32), ("nchan", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("flushed", ctypes.c_int32), ("stage_ms", ctypes.c_double * POND_NSTAGE),
                 ("stage_launches", ctypes.c_int64 * POND_NSTAGE),
-                ("algo_bytes", ctypes.c_double * POND_NSTAGE),
-                ("stage_name", ctypes.c_char_p * POND_NSTAGE)]
+                ("pass_bytes", ctypes.c_double * POND_NSTAGE),
+                ("stage_name", ctypes.c_char_p * POND_NSTAGE),
+                ("algo_flops", ctypes.c_double * POND_NSTAGE)]
 
 
 _lib = None
@@ -169,6 +170,7 @@ def lib() -> ctypes.CDLL:
                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, vp, ctypes.c_int64,
                             P(ctypes.c_int64), P(ctypes.c_int64), vp],
         "pond_incoh_destroy": [vp],
+        "pond_probe_fp32_fma": [vp, ctypes.c_int32, ctypes.c_int32, vp, P(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -194,6 +196,13 @@ def check_bounded_wait(limit_s: float = 0.05, device: int = 0) -> tuple[int, flo
     w = ctypes.c_double()
     rc = lib().pond_check_bounded_wait(limit_s, device, ctypes.byref(w))
     return rc, w.value
+
+
+def probe_fp32_fma(d_out_ptr: int, blocks: int, iters: int, stream: int = 0) -> float:
+    """Enqueue the FP32 FMA ceiling probe on `stream`; returns the FP32 operations enqueued."""
+    fl = ctypes.c_double()
+    _check(lib().pond_probe_fp32_fma(d_out_ptr, blocks, iters, stream, ctypes.byref(fl)))
+    return fl.value
 
 
 def boxcar(d_series_ptr: int, ndm: int, n: int, stride: int, threshold: float = 6.0, cap: int = 1 << 16,
@@ -352,13 +361,13 @@ class Engine:
         s = pond_stats_t()
         _check(lib().pond_stats(self._h, ctypes.byref(s)))
         d = {f: getattr(s, f) for f, _ in pond_stats_t._fields_ if f not in
-             ("stage_ms", "stage_launches", "algo_bytes", "stage_name")}
+             ("stage_ms", "stage_launches", "pass_bytes", "stage_name", "algo_flops")}
         d["stages"] = {}
         for i in range(POND_NSTAGE):
             name = s.stage_name[i]
             if name:
                 d["stages"][name.decode()] = {"ms": s.stage_ms[i], "launches": s.stage_launches[i],
-                                              "algo_bytes": s.algo_bytes[i]}
+                                              "pass_bytes": s.pass_bytes[i], "algo_flops": s.algo_flops[i]}
         return d
 
     def close(self) -> None:

@@ -24,7 +24,7 @@ def built():
 def _header_functions():
     src = open(os.path.join(ROOT, "include", "pond.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pond_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pond_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_function():

@@ -57,3 +57,32 @@ def test_workload_description_and_peaks():
     assert p["hbm_gbs"] > 1000 and p["src"] in ("measured", "fallback")
     if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
         assert p["src"] == "measured"
+
+
+def test_roofline_arithmetic():
+    """The roofline object: FP32 operations per launch over the mean launch time
+    against the nominal FP32 ceiling; the method's bytes (one segment's input
+    per launch) and the pass's own bytes against measured HBM."""
+    stages = {"fwd_cols_unpack": {"ms": 20.0, "launches": 100, "pass_bytes": 1e8, "algo_flops": 4e8},
+              "fwd_rows_chirp_inv": {"ms": 40.0, "launches": 100, "pass_bytes": 2e8, "algo_flops": 8e8},
+              "inv_cols_detect": {"ms": 10.0, "launches": 100, "pass_bytes": 1e8, "algo_flops": 5e8}}
+    st = {"nfft": 1 << 24, "nchan": 64, "seg_step": 13_501_440}
+    fp32 = {"tflops": 70.0}
+    peaks = {"hbm_gbs": 6800.0, "src": "measured"}
+    r = bench.roofline(stages, 2, 35.0, 100 * 13_501_440 // 2, 1, st, fp32, peaks)
+    assert r["kernel"] == "k_fwd_rows_inv" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["launch_us"] - 400.0) < 1e-9
+    assert abs(r["achieved"] - 8e8 / 400e-6 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / bench.FP32_NOMINAL_TFLOPS) < 1e-12
+    assert abs(r["frac_of_measured"] - r["achieved"] / 70.0) < 1e-12
+    seg = (1 << 24) + 4.0 * (13_501_440 // 128)
+    assert abs(r["algo_hbm_gbs"] - seg / 400e-6 / 1e9) < 1e-9
+    assert abs(r["pass_bytes_frac"] - 2e8 / 400e-6 / 1e9 / 6800.0) < 1e-12
+    # the path: 100 launches of each stage over 2 steps of 35 ms
+    assert abs(r["path"]["tflops"] - (17e8 * 100 / 2) / 35e-3 / 1e12) < 1e-9
+    assert abs(bench.FP32_NOMINAL_TFLOPS - 80.55) < 0.01
+
+
+def test_host_cpu_record():
+    h = bench.host_cpu()
+    assert h["nproc"] >= 1 and isinstance(h["model"], str) and h["model"]
