@@ -290,17 +290,22 @@ def quiet_gc():
         gc.freeze()
 
 
+def pass_sources_hash(root: str | None = None) -> str:
+    """Hash of the pass sources (the kernels the traffic counters describe)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh"):
+        with open(os.path.join(root or ROOT, "paper_1503_01405_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256()
-    for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh"):
-        with open(os.path.join(ROOT, "paper_1503_01405_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    src = h.hexdigest()[:16]
+    src = pass_sources_hash()
     rows = {}
     with open(path) as f:
         for line in f:

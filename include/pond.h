@@ -124,8 +124,27 @@ typedef struct {
                              x[m] = N[m] + S[m] (PONDER's AIP; -256..254): pushes then
                              take whole pairs (an even byte count, POND_E_ARG otherwise)
                              and stats count pairs */
-  int32_t reserved[5];
+  int32_t trial_mode;   /* batched plans: how the trials of a lane run their per-trial passes
+                           (POND_TRIALS_*); 0 = chosen by the autotuner when autotune is set,
+                           else the multi-trial table form where the lane's DMs allow it */
+  int32_t trials_per_launch; /* batched plans with a multi-trial mode: trials per launch
+                                (1 .. 128); 0 = chosen as for trial_mode (default 32) */
+  int32_t reserved[3];
 } pond_opts;
+
+/* Per-trial passes of a batched lane (one FFT length).  Every trial of the lane
+ * shares the lane's forward spectrum; its own passes are the chirp (Eq. 4) with
+ * the first inverse factor (row pass), the rest of the sub-channel inverse with
+ * detection (column pass) and the decimation. */
+#define POND_TRIALS_AUTO 0
+#define POND_TRIALS_PER_TRIAL 1    /* three launches per trial, chirp from the trial's anchors */
+#define POND_TRIALS_MULTI_ANCHOR 2 /* one launch of each pass over trials_per_launch trials,
+                                      chirp from each trial's anchors */
+#define POND_TRIALS_MULTI_TABLE 3  /* as POND_TRIALS_MULTI_ANCHOR, chirp from one per-bin
+                                      table: the lane's DMs are whole multiples n_d of a step
+                                      dDM (e.g. a uniform grid from 0), the table holds the
+                                      phase of dDM mod 1 in Q0.32 and trial d's phase is
+                                      n_d times it mod 2^32 (exact integer product) */
 
 /* Fold metadata returned with a profile snapshot. */
 typedef struct {
@@ -267,6 +286,30 @@ int pond_profile(pond_t h, double* sum, int64_t* hits, pond_meta* meta);
  *   entries; *ntrials receives the number of trials.
  */
 int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntrials);
+
+/*
+ * pond_tuning: how each lane of a batched plan runs its trials (the
+ *   autotuner's choices).  Lanes in increasing FFT length; out holds cap
+ *   entries and *nlanes receives the number of lanes.  With autotune, each
+ *   lane's candidates (per-trial launches, and the multi-trial forms with 8 or
+ *   32 trials per launch, anchors or table) were timed on the lane's own
+ *   buffers with CUDA events, and the fastest per trial is the one used; the
+ *   choice is cached per (nfft, nchan, device, trial count).  A single-DM plan
+ *   has one lane with mode POND_TRIALS_PER_TRIAL.
+ */
+#define POND_TUNE_MAXCAND 8
+typedef struct {
+  int64_t nfft;
+  int32_t ntrials;
+  int32_t mode;               /* POND_TRIALS_PER_TRIAL, _MULTI_ANCHOR or _MULTI_TABLE */
+  int32_t trials_per_launch;
+  int32_t ncand;              /* candidates timed (0 without autotune) */
+  double dm_step;             /* the table form's dDM (0 when the DMs allow no table) */
+  int32_t cand_mode[POND_TUNE_MAXCAND];
+  int32_t cand_kt[POND_TUNE_MAXCAND];
+  double cand_us[POND_TUNE_MAXCAND];   /* device time per trial and segment, us */
+} pond_lane_info;
+int pond_tuning(pond_t h, pond_lane_info* out, int32_t cap, int32_t* nlanes);
 
 /*
  * pond_timeseries: drain completed samples of the decimated time series

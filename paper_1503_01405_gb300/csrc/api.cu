@@ -132,6 +132,21 @@ struct Lane {
   int8_t* carry[2] = {nullptr, nullptr};
   int carry_cur = 0;
   long long seg_start = 0, carry_pos = 0, segments = 0;
+  // batched lanes with several trials per launch (POND_TRIALS_MULTI_*)
+  int mode = POND_TRIALS_PER_TRIAL;
+  int kt = 1;                               // trials per launch
+  float2* bufT[NSLOT] = {};                 // [kt][L] row-pass outputs
+  float* Pm[NSLOT] = {};                    // [kt][M] detected power
+  float* partm[NSLOT] = {};                 // [kt][G][M] column-pass group partials
+  int* cntm[NSLOT] = {};                    // [kt][FUSED_J] column-pass tickets
+  unsigned* atab = nullptr;                 // table form: Q0.32 phase of one DM step per bin (row layout)
+  unsigned* d_nmul = nullptr;               // per lane trial: its DM in DM steps
+  const ChirpAnchor** d_anc = nullptr;      // per lane trial: its anchor table
+  int* d_clog = nullptr;
+  int* d_rows = nullptr;                    // per lane trial: its series row (the caller's trial index)
+  double dm_step = 0;                       // table form's DM step (0: no table)
+  std::vector<int> cand_mode, cand_kt;      // autotuner candidates and their time per trial
+  std::vector<double> cand_us;
 };
 
 }  // namespace
@@ -245,6 +260,10 @@ int validate(const pond_opts* o) {
   }
   if (o->precision != POND_FP32 && o->precision != POND_SPLIT_BF16 && o->precision != POND_SPLIT_BF16_5T)
     return fail(POND_E_ARG, "precision must be POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T");
+  if (o->trial_mode < POND_TRIALS_AUTO || o->trial_mode > POND_TRIALS_MULTI_TABLE)
+    return fail(POND_E_ARG, "trial_mode %d is not a POND_TRIALS_* value", o->trial_mode);
+  if (o->trials_per_launch < 0 || o->trials_per_launch > 128)
+    return fail(POND_E_ARG, "trials_per_launch must be in 0 .. 128");
   if (o->schedule != POND_SCHEDULE_AUTO && o->schedule != POND_SCHEDULE_FOUR_PASS)
     return fail(POND_E_ARG, "schedule must be POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS");
   if (o->input_channels < 0 || o->input_channels > 2)
@@ -378,9 +397,18 @@ void free_lane(Lane* ln) {
     cudaFree(ln->P[k]);
     cudaFree(ln->part[k]);
     cudaFree(ln->cnt[k]);
+    cudaFree(ln->bufT[k]);
+    cudaFree(ln->Pm[k]);
+    cudaFree(ln->partm[k]);
+    cudaFree(ln->cntm[k]);
     for (auto e : ln->ev_chain[k]) cudaEventDestroy(e);
     ln->ev_chain[k].clear();
   }
+  cudaFree(ln->atab);
+  cudaFree(ln->d_nmul);
+  cudaFree(ln->d_anc);
+  cudaFree(ln->d_clog);
+  cudaFree(ln->d_rows);
   cudaFree(ln->stw);
   cudaFree(ln->tw2buf);
   cudaFree(ln->carry[0]);
@@ -597,39 +625,73 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
     RC(record(h, 1 + ST_F2, cs));
     h->launches += 2;
-    for (size_t q = 0; q < ln.trials.size(); ++q) {
-      const int d = ln.trials[q];
-      const Trial& t = h->trials[d];
-      if (ln.fused_multi) {
-        // the trial's chirp and the first inverse factor as Ir loads the shared spectrum's rows
-        CK(launch_inv_rows_chirp(g, bufB, bufA, ln.tw3L, ln.stwJ, t.anc, t.clog, cs));
-        if (q == 0) RC(record(h, 1 + ST_IR, cs));
-        CK(launch_inv_cols_det(g, bufA, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
-                               (int)m_hi, ln.stwR2, cs));
-        if (q == 0) RC(record(h, 1 + ST_IC, cs));
-      } else {
-        // every trial's chirp is applied as I1 loads the shared forward spectrum
-        CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
-        if (q == 0) RC(record(h, 1 + ST_I1, cs));
-        CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
-        if (q == 0) RC(record(h, 1 + ST_I2, cs));
+    if (ln.mode != POND_TRIALS_PER_TRIAL) {
+      // kt trials per launch: the row pass with each trial's chirp, the column
+      // pass with detection, then the decimation of every trial's series row
+      const int ntr = (int)ln.trials.size();
+      for (int b = 0, q0 = 0; q0 < ntr; ++b, q0 += ln.kt) {
+        const int nq = std::min(ln.kt, ntr - q0);
+        const MultiChirp mc{ln.atab, ln.d_nmul + q0, ln.d_anc + q0, ln.d_clog + q0};
+        CK(launch_inv_rows_chirp_multi(g, bufB, ln.bufT[slot], nq, ln.tw3L, ln.stwJ, mc,
+                                       ln.mode == POND_TRIALS_MULTI_TABLE, cs));
+        if (b == 0) RC(record(h, 1 + ST_IR, cs));
+        CK(launch_inv_cols_det(g, ln.bufT[slot], ln.Pm[slot], ln.partm[slot], ln.cntm[slot], nullptr, 0, 0,
+                               (int)m_lo, (int)m_hi, ln.stwR2, cs, nq));
+        if (b == 0) RC(record(h, 1 + ST_IC, cs));
+        // the block's series rows are updated in segment order
+        CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][b], 0));
+        if (h->dec_num < 64 * h->dec_den) {
+          CK(launch_decimate_multi(ln.Pm[slot], g.M, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts,
+                                   h->ts_cnt, h->ring, ln.d_rows + q0, nq, cs));
+          h->launches += 1;
+        } else {
+          for (int q = 0; q < nq; ++q) {
+            const int d = ln.trials[q0 + q];
+            CK(launch_decimate(ln.Pm[slot] + (size_t)q * g.M, nv, g0, h->dec_num, h->dec_den, j_lo,
+                               j_hi - j_lo + 1, h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring,
+                               h->ring, cs));
+          }
+          h->launches += nq;
+        }
+        if (b == 0) RC(record(h, 1 + ST_DEC, cs, true));
+        CK(cudaEventRecord(ln.ev_chain[slot][b], cs));
+        h->launches += 2;
       }
-      // each trial's series row (and the fold partials) is updated in segment order
-      CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
-      if (!h->multi) {
-        // fold and decimation in one launch; the profile is merged when read
-        CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
-                           h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum,
-                           h->phits, cs));
-        RC(record(h, 1 + ST_FOLD, cs));
-        RC(record(h, 1 + ST_DEC, cs, true));
-      } else {
-        CK(launch_decimate(P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
-                           h->ts_cnt + (size_t)d * h->ring, h->ring, cs));
-        if (q == 0) RC(record(h, 1 + ST_DEC, cs, true));
+    } else {
+      for (size_t q = 0; q < ln.trials.size(); ++q) {
+        const int d = ln.trials[q];
+        const Trial& t = h->trials[d];
+        if (ln.fused_multi) {
+          // the trial's chirp and the first inverse factor as Ir loads the shared spectrum's rows
+          CK(launch_inv_rows_chirp(g, bufB, bufA, ln.tw3L, ln.stwJ, t.anc, t.clog, cs));
+          if (q == 0) RC(record(h, 1 + ST_IR, cs));
+          CK(launch_inv_cols_det(g, bufA, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
+                                 (int)m_hi, ln.stwR2, cs));
+          if (q == 0) RC(record(h, 1 + ST_IC, cs));
+        } else {
+          // every trial's chirp is applied as I1 loads the shared forward spectrum
+          CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
+          if (q == 0) RC(record(h, 1 + ST_I1, cs));
+          CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
+          if (q == 0) RC(record(h, 1 + ST_I2, cs));
+        }
+        // each trial's series row (and the fold partials) is updated in segment order
+        CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
+        if (!h->multi) {
+          // fold and decimation in one launch; the profile is merged when read
+          CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                             h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum,
+                             h->phits, cs));
+          RC(record(h, 1 + ST_FOLD, cs));
+          RC(record(h, 1 + ST_DEC, cs, true));
+        } else {
+          CK(launch_decimate(P, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts + (size_t)d * h->ring,
+                             h->ts_cnt + (size_t)d * h->ring, h->ring, cs));
+          if (q == 0) RC(record(h, 1 + ST_DEC, cs, true));
+        }
+        CK(cudaEventRecord(ln.ev_chain[slot][q], cs));
+        h->launches += 3;
       }
-      CK(cudaEventRecord(ln.ev_chain[slot][q], cs));
-      h->launches += 3;
     }
   }
   if (h->want_voltages) h->v_len += nv;
@@ -894,6 +956,221 @@ int choose_groups(pond_t h, const pond_opts* o, const std::vector<double>& dms, 
   return POND_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Trials of a batched lane: per-trial launches, or kt trials per launch with
+// the chirp from each trial's anchors or from one per-bin table
+// ---------------------------------------------------------------------------
+
+// The lane's DMs as whole multiples n_d of one step dDM (the table form): the
+// step is the smallest positive gap between the sorted DMs (0 included), refined
+// by least squares over the n_d; every DM must lie within 1e-13 of the largest
+// DM from n_d dDM, so that the table's phase differs from Eq. 4's at the
+// trial's own DM by under 1e-7 cycles across the band.
+bool dm_steps(const std::vector<double>& dms, double* step, std::vector<unsigned>* n) {
+  std::vector<double> v(dms);
+  std::sort(v.begin(), v.end());
+  const double dmax = v.back();
+  if (!(dmax > 0) || v.front() < 0) return false;
+  double gap = 0, prev = 0;
+  for (double x : v) {
+    const double d = x - prev;
+    if (d > 1e-9 * dmax && (gap == 0 || d < gap)) gap = d;
+    prev = x;
+  }
+  if (!(gap > 0)) return false;
+  n->resize(dms.size());
+  double sxn = 0, snn = 0;
+  for (size_t i = 0; i < dms.size(); ++i) {
+    const double q = std::nearbyint(dms[i] / gap);
+    if (q < 0 || q > (double)(1 << 24)) return false;
+    (*n)[i] = (unsigned)q;
+    sxn += q * dms[i];
+    snn += q * q;
+  }
+  const double st = sxn / snn;
+  for (size_t i = 0; i < dms.size(); ++i)
+    if (std::fabs(dms[i] - (*n)[i] * st) > 1e-13 * dmax) return false;
+  *step = st;
+  return true;
+}
+
+int alloc_multi(Lane* ln, int kt) {
+  const Geom& g = ln->g;
+  const int G = fused_groups(g);
+  for (int k = 0; k < NSLOT; ++k) {
+    cudaFree(ln->bufT[k]);
+    cudaFree(ln->Pm[k]);
+    cudaFree(ln->partm[k]);
+    cudaFree(ln->cntm[k]);
+    ln->bufT[k] = nullptr;
+    ln->Pm[k] = ln->partm[k] = nullptr;
+    ln->cntm[k] = nullptr;
+  }
+  for (int k = 0; k < NSLOT; ++k) {
+    CK(cudaMalloc(&ln->bufT[k], (size_t)kt * g.L * sizeof(float2)));
+    CK(cudaMalloc(&ln->Pm[k], (size_t)kt * g.M * sizeof(float)));
+    if (G > 1) CK(cudaMalloc(&ln->partm[k], (size_t)kt * G * g.M * sizeof(float)));
+    CK(cudaMalloc(&ln->cntm[k], (size_t)kt * FUSED_J * sizeof(int)));
+    CK(cudaMemset(ln->cntm[k], 0, (size_t)kt * FUSED_J * sizeof(int)));
+  }
+  ln->kt = kt;
+  return POND_OK;
+}
+
+// Device time per trial (us) of one block of min(kt, ntrials) trials of the
+// lane in the given mode (row pass, column pass, decimation), on slot 0, by
+// CUDA events over three launches after a warm-up.  The series rows it adds to
+// are cleared by the caller afterwards.
+int time_trials(pond_t h, Lane* ln, int mode, int kt, double* us) {
+  const Geom& g = ln->g;
+  const int nq = std::min(kt, (int)ln->trials.size());
+  const long long m_lo = g.n_past, m_hi = g.M - g.n_fut, g0 = m_lo, nv = m_hi - m_lo;
+  const long long j_lo = (g0 * h->dec_den) / h->dec_num, j_hi = ((g0 + nv - 1) * h->dec_den) / h->dec_num;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  const int reps = 3;
+  for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
+    if (it == 1) ce = cudaEventRecord(e0, h->st);
+    if (mode == POND_TRIALS_PER_TRIAL) {
+      for (int q = 0; q < nq && ce == cudaSuccess; ++q) {
+        const Trial& t = h->trials[ln->trials[q]];
+        ce = launch_inv_rows_chirp(g, ln->bufB[0], ln->bufA[0], ln->tw3L, ln->stwJ, t.anc, t.clog, h->st);
+        if (ce == cudaSuccess)
+          ce = launch_inv_cols_det(g, ln->bufA[0], ln->P[0], ln->part[0], ln->cnt[0], nullptr, 0, 0, (int)m_lo,
+                                   (int)m_hi, ln->stwR2, h->st);
+        if (ce == cudaSuccess)
+          ce = launch_decimate(ln->P[0], nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                               h->ts + (size_t)ln->trials[q] * h->ring, h->ts_cnt + (size_t)ln->trials[q] * h->ring,
+                               h->ring, h->st);
+      }
+    } else {
+      const MultiChirp mc{ln->atab, ln->d_nmul, ln->d_anc, ln->d_clog};
+      ce = launch_inv_rows_chirp_multi(g, ln->bufB[0], ln->bufT[0], nq, ln->tw3L, ln->stwJ, mc,
+                                       mode == POND_TRIALS_MULTI_TABLE, h->st);
+      if (ce == cudaSuccess)
+        ce = launch_inv_cols_det(g, ln->bufT[0], ln->Pm[0], ln->partm[0], ln->cntm[0], nullptr, 0, 0, (int)m_lo,
+                                 (int)m_hi, ln->stwR2, h->st, nq);
+      if (ce == cudaSuccess && h->dec_num < 64 * h->dec_den)
+        ce = launch_decimate_multi(ln->Pm[0], g.M, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts,
+                                   h->ts_cnt, h->ring, ln->d_rows, nq, h->st);
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaEventRecord(e1, h->st);
+  float ms = 0;
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return fail(POND_E_CUDA, "trial autotune: %s", cudaGetErrorString(ce));
+  *us = 1e3 * ms / reps / nq;
+  return POND_OK;
+}
+
+std::map<std::tuple<long long, int, int, int, bool, int, int>, std::tuple<int, int, std::vector<int>, std::vector<int>,
+                                                                        std::vector<double>>>
+    g_trial_tune;
+
+// Choose how the lane runs its trials (after its trials' anchors exist and the
+// series rings are allocated; the rings are cleared afterwards by the caller).
+int setup_trials(pond_t h, const pond_opts* o, Lane* ln) {
+  const Geom& g = ln->g;
+  const int ntr = (int)ln->trials.size();
+  ln->mode = POND_TRIALS_PER_TRIAL;
+  ln->kt = 1;
+  const int req = o->trial_mode;
+  // several trials per launch need the three-pass lane geometry and two or more trials
+  if (!h->multi || !ln->fused_multi || ntr < 2 || req == POND_TRIALS_PER_TRIAL)
+    return POND_OK;
+  std::vector<int> rows(ntr), clogs(ntr);
+  std::vector<const ChirpAnchor*> ancs(ntr);
+  std::vector<double> dms(ntr);
+  for (int q = 0; q < ntr; ++q) {
+    const Trial& t = h->trials[ln->trials[q]];
+    rows[q] = ln->trials[q];
+    ancs[q] = t.anc;
+    clogs[q] = t.clog;
+    dms[q] = t.dm;
+  }
+  CK(cudaMalloc(&ln->d_rows, ntr * sizeof(int)));
+  CK(cudaMalloc(&ln->d_clog, ntr * sizeof(int)));
+  CK(cudaMalloc(&ln->d_anc, ntr * sizeof(ChirpAnchor*)));
+  CK(cudaMemcpy(ln->d_rows, rows.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ln->d_clog, clogs.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ln->d_anc, ancs.data(), ntr * sizeof(ChirpAnchor*), cudaMemcpyHostToDevice));
+  double step = 0;
+  std::vector<unsigned> nm;
+  if (dm_steps(dms, &step, &nm)) {
+    ln->dm_step = step;
+    CK(cudaMalloc(&ln->d_nmul, ntr * sizeof(unsigned)));
+    CK(cudaMemcpy(ln->d_nmul, nm.data(), ntr * sizeof(unsigned), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ln->atab, (size_t)g.L * sizeof(unsigned)));
+    const double alpha = K_DM * 1e6 * step / (o->f0_mhz * o->f0_mhz);
+    CK(launch_chirp_table(ln->atab, g, o->fs_hz / (double)g.N * 1e-6, std::fabs(o->bw_mhz) / 2.0, o->f0_mhz, alpha,
+                          h->sgn, h->st));
+  }
+  const int best_multi = ln->dm_step > 0 ? POND_TRIALS_MULTI_TABLE : POND_TRIALS_MULTI_ANCHOR;
+  const int kt_req = o->trials_per_launch ? std::min(o->trials_per_launch, ntr) : 0;
+  if (req != POND_TRIALS_AUTO || !o->autotune) {
+    // the requested form (the table form only where the DMs allow it), else the table form where possible
+    ln->mode = (req == POND_TRIALS_MULTI_ANCHOR) ? POND_TRIALS_MULTI_ANCHOR : best_multi;
+    return alloc_multi(ln, kt_req ? kt_req : std::min(32, ntr));
+  }
+  // autotune: time every candidate on this lane, keep the fastest per trial
+  std::vector<std::pair<int, int>> cands{{POND_TRIALS_PER_TRIAL, 1}};
+  std::vector<int> kts;
+  if (kt_req) kts.push_back(kt_req);
+  else kts = {std::min(8, ntr), std::min(32, ntr)};
+  kts.erase(std::unique(kts.begin(), kts.end()), kts.end());
+  for (int kt : kts) {
+    cands.push_back({POND_TRIALS_MULTI_ANCHOR, kt});
+    if (ln->dm_step > 0) cands.push_back({POND_TRIALS_MULTI_TABLE, kt});
+  }
+  const auto key = std::make_tuple(g.N, g.nchan, o->device, ntr, ln->dm_step > 0, kt_req, (int)(h->dec_num / h->dec_den));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_trial_tune.find(key);
+    if (it != g_trial_tune.end()) {
+      ln->mode = std::get<0>(it->second);
+      ln->cand_mode = std::get<2>(it->second);
+      ln->cand_kt = std::get<3>(it->second);
+      ln->cand_us = std::get<4>(it->second);
+      return ln->mode == POND_TRIALS_PER_TRIAL ? POND_OK : alloc_multi(ln, std::get<1>(it->second));
+    }
+  }
+  RC(alloc_multi(ln, *std::max_element(kts.begin(), kts.end())));
+  CK(cudaMemsetAsync(ln->bufB[0], 0, (size_t)g.L * sizeof(float2), h->st));
+  size_t best = 0;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    double us = 0;
+    RC(time_trials(h, ln, cands[c].first, cands[c].second, &us));
+    ln->cand_mode.push_back(cands[c].first);
+    ln->cand_kt.push_back(cands[c].second);
+    ln->cand_us.push_back(us);
+    if (us < ln->cand_us[best]) best = c;
+  }
+  ln->mode = cands[best].first;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_trial_tune[key] = std::make_tuple(ln->mode, cands[best].second, ln->cand_mode, ln->cand_kt, ln->cand_us);
+  }
+  if (ln->mode == POND_TRIALS_PER_TRIAL) {
+    for (int k = 0; k < NSLOT; ++k) {
+      cudaFree(ln->bufT[k]);
+      cudaFree(ln->Pm[k]);
+      cudaFree(ln->partm[k]);
+      cudaFree(ln->cntm[k]);
+      ln->bufT[k] = nullptr;
+      ln->Pm[k] = ln->partm[k] = nullptr;
+      ln->cntm[k] = nullptr;
+    }
+    ln->kt = 1;
+    return POND_OK;
+  }
+  if (cands[best].second != ln->kt) RC(alloc_multi(ln, cands[best].second));
+  return POND_OK;
+}
+
 int plan_impl(pond_t* out, const pond_opts* o) {
   RC(validate(o));
   // trials (caller's order) and their DMs
@@ -1051,6 +1328,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   CKD(cudaMemsetAsync(h->ts, 0, (size_t)ntr * h->ring * sizeof(float), h->st));
   CKD(cudaMemsetAsync(h->ts_cnt, 0, (size_t)ntr * h->ring * sizeof(int), h->st));
   h->ts_host.assign(ntr, {});
+  for (auto& ln : h->lanes) RCD(setup_trials(h, o, &ln));
+  if (multi) {   // the trial autotuner's launches added to the series rings
+    CKD(cudaMemsetAsync(h->ts, 0, (size_t)ntr * h->ring * sizeof(float), h->st));
+    CKD(cudaMemsetAsync(h->ts_cnt, 0, (size_t)ntr * h->ring * sizeof(int), h->st));
+  }
   if (!multi) {
     CKD(cudaMalloc(&h->prof_sum, h->nbins * sizeof(double)));
     CKD(cudaMalloc(&h->prof_hits, h->nbins * sizeof(long long)));
@@ -1327,6 +1609,28 @@ int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntria
 
 // Boxcar candidates over the undrained series block; with net, each is scored
 // by the classifier on its patch of the same block.
+int pond_tuning(pond_t h, pond_lane_info* out, int32_t cap, int32_t* nlanes) {
+  if (!h || !nlanes || (cap > 0 && !out)) return fail(POND_E_ARG, "null argument");
+  *nlanes = (int32_t)h->lanes.size();
+  for (int i = 0; i < cap && i < (int)h->lanes.size(); ++i) {
+    const Lane& ln = h->lanes[i];
+    pond_lane_info& r = out[i];
+    memset(&r, 0, sizeof r);
+    r.nfft = ln.g.N;
+    r.ntrials = (int32_t)ln.trials.size();
+    r.mode = ln.mode;
+    r.trials_per_launch = ln.kt;
+    r.dm_step = ln.dm_step;
+    r.ncand = (int32_t)std::min<size_t>(ln.cand_us.size(), POND_TUNE_MAXCAND);
+    for (int c = 0; c < r.ncand; ++c) {
+      r.cand_mode[c] = ln.cand_mode[c];
+      r.cand_kt[c] = ln.cand_kt[c];
+      r.cand_us[c] = ln.cand_us[c];
+    }
+  }
+  return POND_OK;
+}
+
 static int candidates_impl(pond_t h, pond_cnn_t net, double threshold, pond_cand* out, size_t cap,
                            size_t* n_found) {
   if (!h || !n_found || (cap > 0 && !out)) return fail(POND_E_ARG, "null argument");

@@ -447,9 +447,64 @@ __global__ void k_decimate_short(const float* __restrict__ P, long long n, long 
   C[slot] += (int)max(gb - ga, 0ll);
 }
 
+// k_decimate_short for the trials of one batched launch: blockIdx.y = trial t,
+// reading P + t pstride and adding to series row rows[t].
+__global__ void k_decimate_short_multi(const float* __restrict__ P, long long pstride, long long n, long long g0,
+                                       long long num, long long den, long long j_lo, long long nj,
+                                       float* __restrict__ T, int* __restrict__ C, long long ring,
+                                       const int* __restrict__ rows) {
+  const long long jj = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (jj >= nj) return;
+  const int row = __ldg(rows + blockIdx.y);
+  P += blockIdx.y * pstride;
+  const long long j = j_lo + jj;
+  long long ga = ceil_div_ll(j * num, den), gb = ceil_div_ll((j + 1) * num, den);
+  ga = max(ga, g0);
+  gb = min(gb, g0 + n);
+  float s = 0.f;
+  for (long long g = ga; g < gb; ++g) s += __ldg(P + (g - g0));
+  const long long slot = (size_t)row * ring + j % ring;
+  T[slot] += s;
+  C[slot] += (int)max(gb - ga, 0ll);
+}
+
+// Chirp table of a batched lane whose DMs are whole multiples of dDM: entry
+// k2 R1 + k1 (the spectrum's row layout, bin k = k2 + R2 k1) holds the phase of
+// Eq. 4's inverse at bin k for one DM step, sgn dDM c(f_k) mod 1, as a Q0.32
+// word (FP64, the same formula as the anchors' phase term).
+__global__ void k_make_chirp_table(unsigned* tab, int logR1, int logR2, double du, double half, double f0,
+                                   double alpha, int sgn) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (1ll << (logR1 + logR2))) return;
+  const long long k2 = i >> logR1, k1 = i & ((1ll << logR1) - 1);
+  const double k = (double)(k2 + (k1 << logR2));
+  const double f = sgn > 0 ? __dsub_rn(__dmul_rn(k, du), half) : __dsub_rn(half, __dmul_rn(k, du));
+  const double g = f0 + f;
+  const double phi = sgn * (alpha * f * f / g);
+  const double fr = phi - floor(phi);
+  tab[i] = (unsigned)((unsigned long long)llrint(fr * 4294967296.0) & 0xffffffffull);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_chirp_table(unsigned* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
+                               cudaStream_t st) {
+  const long long n = g.L;
+  k_make_chirp_table<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tab, g.logR1, g.logR2, du, half, f0, alpha, sgn);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decimate_multi(const float* P, long long pstride, long long n, long long g0, long long num,
+                                  long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
+                                  const int* rows, int ntr, cudaStream_t st) {
+  if (n <= 0 || nj <= 0) return cudaSuccess;
+  if (num >= 64 * den) return cudaErrorInvalidValue;   // short spans only (batched plans decimate by a few)
+  const dim3 grid((unsigned)((nj + 255) / 256), (unsigned)ntr);
+  k_decimate_short_multi<<<grid, 256, 0, st>>>(P, pstride, n, g0, num, den, j_lo, nj, T, C, ring, rows);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_stage_tw(float2* out, int R, cudaStream_t st) {
   const int n = stage_table_size(R);
@@ -532,6 +587,30 @@ cudaError_t launch_inv_rows_chirp(const Geom& g, const float2* in, float2* out, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_inv_rows_chirp_multi(const Geom& g, const float2* in, float2* out, int ntr, const float2* tw3L,
+                                        const float2* twJ, MultiChirp mc, bool table, cudaStream_t st) {
+  const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
+  const int nl = std::min(TILE / R1, R2);
+  if (ntr < 1) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ntr, (unsigned)(R2 / nl));
+  switch (R1) {
+#define CASE(R)                                                                                             \
+  case R:                                                                                                   \
+    if (table)                                                                                              \
+      k_inv_rows_chirp_multi<R, FUSED_J, true><<<grid, NT, smem_inv_rows_chirp(R, nl), st>>>(in, out, g.L, \
+                                                                                              g.logR2, tw3L, \
+                                                                                              twJ, mc);     \
+    else                                                                                                    \
+      k_inv_rows_chirp_multi<R, FUSED_J, false><<<grid, NT, smem_inv_rows_chirp(R, nl), st>>>(             \
+          in, out, g.L, g.logR2, tw3L, twJ, mc);                                                            \
+    break;
+    POND_FUSED_R1(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 int fused_groups(const Geom& g) {
   const int nl = std::min(TILE >> g.logR2, g.nchan);
   return g.nchan / nl;
@@ -539,14 +618,17 @@ int fused_groups(const Geom& g) {
 
 cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
                                 long long vstride, long long vofs, int m_lo, int m_hi, const float2* tw,
-                                cudaStream_t st) {
+                                cudaStream_t st, int ntr) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R2, g.nchan);
-  const unsigned grid = (unsigned)(R1 / nl);
+  const dim3 grid((unsigned)(R1 / nl), (unsigned)ntr);
   const float scale = 1.0f / (float)(1u << g.logM);
   const int lognch = g.logR1 - (g.logM - g.logR2);
+  // several trials: each has its own L-element input, M-element P, partials and tickets
+  const TrialStride ts = ntr > 1 ? TrialStride{g.L, g.M, (long long)fused_groups(g) * g.M, FUSED_J}
+                                 : TrialStride{0, 0, 0, 0};
   switch (R2) {
-#define CASE(R) case R: k_inv_cols_det<R><<<grid, NT, smem_inv_cols_det<R>(nl), st>>>(in, P, part, cnt, vout, vstride, vofs, g.logR1, lognch, g.logM - g.logR2, m_lo, m_hi, scale, tw); break;
+#define CASE(R) case R: k_inv_cols_det<R><<<grid, NT, smem_inv_cols_det<R>(nl), st>>>(in, P, part, cnt, vout, vstride, vofs, g.logR1, lognch, g.logM - g.logR2, m_lo, m_hi, scale, tw, ts); break;
     POND_FUSED_R2(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -564,6 +646,15 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows_chirp<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_rows_chirp(R, TILE / R));
   POND_FUSED_R1(SET_I)
 #undef SET_I
+#define SET_M(R)                                                                                       \
+  if (e == cudaSuccess)                                                                                \
+    e = cudaFuncSetAttribute(k_inv_rows_chirp_multi<R, FUSED_J, true>,                                 \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_rows_chirp(R, TILE / R)); \
+  if (e == cudaSuccess)                                                                                \
+    e = cudaFuncSetAttribute(k_inv_rows_chirp_multi<R, FUSED_J, false>,                                \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_rows_chirp(R, TILE / R));
+  POND_FUSED_R1(SET_M)
+#undef SET_M
 #define SET_C(R) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols_det<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_inv_cols_det<R>(TILE / R));
   POND_FUSED_R2(SET_C)

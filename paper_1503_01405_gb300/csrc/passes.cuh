@@ -102,6 +102,13 @@ struct Lin {
   }
 };
 
+// Per-trial strides (elements) of a column pass launched over several trials
+// (blockIdx.y = trial); all zero for a single trial.
+struct TrialStride {
+  long long in, P, part;
+  int cnt;
+};
+
 // Three-level table of w^e, e < 2^24, held in shared memory by F2 and I2:
 // w^e = t0[e0] t1[e1] t2[e2], e = e0 + 2^8 e1 + 2^16 e2 (each level built in
 // FP64 on the device; two FP32 products).  In shared memory level 0 is padded
@@ -689,6 +696,91 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows_chirp(const float2* __restri
   j_runs<R1, J>(sm, stwj, twk, out, nl, logR2, [&](int slot) { return r0 + slot; });
 }
 
+// exp(-2 pi i r) for the phase r = u 2^-32 (mod 1) held as a Q0.32 word u: the
+// same final sine and cosine as chirp_from.
+__device__ __forceinline__ float2 chirp_q32(unsigned u) {
+  const float r = (float)(int)u * 2.3283064365386963e-10f;   // 2^-32
+  float s, c;
+  __sincosf(6.2831853071795865f * r, &s, &c);
+  return make_float2(c, -s);
+}
+
+// IrK: Ir for the ntr trials of one batched launch, one trial per CTA.
+// blockIdx.y is the row tile (nl rows of the shared spectrum) and blockIdx.x
+// the trial, so the CTAs that read the same rows (and, in the table form, the
+// same table words, stored in the spectrum's row layout) are adjacent in
+// launch order and find them in L2 after the first.  Trial t's output (the
+// blocked layout of F2f) goes to out + t out_tstride.
+template <int R1, int J, bool TABLE>
+__global__ void __launch_bounds__(NT, 2) k_inv_rows_chirp_multi(const float2* __restrict__ in,
+                                                                float2* __restrict__ out, long long out_tstride,
+                                                                int logR2, const float2* __restrict__ tw3L,
+                                                                const float2* __restrict__ twJ, MultiChirp mc) {
+  static_assert(J == 64 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
+  constexpr int NCH = R1 / J;
+  constexpr int LSTR = R1 + R1 / 16;
+  constexpr int LOGJ = ilog2c(J), LOGNCH = ilog2c(NCH), LOGR1 = ilog2c(R1);
+  extern __shared__ float2 smem[];
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stwj = st3 + TW3_SN;
+  float2* twk = stwj + stage_table_size(J);        // [nl][J]: e^{2 pi i k2 m1 / M}
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);
+  float2* sm = twk + nl * J;
+  const int t = blockIdx.x;
+  const int r0 = blockIdx.y * nl;
+  const int tot = nl * R1;
+  load_tw3(st3, tw3L);
+  load_twiddles<J>(stwj, twJ);
+  // rows r0 .. r0 + nl - 1 are contiguous: 16-byte loads of columns k1, k1 + 1
+  // (and, in the table form, 8-byte loads of their table words)
+  const float4* in4 = reinterpret_cast<const float4*>(in) + ((size_t)r0 << (LOGR1 - 1));
+  const uint2* a2 = reinterpret_cast<const uint2*>(mc.atab) + ((size_t)r0 << (LOGR1 - 1));
+  constexpr int H = EPT / 2;
+  float4 r[H];
+#pragma unroll
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * ((int)threadIdx.x + u * NT);
+    if (idx < tot) r[u] = __ldg(in4 + (idx >> 1));
+  }
+  if constexpr (TABLE) {
+    const unsigned nm = __ldg(mc.nmul + t);
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+      const int idx = 2 * ((int)threadIdx.x + u * NT);
+      if (idx < tot) {
+        const uint2 w = __ldg(a2 + (idx >> 1));
+        const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
+        float2* p = sm + pidx(slot, k1, LSTR);        // k1 even: no pad between the two
+        p[0] = cmul(make_float2(r[u].x, r[u].y), chirp_q32(nm * w.x));
+        p[1] = cmul(make_float2(r[u].z, r[u].w), chirp_q32(nm * w.y));
+      }
+    }
+  } else {
+    const ChirpAnchor* anc = mc.anc[t];
+    const int clog = __ldg(mc.clog + t);
+#pragma unroll
+    for (int u = 0; u < H; ++u) {
+      const int idx = 2 * ((int)threadIdx.x + u * NT);
+      if (idx < tot) {
+        const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
+        const unsigned ka = (unsigned)(r0 + slot) + ((unsigned)k1 << logR2), kb = ka + (1u << logR2);
+        const ChirpAnchor a = anc[ka >> clog], b = anc[kb >> clog];
+        float2* p = sm + pidx(slot, k1, LSTR);
+        p[0] = cmul(make_float2(r[u].x, r[u].y), chirp_from(a, clog, ka));
+        p[1] = cmul(make_float2(r[u].z, r[u].w), chirp_from(b, clog, kb));
+      }
+    }
+  }
+  __syncthreads();   // st3 and the tile
+  for (int i = threadIdx.x; i < nl * J; i += NT) {
+    const unsigned k2 = (unsigned)(r0 + (i >> LOGJ)), m1 = (unsigned)(i & (J - 1));
+    twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
+  }
+  __syncthreads();
+  j_runs<R1, J>(sm, stwj, twk, out + (size_t)t * out_tstride, nl, logR2, [&](int slot) { return r0 + slot; });
+}
+
 // ---------------------------------------------------------------------------
 // I1: per-sub-channel inverse column FFTs
 // ---------------------------------------------------------------------------
@@ -907,9 +999,14 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
                                                         float2* __restrict__ vout, long long vstride,
                                                         long long vofs, int logR1, int lognch, int logJ,
                                                         int m_lo, int m_hi, float scale,
-                                                        const float2* __restrict__ tw) {
+                                                        const float2* __restrict__ tw, TrialStride ts) {
   extern __shared__ float2 smem[];
   __shared__ int s_last;
+  // batched launches: blockIdx.y is the trial, with its own input, P, partials and tickets
+  in += blockIdx.y * ts.in;
+  P += blockIdx.y * ts.P;
+  part += blockIdx.y * ts.part;
+  cnt += blockIdx.y * ts.cnt;
   float2* stw = smem;
   float2* sm = smem + stage_table_size(R2);
   constexpr int LSTR = col_stride<R2>();

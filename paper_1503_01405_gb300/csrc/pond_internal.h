@@ -25,6 +25,19 @@ struct __align__(16) ChirpAnchor {
   unsigned pad[2];
 };
 
+// Chirps of the trials of one batched launch.  Table form (the lane's DMs are
+// whole multiples n_d of one step dDM): atab[k] = frac(sgn dDM c(f_k)) in Q0.32,
+// built once per lane in FP64, and trial d's phase at bin k is n_d atab[k]
+// mod 2^32, an exact integer product (its error is n_d times the table's
+// rounding, below 2^-33 cycles per step).  Anchor form: each trial's own
+// anchor table (chirp_from).
+struct MultiChirp {
+  const unsigned* atab;            // table form: [L], bin k2 + R2 k1 at k2 R1 + k1
+  const unsigned* nmul;            // table form: per trial of the launch, n_d
+  const ChirpAnchor* const* anc;   // anchor form: per trial of the launch
+  const int* clog;                 // anchor form: per trial of the launch
+};
+
 // Two-level twiddle table for exponents e < n: w^e = hi[e >> 12] * lo[e & 4095].
 constexpr int TW2_LOG = 12;
 constexpr int TW2_LO = 1 << TW2_LOG;
@@ -112,9 +125,20 @@ cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, co
                                 cudaStream_t st);
 cudaError_t launch_inv_rows_chirp(const Geom& g, const float2* in, float2* out, const float2* tw3L, const float2* twJ,
                                   const ChirpAnchor* anc, int clog, cudaStream_t st);
+// ntr > 1: one launch over ntr trials, trial t reading in + t L and writing
+// P + t M, part + t G M, cnt + t FUSED_J (G = fused_groups)
 cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
                                 long long vstride, long long vofs, int m_lo, int m_hi, const float2* tw,
-                                cudaStream_t st);
+                                cudaStream_t st, int ntr = 1);
+// Batched lanes: Ir over ntr trials in one launch (trial t writes out + t L),
+// the chirp from the lane's Q0.32 table (table = true) or each trial's anchors
+cudaError_t launch_inv_rows_chirp_multi(const Geom& g, const float2* in, float2* out, int ntr, const float2* tw3L,
+                                        const float2* twJ, MultiChirp mc, bool table, cudaStream_t st);
+cudaError_t launch_chirp_table(unsigned* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
+                               cudaStream_t st);
+cudaError_t launch_decimate_multi(const float* P, long long pstride, long long n, long long g0, long long num,
+                                  long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
+                                  const int* rows, int ntr, cudaStream_t st);
 size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,

@@ -28,6 +28,12 @@ POND_SPLIT_BF16 = 1
 POND_SPLIT_BF16_5T = 2
 POND_SCHEDULE_AUTO = 0
 POND_SCHEDULE_FOUR_PASS = 1
+POND_TRIALS_AUTO = 0
+POND_TRIALS_PER_TRIAL = 1
+POND_TRIALS_MULTI_ANCHOR = 2
+POND_TRIALS_MULTI_TABLE = 3
+TRIAL_MODE_NAMES = {POND_TRIALS_PER_TRIAL: "per-trial", POND_TRIALS_MULTI_ANCHOR: "multi-anchor",
+                    POND_TRIALS_MULTI_TABLE: "multi-table"}
 POND_NSTAGE = 9
 POND_NOALLOC_MAX_NBINS = 1024
 POND_STACK_ROTATION = 0
@@ -48,7 +54,7 @@ EXPORTS = ["pond_plan", "pond_plan_ex", "pond_push", "pond_push_device", "pond_f
            "pond_cnn_forward", "pond_cnn_gradient", "pond_cnn_train_step", "pond_cnn_destroy", "pond_patches",
            "pond_incoh_create", "pond_incoh_run", "pond_incoh_info_get", "pond_incoh_filterbank",
            "pond_incoh_series", "pond_incoh_profile", "pond_incoh_delays", "pond_incoh_destroy", "pond_incoh_ips",
-           "pond_stack_rows", "pond_fold_stack", "pond_probe_fp32_fma"]
+           "pond_stack_rows", "pond_fold_stack", "pond_probe_fp32_fma", "pond_tuning"]
 
 
 class PondError(RuntimeError):
@@ -68,7 +74,18 @@ class pond_opts(ctypes.Structure):
                 ("ndm", ctypes.c_int32), ("dm_list", ctypes.POINTER(ctypes.c_double)),
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("input_channels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("trial_mode", ctypes.c_int32), ("trials_per_launch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+POND_TUNE_MAXCAND = 8
+
+
+class pond_lane_info(ctypes.Structure):
+    _fields_ = [("nfft", ctypes.c_int64), ("ntrials", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("trials_per_launch", ctypes.c_int32), ("ncand", ctypes.c_int32), ("dm_step", ctypes.c_double),
+                ("cand_mode", ctypes.c_int32 * POND_TUNE_MAXCAND), ("cand_kt", ctypes.c_int32 * POND_TUNE_MAXCAND),
+                ("cand_us", ctypes.c_double * POND_TUNE_MAXCAND)]
 
 
 class pond_meta(ctypes.Structure):
@@ -171,6 +188,7 @@ def lib() -> ctypes.CDLL:
                             P(ctypes.c_int64), P(ctypes.c_int64), vp],
         "pond_incoh_destroy": [vp],
         "pond_probe_fp32_fma": [vp, ctypes.c_int32, ctypes.c_int32, vp, P(ctypes.c_double)],
+        "pond_tuning": [vp, vp, ctypes.c_int32, P(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -225,7 +243,8 @@ class Engine:
                  period: float, t_dec: float = 61.44e-6, want_voltages: bool = False,
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
                  precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
-                 schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1):
+                 schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1, trial_mode: int = POND_TRIALS_AUTO,
+                 trials_per_launch: int = 0):
         """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
@@ -238,6 +257,8 @@ class Engine:
         o.device = device
         o.schedule = schedule
         o.input_channels = input_channels
+        o.trial_mode = trial_mode
+        o.trials_per_launch = trials_per_launch
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])
@@ -339,6 +360,22 @@ class Engine:
         nf = np.zeros(n.value, np.int64)
         _check(lib().pond_trials(self._h, _ptr(dm), _ptr(nf), n.value, ctypes.byref(n)))
         return dm, nf
+
+    def tuning(self) -> list:
+        """How each lane runs its trials: FFT length, trials, mode, trials per
+        launch, DM step of the table form, and the autotuner's timed candidates."""
+        n = ctypes.c_int32()
+        _check(lib().pond_tuning(self._h, None, 0, ctypes.byref(n)))
+        arr = (pond_lane_info * max(1, n.value))()
+        _check(lib().pond_tuning(self._h, arr, n.value, ctypes.byref(n)))
+        out = []
+        for r in arr[:n.value]:
+            out.append({"nfft": r.nfft, "ntrials": r.ntrials, "mode": TRIAL_MODE_NAMES.get(r.mode, r.mode),
+                        "trials_per_launch": r.trials_per_launch, "dm_step": r.dm_step,
+                        "candidates_us_per_trial": [
+                            {"mode": TRIAL_MODE_NAMES.get(r.cand_mode[c], r.cand_mode[c]),
+                             "trials_per_launch": r.cand_kt[c], "us": r.cand_us[c]} for c in range(r.ncand)]})
+        return out
 
     def voltages(self, cap: int = 1 << 22):
         """Drain every kept dedispersed voltage: (complex64 [nchan, n], first g)."""

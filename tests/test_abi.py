@@ -114,6 +114,10 @@ def test_batched_plan_validation():
     with pytest.raises(pond.PondError) as e:        # the fixed nfft cannot carry DM 30
         pond.Engine(**base, dms=[0.1, 30.0])
     assert e.value.name == "NFFT"
+    for kw in (dict(trial_mode=4), dict(trial_mode=-1), dict(trials_per_launch=129), dict(trials_per_launch=-2)):
+        with pytest.raises(pond.PondError) as e:
+            pond.Engine(**base, dms=[0.1, 0.2], **kw)
+        assert e.value.name == "ARG", kw
 
 
 INCOH_CASES = [  # (options changed from a valid incoherent plan, expected code)
@@ -195,7 +199,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     structs = {"pond_opts": pond.pond_opts, "pond_meta": pond.pond_meta, "pond_cand": pond.pond_cand,
                "pond_stats_t": pond.pond_stats_t, "pond_incoh_opts": pond.pond_incoh_opts,
-               "pond_incoh_info": pond.pond_incoh_info}
+               "pond_incoh_info": pond.pond_incoh_info, "pond_lane_info": pond.pond_lane_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pond.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append(f'  printf("{cname} . %zu\\n", sizeof({cname}));')

@@ -20,30 +20,34 @@ def test_clock_summary_median_max_and_reasons():
 
 
 def test_traffic_lookup_follows_the_kernel_sources(tmp_path, monkeypatch):
-    """The committed counters are returned while the pass sources are the ones they
-    were taken with, and null for a kernel without counters or changed sources."""
+    """Counters are returned while the pass sources are the ones they were taken
+    with (the hash in their row), and null for a kernel without counters or for
+    changed sources."""
     rows = {}
     for line in open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.txt")):
         if line.strip() and not line.startswith("#"):
             k, h, v = line.split()[:3]
-            rows[k] = float(v)
-    assert rows
-    for k, v in rows.items():
-        assert bench.traffic_from_profiles(k) == v
-    assert bench.traffic_from_profiles("k_not_a_kernel") is None
-    # a copy of the tree whose pass sources differ by one byte
+            rows[k] = (h, float(v))
+    assert rows and all(len(h) == 16 for h, _ in rows.values())
+    for k, (h, v) in rows.items():
+        assert bench.traffic_from_profiles(k) == (v if h == bench.pass_sources_hash() else None)
+    # a copy of the tree whose counters carry the current hash, then a changed source
     root = tmp_path / "r"
     csrc = root / "paper_1503_01405_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (root / "profiles").mkdir()
-    shutil.copy(os.path.join(bench.ROOT, "profiles", "ncu_traffic.txt"), root / "profiles")
     for f in ("passes.cuh", "fft_block.cuh", "tc_dft.cuh"):
         shutil.copy(os.path.join(bench.ROOT, "paper_1503_01405_gb300", "csrc", f), csrc / f)
+    cur = bench.pass_sources_hash(str(root))
+    (root / "profiles" / "ncu_traffic.txt").write_text(
+        "# header\n" + "".join(f"{k} {cur} {v}\n" for k, (_, v) in rows.items()))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    k = next(iter(rows))
-    assert bench.traffic_from_profiles(k) == rows[k]
+    for k, (_, v) in rows.items():
+        assert bench.traffic_from_profiles(k) == v
+    assert bench.traffic_from_profiles("k_not_a_kernel") is None
     with open(csrc / "passes.cuh", "a") as f:
         f.write("\n")
+    k = next(iter(rows))
     assert bench.traffic_from_profiles(k) is None
 
 

@@ -141,3 +141,93 @@ def test_single_trial_batch_equals_single_dm_plan_three_pass():
         Ts, Cs, js = e.timeseries()
     assert js == j0 and np.array_equal(Cs, C)
     assert np.array_equal(T[0], Ts)
+
+
+# Uniform DM grid from 0 (whole multiples of one step), three-pass geometry
+# (nfft 2^21, 16 sub-channels): the forms that run several trials per launch
+# against the oracle, with a trial block that does not divide the trial count.
+GRID = [0.6 * d for d in range(6)]
+
+
+@pytest.fixture(scope="module")
+def grid_case():
+    nfft, nchan, t_dec = 1 << 21, 16, 16e-6
+    p = pcd.make_plan(F0, BW, FS, max(GRID), nfft, nchan, 1, 1.0, t_dec)
+    x = stream(3 * p.S + nfft + 4321, seed=37, dm=1.8)
+    return x, nfft, nchan, t_dec, oracle_batched(x, GRID, [nfft] * len(GRID), nchan, t_dec)
+
+
+def tuned(dms, nfft, nchan, t_dec, **kw):
+    with pond.Engine(F0, BW, FS, 0.0, nfft, nchan, 1, 1.0, t_dec=t_dec, dms=dms, **kw) as e:
+        return e.tuning()
+
+
+@pytest.mark.parametrize("mode,kt", [(pond.POND_TRIALS_PER_TRIAL, 0), (pond.POND_TRIALS_MULTI_ANCHOR, 4),
+                                     (pond.POND_TRIALS_MULTI_TABLE, 4), (pond.POND_TRIALS_MULTI_TABLE, 0),
+                                     (pond.POND_TRIALS_MULTI_ANCHOR, 6)])
+def test_multi_trial_forms_match_oracle(grid_case, mode, kt):
+    x, nfft, nchan, t_dec, res = grid_case
+    T, C, j0, nf = run_engine(x, GRID, nfft, nchan, t_dec, trial_mode=mode, trials_per_launch=kt)
+    info = tuned(GRID, nfft, nchan, t_dec, trial_mode=mode, trials_per_launch=kt)
+    assert len(info) == 1 and info[0]["mode"] == pond.TRIAL_MODE_NAMES[mode]
+    assert info[0]["trials_per_launch"] == (1 if mode == pond.POND_TRIALS_PER_TRIAL else (kt or len(GRID)))
+    assert abs(info[0]["dm_step"] - 0.6) < 1e-12 or mode == pond.POND_TRIALS_PER_TRIAL
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (mode, kt, d, rel(T[d], r.ts))
+
+
+def test_multi_anchor_form_equals_per_trial_launches_bit_exact(grid_case):
+    """The multi-trial anchor form runs the same chirp, runs and column pass per
+    trial as the per-trial launches: identical series, bit for bit."""
+    x, nfft, nchan, t_dec, _ = grid_case
+    a = run_engine(x, GRID, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_PER_TRIAL)
+    b = run_engine(x, GRID, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_ANCHOR, trials_per_launch=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_multi_table_streaming_invariance_bit_exact(grid_case):
+    x, nfft, nchan, t_dec, _ = grid_case
+    a = run_engine(x, GRID, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_TABLE, trials_per_launch=4)
+    rng = np.random.default_rng(5)
+    cuts, left = [], len(x)
+    while left > 0:
+        c = int(min(left, rng.integers(1, 3_000_000)))
+        cuts.append(c)
+        left -= c
+    b = run_engine(x, GRID, nfft, nchan, t_dec, chunks=cuts, trial_mode=pond.POND_TRIALS_MULTI_TABLE,
+                   trials_per_launch=4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_table_form_falls_back_to_anchors_off_grid():
+    """DMs that are not whole multiples of one step cannot use the table: the
+    lane runs the anchor form (reported by pond_tuning), still against the oracle."""
+    dms = [0.0, 1.0, 2.5, 2.9]
+    nfft, nchan, t_dec = 1 << 21, 16, 16e-6
+    info = tuned(dms, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_TABLE)
+    assert info[0]["mode"] == "multi-anchor" and info[0]["dm_step"] == 0.0
+    p = pcd.make_plan(F0, BW, FS, max(dms), nfft, nchan, 1, 1.0, t_dec)
+    x = stream(2 * p.S + nfft + 99, seed=38, dm=1.0)
+    T, C, j0, _ = run_engine(x, dms, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_TABLE)
+    res = oracle_batched(x, dms, [nfft] * len(dms), nchan, t_dec)
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
+
+
+def test_trial_autotuner_times_every_form(grid_case):
+    """With autotune the lane's forms (per-trial launches; anchors and table at 8
+    and 32 trials per launch, clipped to the trial count) are timed, the fastest
+    per trial runs, and the result still matches the oracle."""
+    x, nfft, nchan, t_dec, res = grid_case
+    info = tuned(GRID, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
+    c = info[0]["candidates_us_per_trial"]
+    assert {k["mode"] for k in c} == {"per-trial", "multi-anchor", "multi-table"}
+    assert all(k["us"] > 0 for k in c)
+    best = min(c, key=lambda k: k["us"])
+    assert info[0]["mode"] == best["mode"]
+    T, C, j0, nf = run_engine(x, GRID, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
