@@ -853,6 +853,7 @@ def run_learned(args, rank):
     t0 = time.perf_counter()
     Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000, shifts=args.shifts)
     Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000, shifts=args.shifts)
+    Xva, Yva, Fva = learn.build_dataset(max(2, args.chunks // 8), seed=3000, shifts=args.shifts)
     gen_s = time.perf_counter() - t0
     theta = learn.init_params(99)
     clf = pond.Classifier(theta, max_batch=512)
@@ -861,7 +862,12 @@ def run_learned(args, rank):
     hist = learn.train(clf, Xtr, Ytr, epochs=args.epochs, batch=256, lr=2e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    res = learn.evaluate(learn.predict(clf, Xte), Yte, Fte)
+    pte = learn.predict(clf, Xte)
+    res = learn.evaluate(pte, Yte, Fte)
+    # the boxcar with the network's veto, at the operating point that keeps the
+    # boxcar's recall on the validation chunks
+    tau = learn.veto_threshold(learn.predict(clf, Xva), Yva, Fva, 0.0)
+    veto = learn.evaluate_veto(pte, Yte, Fte, tau)
     rate = learn.inference_rate(clf, Xte)
     clf.close()
     line = {"metric": "single-pulse candidates classified per second (CNN inference)", "value": rate,
@@ -871,7 +877,8 @@ def run_learned(args, rank):
                        "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)), "epochs": args.epochs,
                        "shifts_per_event": args.shifts, "train_chunks": args.chunks,
                        "batch": 256, "lr": 2e-3},
-            "evaluation": res, "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
+            "evaluation": res, "boxcar_with_network_veto": veto, "validation_patches": int(len(Yva)),
+            "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
             "dataset_s": gen_s}
     print(json.dumps(line), flush=True)
 
@@ -962,6 +969,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=20, help="learned: training epochs")
     ap.add_argument("--incoh-mode", default="aid", choices=["aid", "cid"],
                     help="incoherent: adding in phase (AID) or correlation (CID)")
+    ap.add_argument("--chirp", default="auto", choices=["auto", "anchors", "table"],
+                    help="full-rate: chirp source of the fused forward row pass (POND_CHIRP_*)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16x5"],
                     help="full-rate: arithmetic of the radix-16 FFT stages (FP32, or split-BF16 tensor-core "
                          "DFT products with three or five terms)")
@@ -1010,8 +1019,9 @@ def main():
     # the timed engine runs consecutive segments on two streams (they overlap);
     # a second engine with per-stage timing runs them one after another, so its
     # CUDA events give each kernel's own duration for the roofline
+    chirp = {"auto": pond.POND_CHIRP_AUTO, "anchors": pond.POND_CHIRP_ANCHORS, "table": pond.POND_CHIRP_TABLE}[args.chirp]
     eng = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
-                      t_dec=PLAN["t_dec"], device=local, precision=prec, input_channels=ch)
+                      t_dec=PLAN["t_dec"], device=local, precision=prec, input_channels=ch, chirp=chirp)
     stream = torch.cuda.current_stream(dev)
 
     def step_device(e):
@@ -1041,7 +1051,7 @@ def main():
     # dominant kernel from per-stage CUDA-event times of serialized steps
     eng_t = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
                         t_dec=PLAN["t_dec"], timing=True, device=local, precision=prec,
-                        input_channels=ch)
+                        input_channels=ch, chirp=chirp)
     step_device(eng_t)
     tst0 = eng_t.stats()
     t_steps = max(1, min(args.steps, 2))
@@ -1089,7 +1099,7 @@ def main():
         h2d_s.append(time.perf_counter() - t0)
     h2d_gbs = n * ch / min(h2d_s) / 1e9
     eng_h = pond.Engine(F0, BW, FS, PLAN["dm"], PLAN["nfft"], PLAN["nchan"], PLAN["nbins"], PLAN["period"],
-                        t_dec=PLAN["t_dec"], device=local, precision=prec, input_channels=ch)
+                        t_dec=PLAN["t_dec"], device=local, precision=prec, input_channels=ch, chirp=chirp)
     prof = {}
     phases = []
 

@@ -129,8 +129,18 @@ typedef struct {
                            else the multi-trial table form where the lane's DMs allow it */
   int32_t trials_per_launch; /* batched plans with a multi-trial mode: trials per launch
                                 (1 .. 128); 0 = chosen as for trial_mode (default 32) */
-  int32_t reserved[3];
+  int32_t chirp;        /* single-DM three-pass plans: where the forward row pass takes Eq. 4's
+                           inverse filter from (POND_CHIRP_*) */
+  int32_t reserved[2];
 } pond_opts;
+
+/* Chirp source of a single-DM plan's fused forward row pass. */
+#define POND_CHIRP_AUTO 0     /* this build's default: POND_CHIRP_ANCHORS */
+#define POND_CHIRP_ANCHORS 1  /* evaluated per bin from FP64-built anchors (exact Q0.64 phase
+                                 polynomial, FP32 sine and cosine): no per-bin memory read, as the
+                                 paper's convolution kernel computes the chirp per thread */
+#define POND_CHIRP_TABLE 2    /* read per bin from an FP32 (cos, -sin) table built once per plan in
+                                 FP64 (8 bytes per bin, nfft * 4 bytes of device memory) */
 
 /* Per-trial passes of a batched lane (one FFT length).  Every trial of the lane
  * shares the lane's forward spectrum; its own passes are the chirp (Eq. 4) with

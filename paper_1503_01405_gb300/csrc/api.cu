@@ -105,6 +105,7 @@ struct Trial {
   ChirpAnchor* anc = nullptr;
   int clog = 0;
   long long nanc = 0;
+  float2* ctab = nullptr;   // per-bin inverse filter (POND_CHIRP_TABLE, single-DM three-pass plans)
 };
 
 // One FFT length: segmentation, buffers, stream state.
@@ -264,6 +265,8 @@ int validate(const pond_opts* o) {
     return fail(POND_E_ARG, "trial_mode %d is not a POND_TRIALS_* value", o->trial_mode);
   if (o->trials_per_launch < 0 || o->trials_per_launch > 128)
     return fail(POND_E_ARG, "trials_per_launch must be in 0 .. 128");
+  if (o->chirp < POND_CHIRP_AUTO || o->chirp > POND_CHIRP_TABLE)
+    return fail(POND_E_ARG, "chirp %d is not a POND_CHIRP_* value", o->chirp);
   if (o->schedule != POND_SCHEDULE_AUTO && o->schedule != POND_SCHEDULE_FOUR_PASS)
     return fail(POND_E_ARG, "schedule must be POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS");
   if (o->input_channels < 0 || o->input_channels > 2)
@@ -338,6 +341,10 @@ int build_trial(pond_t h, const pond_opts* o, Trial* t) {
   const double half = std::fabs(o->bw_mhz) / 2.0;
   const double alpha = K_DM * 1e6 * t->dm / (o->f0_mhz * o->f0_mhz);
   CK(launch_tables(t->anc, t->nanc, t->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  if (o->chirp == POND_CHIRP_TABLE && ln.fused) {
+    CK(cudaMalloc(&t->ctab, (size_t)ln.g.L * sizeof(float2)));
+    CK(launch_chirp_c64(t->ctab, ln.g, du, half, o->f0_mhz, alpha, h->sgn, h->st));
+  }
   return POND_OK;
 }
 
@@ -601,7 +608,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   if (ln.fused) {
     // three passes: F2f takes the chirp and the first inverse factor, Ic the rest
     const Trial& t = h->trials[ln.trials[0]];
-    CK(launch_fwd_rows_inv(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, ln.stwJ, t.anc, t.clog, cs));
+    CK(launch_fwd_rows_inv(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, ln.stwJ, t.anc, t.clog, t.ctab, cs));
     RC(record(h, 1 + ST_F2F, cs));
     // P of this slot is free once the fold of segment s - NSLOT has read it
     if (!h->timing) CK(cudaStreamWaitEvent(cs, h->ev_pfree[slot], 0));
@@ -775,7 +782,10 @@ void destroy_all(pond_t h) {
     if (h->sx[k]) cudaStreamSynchronize(h->sx[k]);
   if (h->st) cudaStreamSynchronize(h->st);
   for (auto& ln : h->lanes) free_lane(&ln);
-  for (auto& t : h->trials) cudaFree(t.anc);
+  for (auto& t : h->trials) {
+    cudaFree(t.anc);
+    cudaFree(t.ctab);
+  }
   cudaFree(h->prof_sum);
   cudaFree(h->prof_hits);
   cudaFree(h->psum);

@@ -485,9 +485,35 @@ __global__ void k_make_chirp_table(unsigned* tab, int logR1, int logR2, double d
   tab[i] = (unsigned)((unsigned long long)llrint(fr * 4294967296.0) & 0xffffffffull);
 }
 
+// The inverse filter of Eq. 4 per bin as FP32 (cos, -sin) of 2 pi phi(k), in
+// the spectrum's row layout (bin k2 + R2 k1 at k2 R1 + k1): phi in FP64 with the
+// anchors' formula, reduced mod 1, then FP64 sincospi, rounded once to FP32.
+__global__ void k_make_chirp_c64(float2* tab, int logR1, int logR2, double du, double half, double f0, double alpha,
+                                 int sgn) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (1ll << (logR1 + logR2))) return;
+  const long long k2 = i >> logR1, k1 = i & ((1ll << logR1) - 1);
+  const double k = (double)(k2 + (k1 << logR2));
+  const double f = sgn > 0 ? __dsub_rn(__dmul_rn(k, du), half) : __dsub_rn(half, __dmul_rn(k, du));
+  const double g = f0 + f;
+  const double phi = sgn * (alpha * f * f / g);
+  double r = phi - floor(phi);
+  if (r > 0.5) r -= 1.0;
+  double sn, cs;
+  sincospi(2.0 * r, &sn, &cs);
+  tab[i] = make_float2((float)cs, (float)-sn);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_chirp_c64(float2* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
+                             cudaStream_t st) {
+  const long long n = g.L;
+  k_make_chirp_c64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tab, g.logR1, g.logR2, du, half, f0, alpha, sgn);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chirp_table(unsigned* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
                                cudaStream_t st) {
@@ -553,12 +579,20 @@ size_t smem_inv_cols_det(int nl) {
 
 cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L,
                                 const float2* tw, const float2* twJ, const ChirpAnchor* anc, int clog,
-                                cudaStream_t st) {
+                                const float2* ctab, cudaStream_t st) {
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   const unsigned grid = (unsigned)(R2 / nl);
   switch (R1) {
-#define CASE(R) case R: k_fwd_rows_inv<R, FUSED_J><<<grid, NT, smem_fwd_rows_inv(R, nl), st>>>(in, out, g.logR2, g.logL, tw3L, tw2L, tw, twJ, anc, clog); break;
+#define CASE(R)                                                                                             \
+  case R:                                                                                                   \
+    if (ctab)                                                                                               \
+      k_fwd_rows_inv<R, FUSED_J, true><<<grid, NT, smem_fwd_rows_inv(R, nl), st>>>(                        \
+          in, out, g.logR2, g.logL, tw3L, tw2L, tw, twJ, anc, clog, ctab);                                  \
+    else                                                                                                    \
+      k_fwd_rows_inv<R, FUSED_J, false><<<grid, NT, smem_fwd_rows_inv(R, nl), st>>>(                       \
+          in, out, g.logR2, g.logL, tw3L, tw2L, tw, twJ, anc, clog, ctab);                                  \
+    break;
     POND_FUSED_R1(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -639,7 +673,8 @@ cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float
 cudaError_t set_kernel_attributes() {
   cudaError_t e = set_attributes_t<false>();
 #define SET_F(R) \
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows_inv<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd_rows_inv(R, TILE / R));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows_inv<R, FUSED_J, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd_rows_inv(R, TILE / R)); \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows_inv<R, FUSED_J, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_fwd_rows_inv(R, TILE / R));
   POND_FUSED_R1(SET_F)
 #undef SET_F
 #define SET_I(R) \

@@ -596,12 +596,13 @@ __device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const flo
 // c = g nl + ci, at ((m1 G + g) R2 + k2) nl + ci, so that each Ic CTA reads one
 // contiguous block (its stores here are runs of 4 sub-channels, 32 bytes).
 // The row stride R1 + R1/16 makes each run a line of stride J + J/16.
-template <int R1, int J>
+template <int R1, int J, bool CTAB>
 __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict__ in, float2* __restrict__ out,
                                                         int logR2, int logL, const float2* __restrict__ tw3L,
                                                         Tw2 tw2L, const float2* __restrict__ tw,
                                                         const float2* __restrict__ twJ,
-                                                        const ChirpAnchor* __restrict__ anc, int clog) {
+                                                        const ChirpAnchor* __restrict__ anc, int clog,
+                                                        const float2* __restrict__ ctab) {
   static_assert(J >= 16 && J % 16 == 0 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
   constexpr int NCH = R1 / J;                 // sub-channels
   constexpr int LSTR = R1 + R1 / 16;
@@ -628,9 +629,14 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   __syncthreads();
   Stages<R1, 16, false, LSTR>::run(sm, nl, stw);          // the stages after the first
   f2_split<R1, LSTR>(sm, q0, np, R2, logR2, logL, tw2L, [&](int slot, int row, int k1, float2 X) {
-    const unsigned k = (unsigned)row + ((unsigned)k1 << logR2);
-    const ChirpAnchor a = anc[k >> clog];   // every row spans the band: L1/L2-resident table
-    sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
+    if constexpr (CTAB) {
+      // the chirp of bin row + R2 k1 from the plan's table (row layout: consecutive lanes, consecutive words)
+      sm[pidx(slot, k1, LSTR)] = cmul(X, __ldg(ctab + ((size_t)row << LOGR1) + k1));
+    } else {
+      const unsigned k = (unsigned)row + ((unsigned)k1 << logR2);
+      const ChirpAnchor a = anc[k >> clog];   // every row spans the band: L1/L2-resident table
+      sm[pidx(slot, k1, LSTR)] = cmul(X, chirp_from(a, clog, k));
+    }
   });
   __syncthreads();
   j_runs<R1, J>(sm, stwj, twk, out, nl, logR2, [&](int slot) { return f2_line(slot, q0, np, R2); });

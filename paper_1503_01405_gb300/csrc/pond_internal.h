@@ -120,9 +120,12 @@ cudaError_t launch_inv_rows(const Geom& g, const float2* buf, float* P, float2* 
 constexpr int FUSED_J = 64;
 bool fused_geometry(const Geom& g);
 int fused_groups(const Geom& g);
+// ctab non-null: the chirp from that per-bin table (launch_chirp_c64), else from the anchors
 cudaError_t launch_fwd_rows_inv(const Geom& g, const float2* in, float2* out, const float2* tw3L, Tw2 tw2L,
                                 const float2* tw, const float2* twJ, const ChirpAnchor* anc, int clog,
-                                cudaStream_t st);
+                                const float2* ctab, cudaStream_t st);
+cudaError_t launch_chirp_c64(float2* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
+                             cudaStream_t st);
 cudaError_t launch_inv_rows_chirp(const Geom& g, const float2* in, float2* out, const float2* tw3L, const float2* twJ,
                                   const ChirpAnchor* anc, int clog, cudaStream_t st);
 // ntr > 1: one launch over ntr trials, trial t reading in + t L and writing

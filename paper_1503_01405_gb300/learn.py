@@ -139,10 +139,51 @@ def predict(clf: pond.Classifier, X, batch: int = 512) -> np.ndarray:
     return np.concatenate(out)
 
 
-def evaluate(prob: np.ndarray, Y: np.ndarray, flags: np.ndarray) -> dict:
+def threshold_for_recall(prob: np.ndarray, Y: np.ndarray, recall: float) -> float:
+    """The largest threshold on the pulse-class probability whose recall on
+    (prob, Y) reaches `recall` (an operating point chosen on a validation set)."""
+    p = np.sort(prob[Y == synth.EV_PULSE, synth.EV_PULSE])[::-1]
+    if len(p) == 0:
+        return 0.5
+    k = min(len(p) - 1, max(0, int(np.ceil(recall * len(p))) - 1))
+    return float(p[k])
+
+
+def veto_threshold(prob: np.ndarray, Y: np.ndarray, flags: np.ndarray, max_recall_loss: float) -> float:
+    """Operating point of the boxcar + network detector (a patch is flagged when
+    the boxcar flags it and the network's pulse probability is >= tau): the
+    largest tau whose recall on (prob, Y, flags) stays within max_recall_loss
+    of the boxcar's own (chosen on a validation set)."""
+    pos = Y == synth.EV_PULSE
+    if not pos.any():
+        return 0.0
+    need = flags[pos].mean() - max_recall_loss
+    p = np.sort(prob[pos & flags, synth.EV_PULSE])[::-1]   # pulse patches the boxcar flags
+    k = int(np.ceil(need * pos.sum())) - 1
+    if k < 0:
+        return float(p[0]) if len(p) else 0.0
+    return float(p[min(k, len(p) - 1)]) if len(p) else 0.0
+
+
+def evaluate_veto(prob: np.ndarray, Y: np.ndarray, flags: np.ndarray, tau: float) -> dict:
+    """Recall and false-positive rate of the boxcar alone and of the boxcar with
+    the network's veto (flag and pulse probability >= tau)."""
+    pos = Y == synth.EV_PULSE
+    neg = ~pos
+    both = flags & (prob[:, synth.EV_PULSE] >= tau)
+    return {"tau": tau, "n_pulse": int(pos.sum()), "n_other": int(neg.sum()),
+            "boxcar_recall": float(flags[pos].mean()), "boxcar_fpr": float(flags[neg].mean()),
+            "boxcar_cnn_recall": float(both[pos].mean()), "boxcar_cnn_fpr": float(both[neg].mean())}
+
+
+def evaluate(prob: np.ndarray, Y: np.ndarray, flags: np.ndarray, threshold: float | None = None) -> dict:
     """Recall on dispersed pulses and false-positive rate on the other classes,
-    for the classifier (argmax = pulse) and for the boxcar flag."""
-    pred_pulse = prob.argmax(1) == synth.EV_PULSE
+    for the classifier (argmax = pulse, or pulse probability >= threshold) and
+    for the boxcar flag."""
+    if threshold is None:
+        pred_pulse = prob.argmax(1) == synth.EV_PULSE
+    else:
+        pred_pulse = prob[:, synth.EV_PULSE] >= threshold
     pos = Y == synth.EV_PULSE
     neg = ~pos
     res = {"n_test": int(len(Y)), "n_pulse": int(pos.sum()),

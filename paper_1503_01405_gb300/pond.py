@@ -28,6 +28,9 @@ POND_SPLIT_BF16 = 1
 POND_SPLIT_BF16_5T = 2
 POND_SCHEDULE_AUTO = 0
 POND_SCHEDULE_FOUR_PASS = 1
+POND_CHIRP_AUTO = 0
+POND_CHIRP_ANCHORS = 1
+POND_CHIRP_TABLE = 2
 POND_TRIALS_AUTO = 0
 POND_TRIALS_PER_TRIAL = 1
 POND_TRIALS_MULTI_ANCHOR = 2
@@ -75,7 +78,7 @@ class pond_opts(ctypes.Structure):
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("input_channels", ctypes.c_int32),
                 ("trial_mode", ctypes.c_int32), ("trials_per_launch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("chirp", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 POND_TUNE_MAXCAND = 8
@@ -244,7 +247,7 @@ class Engine:
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
                  precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
                  schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1, trial_mode: int = POND_TRIALS_AUTO,
-                 trials_per_launch: int = 0):
+                 trials_per_launch: int = 0, chirp: int = POND_CHIRP_AUTO):
         """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
@@ -259,6 +262,7 @@ class Engine:
         o.input_channels = input_channels
         o.trial_mode = trial_mode
         o.trials_per_launch = trials_per_launch
+        o.chirp = chirp
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])

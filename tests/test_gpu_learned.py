@@ -1,5 +1,6 @@
 """The learned form end to end on a small scale: labelled chunks through the
-batched engine, patches, training on the GPU, evaluation beside the boxcar."""
+batched engine, patches, training on the GPU, evaluation beside the boxcar,
+and what the trained network gains over the boxcar detector alone."""
 import numpy as np
 import pytest
 
@@ -73,3 +74,26 @@ def test_scored_candidates_match_patches_and_forward():
     prob = learn.predict(clf, X)
     clf.close()
     assert np.array_equal(np.array([c["score"] for c in scored], np.float32), prob[:, 0].astype(np.float32))
+
+
+def test_network_veto_gains_over_boxcar():
+    """What the trained network adds to the method without it.  The boxcar S/N >= 6
+    detector flags narrowband RFI (a 2-sigma sinusoid integrated over ms widths
+    reaches S/N 6 at every trial); the network, trained on the GPU by the
+    library's kernels, vetoes the boxcar's flags whose pulse probability is
+    below tau, with tau chosen on a validation set (disjoint seeds) as the
+    largest that keeps the boxcar's validation recall.  On held-out chunks
+    (disjoint seeds again) the combination keeps the boxcar's recall within
+    0.03 and cuts its false-positive rate at least fourfold."""
+    Xtr, Ytr, _ = learn.build_dataset(16, seed=1000, shifts=16)
+    Xva, Yva, Fva = learn.build_dataset(4, seed=3000, shifts=16)
+    Xte, Yte, Fte = learn.build_dataset(6, seed=2000, shifts=16)
+    clf = pond.Classifier(learn.init_params(99), max_batch=512)
+    learn.train(clf, Xtr, Ytr, epochs=15, batch=256, lr=2e-3, seed=3)
+    tau = learn.veto_threshold(learn.predict(clf, Xva), Yva, Fva, 0.0)
+    r = learn.evaluate_veto(learn.predict(clf, Xte), Yte, Fte, tau)
+    clf.close()
+    assert r["n_pulse"] > 300 and r["n_other"] > 1000, r
+    assert r["boxcar_fpr"] > 0.03, r                  # the boxcar alone is fooled by RFI ...
+    assert r["boxcar_cnn_recall"] >= r["boxcar_recall"] - 0.03, r
+    assert r["boxcar_cnn_fpr"] <= 0.25 * r["boxcar_fpr"], r   # ... and the network removes most of it

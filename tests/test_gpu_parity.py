@@ -33,9 +33,10 @@ def rel(a, b):
 
 
 def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6,
-               schedule=pond.POND_SCHEDULE_AUTO, input_channels=1):
+               schedule=pond.POND_SCHEDULE_AUTO, input_channels=1, chirp=pond.POND_CHIRP_AUTO):
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
-                     want_voltages=want_voltages, schedule=schedule, input_channels=input_channels) as e:
+                     want_voltages=want_voltages, schedule=schedule, input_channels=input_channels,
+                     chirp=chirp) as e:
         if device_push:
             import torch
             t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -135,6 +136,9 @@ def test_three_pass_schedule(cfg):
     four = run_engine(x, p, schedule=pond.POND_SCHEDULE_FOUR_PASS)
     check(three, r)
     check(four, r)
+    # the fused row pass with its chirp read from the per-bin table instead of the anchors
+    check(run_engine(x, p, chirp=pond.POND_CHIRP_TABLE), r)
+    check(run_engine(x, p, chirp=pond.POND_CHIRP_ANCHORS), r)
     segs = three["stats"]["segments"]
     assert segs == four["stats"]["segments"] and segs >= 2
     assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
