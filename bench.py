@@ -379,7 +379,7 @@ def run_reference(args, rank, ws, dist):
     print(json.dumps(line), flush=True)
 
 
-def batched_core(dev, local, stream, steps, warmup, seed_offset=0, samples=0, dist=None):
+def batched_core(dev, local, stream, steps, warmup, seed_offset=0, samples=0, dist=None, precision=0):
     """Batched DM trials on one 8 s chunk: returns the timing and the plan's choices."""
     import torch
 
@@ -392,7 +392,8 @@ def batched_core(dev, local, stream, steps, warmup, seed_offset=0, samples=0, di
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     eng = pond.Engine(F0, BW, FS, 0.0, 1 << 24, 64, 1, 1.0, t_dec=32e-6, device=local,
-                      dms=synth.BATCH_DMS, nfft_choices=(1 << 22, 1 << 23, 1 << 24), autotune=True)
+                      dms=synth.BATCH_DMS, nfft_choices=(1 << 22, 1 << 23, 1 << 24), autotune=True,
+                      precision=precision)
     plan_s = time.perf_counter() - t0
     _, nf = eng.trials()
     groups = {int(n): int((nf == n).sum()) for n in sorted(set(nf.tolist()))}
@@ -440,12 +441,15 @@ def run_batched(args, rank, ws, dist):
     dev = torch.device("cuda", local)
     pbuild.build()
     stream = torch.cuda.current_stream(dev)
-    r = batched_core(dev, local, stream, args.steps, args.warmup, seed_offset=rank, samples=args.samples, dist=dist)
+    prec = {"fp32": 0, "bf16x3": 1, "bf16x5": 2}[args.precision]
+    r = batched_core(dev, local, stream, args.steps, args.warmup, seed_offset=rank, samples=args.samples, dist=dist,
+                     precision=prec)
     value = ws * r["n"] * args.steps / (r["ms"] / 1e3) / 1e6
     if rank == 0:
         line = {"metric": METRIC + " [batched DM trials]", "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32acc", "bf16x5": "bf16x5+f32acc"}[args.precision],
                 "data": "synthetic", "realtime_factor": value / REALTIME_MSPS,
                 "trial_samples_per_s": value * 1e6 * len(synth.BATCH_DMS),
                 "config": {"workload": BATCHED_WORKLOAD, "samples_per_step": r["n"],

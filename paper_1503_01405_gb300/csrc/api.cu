@@ -120,6 +120,7 @@ struct Lane {
   // fused schedule (F1, F2f, Ic; batched: F1, F2, per trial Ir, Ic): Ic's group
   // partials and per-m1 tickets per slot
   bool fused = false, fused_multi = false;
+  bool ic_tc = false;                       // the column pass on the tensor cores (three-term split-BF16 plans)
   float* part[NSLOT] = {};
   int* cnt[NSLOT] = {};
   // per trial of the lane and slot: after that trial's fold / decimation of a segment
@@ -229,6 +230,7 @@ struct pond_s {
   int tc_terms = 0;
   uint4* wdft = nullptr;
   int* tc_err = nullptr;
+  uint4* ic_ops = nullptr;                  // operand block of the tensor-core column pass
 };
 
 namespace {
@@ -355,8 +357,13 @@ int build_lane(pond_t h, Lane* ln) {
     ln->g.tc_inv = {h->wdft + TC_W_BYTES / 16, h->tc_terms, h->tc_err};
   }
   const Geom& g = ln->g;
-  ln->fused = !h->multi && !h->tc_terms && h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g);
-  ln->fused_multi = h->multi && !h->tc_terms && h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g);
+  // three-pass lanes: FP32 plans with M = 64 R2, and three-term split-BF16 plans whose column
+  // pass has a tensor-core form (R2 = 2048); the fused row pass itself is FP32 in both
+  const bool three = h->schedule == POND_SCHEDULE_AUTO && fused_geometry(g) &&
+                     (!h->tc_terms || (h->tc_terms == 3 && ic_tc_geometry(g)));
+  ln->fused = !h->multi && three;
+  ln->fused_multi = h->multi && three;
+  ln->ic_tc = three && h->tc_terms == 3;
   for (int k = 0; k < NSLOT; ++k) {
     CK(cudaMalloc(&ln->bufA[k], g.L * sizeof(float2)));
     CK(cudaMalloc(&ln->bufB[k], g.L * sizeof(float2)));
@@ -563,6 +570,15 @@ void update_complete(pond_t h) {
 }
 
 // Process segment s of lane li; g_end bounds the emitted channel samples.
+// The column pass of a three-pass lane: FP32 or tensor-core form.
+cudaError_t launch_ic(pond_t h, const Lane& ln, const float2* in, float* P, float* part, int* cnt, float2* vout,
+                      long long vstride, long long vofs, int m_lo, int m_hi, cudaStream_t st, int ntr = 1) {
+  if (ln.ic_tc)
+    return launch_inv_cols_det_tc(ln.g, in, P, part, cnt, vout, vstride, vofs, m_lo, m_hi, h->ic_ops, h->tc_err, st,
+                                  ntr);
+  return launch_inv_cols_det(ln.g, in, P, part, cnt, vout, vstride, vofs, m_lo, m_hi, ln.stwR2, st, ntr);
+}
+
 int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
   Lane& ln = h->lanes[li];
   const Geom& g = ln.g;
@@ -612,8 +628,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     RC(record(h, 1 + ST_F2F, cs));
     // P of this slot is free once the fold of segment s - NSLOT has read it
     if (!h->timing) CK(cudaStreamWaitEvent(cs, h->ev_pfree[slot], 0));
-    CK(launch_inv_cols_det(g, bufB, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
-                           (int)m_hi, ln.stwR2, cs));
+    CK(launch_ic(h, ln, bufB, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, cs));
     RC(record(h, 1 + ST_IC, cs));
     // folds run in segment order on their own stream (on st with per-stage timing)
     cudaStream_t fs = h->timing ? cs : h->sf;
@@ -642,8 +657,8 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
         CK(launch_inv_rows_chirp_multi(g, bufB, ln.bufT[slot], nq, ln.tw3L, ln.stwJ, mc,
                                        ln.mode == POND_TRIALS_MULTI_TABLE, cs));
         if (b == 0) RC(record(h, 1 + ST_IR, cs));
-        CK(launch_inv_cols_det(g, ln.bufT[slot], ln.Pm[slot], ln.partm[slot], ln.cntm[slot], nullptr, 0, 0,
-                               (int)m_lo, (int)m_hi, ln.stwR2, cs, nq));
+        CK(launch_ic(h, ln, ln.bufT[slot], ln.Pm[slot], ln.partm[slot], ln.cntm[slot], nullptr, 0, 0, (int)m_lo,
+                     (int)m_hi, cs, nq));
         if (b == 0) RC(record(h, 1 + ST_IC, cs));
         // the block's series rows are updated in segment order
         CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][b], 0));
@@ -672,8 +687,8 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
           // the trial's chirp and the first inverse factor as Ir loads the shared spectrum's rows
           CK(launch_inv_rows_chirp(g, bufB, bufA, ln.tw3L, ln.stwJ, t.anc, t.clog, cs));
           if (q == 0) RC(record(h, 1 + ST_IR, cs));
-          CK(launch_inv_cols_det(g, bufA, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
-                                 (int)m_hi, ln.stwR2, cs));
+          CK(launch_ic(h, ln, bufA, P, ln.part[slot], ln.cnt[slot], vout, h->v_cap, h->v_len, (int)m_lo,
+                       (int)m_hi, cs));
           if (q == 0) RC(record(h, 1 + ST_IC, cs));
         } else {
           // every trial's chirp is applied as I1 loads the shared forward spectrum
@@ -798,6 +813,7 @@ void destroy_all(pond_t h) {
   cudaFree(h->vbuf);
   cudaFree(h->wdft);
   cudaFree(h->tc_err);
+  cudaFree(h->ic_ops);
   for (auto& se : h->ev_pending)
     for (int i = 0; i <= ST_COUNT; ++i)
       if (se.e[i]) cudaEventDestroy(se.e[i]);
@@ -894,8 +910,8 @@ int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, do
     if (ln.fused_multi) {   // the per-trial passes the plan will run
       if (ce == cudaSuccess) ce = launch_inv_rows_chirp(g, ln.bufB[0], ln.bufA[0], ln.tw3L, ln.stwJ, anc, clog, h->st);
       if (ce == cudaSuccess)
-        ce = launch_inv_cols_det(g, ln.bufA[0], ln.P[0], ln.part[0], ln.cnt[0], nullptr, 0, 0, (int)g.n_past,
-                                 (int)(g.n_past + nv), ln.stwR2, h->st);
+        ce = launch_ic(h, ln, ln.bufA[0], ln.P[0], ln.part[0], ln.cnt[0], nullptr, 0, 0, (int)g.n_past,
+                       (int)(g.n_past + nv), h->st);
     } else {
       if (ce == cudaSuccess) ce = launch_inv_cols(g, ln.bufB[0], ln.bufA[0], anc, clog, ln.stwQ2, h->st);
       if (ce == cudaSuccess)
@@ -1047,8 +1063,8 @@ int time_trials(pond_t h, Lane* ln, int mode, int kt, double* us) {
         const Trial& t = h->trials[ln->trials[q]];
         ce = launch_inv_rows_chirp(g, ln->bufB[0], ln->bufA[0], ln->tw3L, ln->stwJ, t.anc, t.clog, h->st);
         if (ce == cudaSuccess)
-          ce = launch_inv_cols_det(g, ln->bufA[0], ln->P[0], ln->part[0], ln->cnt[0], nullptr, 0, 0, (int)m_lo,
-                                   (int)m_hi, ln->stwR2, h->st);
+          ce = launch_ic(h, *ln, ln->bufA[0], ln->P[0], ln->part[0], ln->cnt[0], nullptr, 0, 0, (int)m_lo, (int)m_hi,
+                         h->st);
         if (ce == cudaSuccess)
           ce = launch_decimate(ln->P[0], nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
                                h->ts + (size_t)ln->trials[q] * h->ring, h->ts_cnt + (size_t)ln->trials[q] * h->ring,
@@ -1059,8 +1075,8 @@ int time_trials(pond_t h, Lane* ln, int mode, int kt, double* us) {
       ce = launch_inv_rows_chirp_multi(g, ln->bufB[0], ln->bufT[0], nq, ln->tw3L, ln->stwJ, mc,
                                        mode == POND_TRIALS_MULTI_TABLE, h->st);
       if (ce == cudaSuccess)
-        ce = launch_inv_cols_det(g, ln->bufT[0], ln->Pm[0], ln->partm[0], ln->cntm[0], nullptr, 0, 0, (int)m_lo,
-                                 (int)m_hi, ln->stwR2, h->st, nq);
+        ce = launch_ic(h, *ln, ln->bufT[0], ln->Pm[0], ln->partm[0], ln->cntm[0], nullptr, 0, 0, (int)m_lo, (int)m_hi,
+                       h->st, nq);
       if (ce == cudaSuccess && h->dec_num < 64 * h->dec_den)
         ce = launch_decimate_multi(ln->Pm[0], g.M, nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1, h->ts,
                                    h->ts_cnt, h->ring, ln->d_rows, nq, h->st);
@@ -1267,6 +1283,10 @@ int plan_impl(pond_t* out, const pond_opts* o) {
     CKD(cudaMalloc(&h->tc_err, sizeof(int)));
     CKD(cudaMemcpy(h->wdft, w.data(), 2 * TC_W_BYTES, cudaMemcpyHostToDevice));
     CKD(cudaMemset(h->tc_err, 0, sizeof(int)));
+    std::vector<unsigned char> icops(ic_tc_ops_bytes());
+    build_ic_tc_ops(icops.data());
+    CKD(cudaMalloc(&h->ic_ops, icops.size()));
+    CKD(cudaMemcpy(h->ic_ops, icops.data(), icops.size(), cudaMemcpyHostToDevice));
   }
   CKD(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
   CKD(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));

@@ -4,10 +4,33 @@
 #include <cstring>
 
 #include "passes.cuh"
+#include "tc_cols.cuh"
 
 namespace pond {
 
-cudaError_t set_kernel_attributes_tc() { return set_attributes_t<true>(); }
+cudaError_t set_kernel_attributes_tc() {
+  cudaError_t e = set_attributes_t<true>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_inv_cols_det_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tcc::SMEM_BYTES);
+  return e;
+}
+
+bool ic_tc_geometry(const Geom& g) { return fused_geometry(g) && g.logR2 == 11 && g.nchan >= 4; }
+
+cudaError_t launch_inv_cols_det_tc(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
+                                   long long vstride, long long vofs, int m_lo, int m_hi, const uint4* ops, int* err,
+                                   cudaStream_t st, int ntr) {
+  if (!ic_tc_geometry(g)) return cudaErrorInvalidValue;
+  const int nl = 4;
+  const dim3 grid((unsigned)((1 << g.logR1) / nl), (unsigned)ntr);
+  const float scale = 1.0f / (float)(1u << g.logM);
+  const int lognch = g.logR1 - (g.logM - g.logR2);
+  const TrialStride ts = ntr > 1 ? TrialStride{g.L, g.M, (long long)fused_groups(g) * g.M, FUSED_J}
+                                 : TrialStride{0, 0, 0, 0};
+  k_inv_cols_det_tc<<<grid, NT, tcc::SMEM_BYTES, st>>>(in, P, part, cnt, vout, vstride, vofs, lognch, m_lo, m_hi,
+                                                       scale, ops, err, ts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fwd_cols_tc(const Geom& g, SegIn in, float2* out, const float2* tw, cudaStream_t st) {
   return launch_fwd_cols_t<true>(g, in, out, tw, st);
@@ -97,5 +120,49 @@ void build_w16_parts(uint16_t* out) {
       }
   }
 }
+
+// Operand block of the tensor-core column pass (tc_cols.cuh): the cosine and
+// sine matrices of the 64- and 32-point inverse factors, e^{+2 pi i b p / 64}
+// and e^{+2 pi i a q / 32}, rows = output index, K = input index, each split
+// into BF16 hi + mid parts in the K-major operand layout, then the twiddle
+// tables T0[i] = e^{2 pi i i / 2048} (i < 64) and T1[j] = e^{2 pi i 64 j / 2048}
+// (j < 32) as FP32 pairs.  Built in FP64.
+void build_ic_tc_ops(unsigned char* out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  std::memset(out, 0, tcc::OPS_BYTES);
+  auto put = [&](int off_part, int off_elem, double v, int part) {
+    uint16_t h = bf16_bits(v);
+    if (part == 1) h = bf16_bits(v - bf16_value(h));
+    std::memcpy(out + off_part + off_elem, &h, 2);
+  };
+  for (int n = 0; n < 64; ++n)
+    for (int k = 0; k < 64; ++k) {
+      const double th = two_pi * (double)((n * k) & 63) / 64.0;
+      const int o = tcc::off_k64(n, k);
+      put(tcc::OFF_C64_HI, o, std::cos(th), 0);
+      put(tcc::OFF_C64_MID, o, std::cos(th), 1);
+      put(tcc::OFF_S64_HI, o, std::sin(th), 0);
+      put(tcc::OFF_S64_MID, o, std::sin(th), 1);
+    }
+  for (int n = 0; n < 32; ++n)
+    for (int k = 0; k < 32; ++k) {
+      const double th = two_pi * (double)((n * k) & 31) / 32.0;
+      const int o = tcc::off_k32(n, k);
+      put(tcc::OFF_C32_HI, o, std::cos(th), 0);
+      put(tcc::OFF_C32_MID, o, std::cos(th), 1);
+      put(tcc::OFF_S32_HI, o, std::sin(th), 0);
+      put(tcc::OFF_S32_MID, o, std::sin(th), 1);
+    }
+  for (int i = 0; i < 64; ++i) {
+    const float v[2] = {(float)std::cos(two_pi * i / 2048.0), (float)std::sin(two_pi * i / 2048.0)};
+    std::memcpy(out + tcc::OFF_T0 + 8 * i, v, 8);
+  }
+  for (int j = 0; j < 32; ++j) {
+    const float v[2] = {(float)std::cos(two_pi * 64 * j / 2048.0), (float)std::sin(two_pi * 64 * j / 2048.0)};
+    std::memcpy(out + tcc::OFF_T1 + 8 * j, v, 8);
+  }
+}
+
+int ic_tc_ops_bytes() { return tcc::OPS_BYTES; }
 
 }  // namespace pond

@@ -137,6 +137,16 @@ cudaError_t launch_inv_cols_det(const Geom& g, const float2* in, float* P, float
 // the chirp from the lane's Q0.32 table (table = true) or each trial's anchors
 cudaError_t launch_inv_rows_chirp_multi(const Geom& g, const float2* in, float2* out, int ntr, const float2* tw3L,
                                         const float2* twJ, MultiChirp mc, bool table, cudaStream_t st);
+// Tensor-core column pass (split-BF16, three terms) for R2 = 2048 and at least
+// four sub-channels: same outputs and arguments as launch_inv_cols_det, plus
+// its operand block (build_ic_tc_ops, ic_tc_ops_bytes() bytes on the device)
+// and the plan's MMA-wait error flag.
+bool ic_tc_geometry(const Geom& g);
+cudaError_t launch_inv_cols_det_tc(const Geom& g, const float2* in, float* P, float* part, int* cnt, float2* vout,
+                                   long long vstride, long long vofs, int m_lo, int m_hi, const uint4* ops, int* err,
+                                   cudaStream_t st, int ntr = 1);
+void build_ic_tc_ops(unsigned char* out);
+int ic_tc_ops_bytes();
 cudaError_t launch_chirp_table(unsigned* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
                                cudaStream_t st);
 cudaError_t launch_decimate_multi(const float* P, long long pstride, long long n, long long g0, long long num,

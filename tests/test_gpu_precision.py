@@ -75,6 +75,8 @@ CONFIGS = [
     (1 << 20, 8, 2.0, -16.0, 512, 0.1),
     (1 << 15, 512, 0.0, 16.0, 32, 0.02),
     (1 << 24, 64, 1.0, 16.0, 1024, 0.25),
+    # three-pass with the tensor-core column pass (R2 = 2048): 8 sub-channel groups, inverted band
+    (1 << 23, 32, 3.0, -16.0, 512, 0.11),
 ]
 
 
@@ -150,3 +152,27 @@ def test_precision_batched_trials(prec):
     for d, r in enumerate(res):
         assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
         assert rel(T[d], r.ts) <= TOL_P, (d, rel(T[d], r.ts))
+
+
+def test_tensor_core_column_pass_three_pass_batched():
+    """Batched trials in the three-pass geometry (nfft 2^23, 32 sub-channels,
+    R2 = 2048) with three-term split-BF16 stages: the forward passes' radix-16
+    stages and the column pass's two DFT-matrix factors run on the tensor
+    cores, the row pass with each trial's chirp in FP32; every trial against
+    the oracle, for several trials per launch and for per-trial launches."""
+    dms = [0.0, 1.0, 2.0, 3.0, 4.0]
+    nfft, nchan, t_dec = 1 << 23, 32, 16e-6
+    p = pcd.make_plan(326.5, 16.0, 32e6, max(dms), nfft, nchan, 1, 1.0, t_dec)
+    x = synth.make_stream(synth.StreamSpec(n=2 * p.S + nfft + 4321, seed=43, dm=2.0, period=0.011, snr=80.0,
+                                           duty=0.05))
+    base = pcd.make_plan(326.5, 16.0, 32e6, 0.0, nfft, nchan, 1, 1.0, t_dec)
+    res = pcd.run_batched(base, [(dm, nfft, max(dms)) for dm in dms], x)
+    for mode in (pond.POND_TRIALS_MULTI_TABLE, pond.POND_TRIALS_PER_TRIAL):
+        with pond.Engine(326.5, 16.0, 32e6, 0.0, nfft, nchan, 1, 1.0, t_dec=t_dec, dms=dms,
+                         precision=pond.POND_SPLIT_BF16, trial_mode=mode, trials_per_launch=3) as e:
+            e.push(x)
+            e.flush()
+            T, C, j0 = e.timeseries()
+        for d, r in enumerate(res):
+            assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+            assert rel(T[d], r.ts) <= TOL_P, (mode, d, rel(T[d], r.ts))
