@@ -8,16 +8,21 @@
 //   Linear(32 -> 4) and softmax (classes: dispersed pulse, broadband RFI,
 //   narrowband RFI, noise),
 // with BF16 weights and activations, FP32 accumulation, FP32 master weights
-// and Adam.  Training minimises the mean cross-entropy of a batch.
+// and Adam.  Training minimises the mean cross-entropy of a batch.  Training's
+// forward and backward passes run on the FP32 pipes (they keep the layers'
+// pre-activations for the backward pass); inference (pond_cnn_forward) runs
+// the three convolutions as implicit GEMMs on the tensor cores (cnn_tc.cuh).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
 
 #include "../../include/pond.h"
 #include "cnn_kernels.cuh"
+#include "cnn_tc.cuh"
 #include "pond_internal.h"
 
 using namespace pond::cnn;
@@ -33,6 +38,9 @@ struct pond_cnn_s {
   uint8_t *a1 = nullptr, *a2 = nullptr;
   float *gap = nullptr, *prob = nullptr, *loss = nullptr, *dg = nullptr, *lmean = nullptr;
   float *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr, *part = nullptr;
+  unsigned char* wtc = nullptr;   // the conv weights in the tensor-core operand layout
+  int* tc_err = nullptr;          // set when a tensor-core MMA wait gave up
+  int sms = 0;
 };
 
 namespace {
@@ -68,14 +76,22 @@ cudaError_t set_attrs() {
                              (int)fwd_smem<128, 0>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_conv_bwd_data<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<64, 0>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cnn_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   return e;
+}
+
+// Refresh the tensor-core copy of the conv weights from the BF16 master copy.
+cudaError_t refresh_wtc(pond_cnn_t n, cudaStream_t st) {
+  k_cnn_tc_weights<<<(3 * CONV + 255) / 256, 256, 0, st>>>(n->wbf, n->wtc);
+  return cudaGetLastError();
 }
 
 void free_net(pond_cnn_t n) {
   for (void* p : {(void*)n->theta, (void*)n->m, (void*)n->v, (void*)n->grad, (void*)n->wbf, (void*)n->z1,
                   (void*)n->z2, (void*)n->z3, (void*)n->h1, (void*)n->h2, (void*)n->a1, (void*)n->a2,
                   (void*)n->gap, (void*)n->prob, (void*)n->loss, (void*)n->dg, (void*)n->lmean, (void*)n->dz3,
-                  (void*)n->dz2, (void*)n->dz1, (void*)n->part})
+                  (void*)n->dz2, (void*)n->dz1, (void*)n->part, (void*)n->wtc, (void*)n->tc_err})
     cudaFree(p);
   delete n;
 }
@@ -91,6 +107,7 @@ int load_params(pond_cnn_t n, const float* params) {
   CKC(cudaGetLastError());
   CKC(cudaMemset(n->m, 0, NPARAM * sizeof(float)));
   CKC(cudaMemset(n->v, 0, NPARAM * sizeof(float)));
+  CKC(refresh_wtc(n, 0));
   CKC(cudaDeviceSynchronize());
   n->step = 0;
   return POND_OK;
@@ -176,6 +193,10 @@ int pond_cnn_create(pond_cnn_t* out, const float* init_params, int32_t max_batch
   A(&n->dz2, B * C * 128 * 4);
   A(&n->dz1, B * C * 256 * 4);
   A(&n->part, B * NPARAM * 4);
+  A(&n->wtc, WTC_BYTES);
+  A(&n->tc_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->tc_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = set_attrs();
   if (e != cudaSuccess) {
     free_net(n);
@@ -201,6 +222,12 @@ int pond_cnn_params(pond_cnn_t n, float* out) {
   CKC(cudaSetDevice(n->device));
   CKC(cudaDeviceSynchronize());
   CKC(cudaMemcpy(out, n->theta, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+  int te = 0;
+  CKC(cudaMemcpy(&te, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (te) {
+    CKC(cudaMemset(n->tc_err, 0, sizeof(int)));
+    return pond::set_error(POND_E_TIMEOUT, "a tensor-core MMA wait of the inference kernel expired");
+  }
   return POND_OK;
 }
 
@@ -210,6 +237,15 @@ int pond_cnn_forward(pond_cnn_t n, const void* d_x, int32_t batch, float* d_prob
   if (!d_prob) return pond::set_error(POND_E_ARG, "pond_cnn_forward: null output");
   CKC(cudaSetDevice(n->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((uintptr_t)d_x % 16 == 0) {
+    // the tensor-core inference kernel: each CTA runs samples blockIdx.x, + gridDim.x, ...
+    const int grid = std::min(batch, 2 * n->sms);
+    k_cnn_infer_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(static_cast<const __nv_bfloat16*>(d_x), batch, n->wtc,
+                                                      n->theta, n->wbf, d_prob, n->tc_err);
+    CKC(cudaGetLastError());
+    return POND_OK;
+  }
+  // patches not 16-byte aligned: the FP32-pipe forward
   rc = forward(n, static_cast<const __nv_bfloat16*>(d_x), batch, nullptr, st);
   if (rc) return rc;
   CKC(cudaMemcpyAsync(d_prob, n->prob, (size_t)batch * NCLS * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -248,6 +284,7 @@ int pond_cnn_train_step(pond_cnn_t n, const void* d_x, const int32_t* d_labels, 
   const float c2 = 1.f - (float)std::pow((double)b2, (double)n->step);
   k_adam<<<(NPARAM + 255) / 256, 256, 0, st>>>(n->theta, n->m, n->v, n->grad, n->wbf, lr, c1, c2, b1, b2, 1e-8f);
   CKC(cudaGetLastError());
+  CKC(refresh_wtc(n, st));
   if (loss_out) {
     CKC(cudaMemcpyAsync(loss_out, n->lmean, sizeof(float), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));

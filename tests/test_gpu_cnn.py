@@ -130,3 +130,42 @@ def test_training_learns_a_separable_task():
     acc = float((net.forward(xt).argmax(1).cpu().numpy() == y).mean())
     net.close()
     assert last < 0.5 * first and acc > 0.9, (first, last, acc)
+
+
+def oracle_prob(th, x):
+    logits, _ = cnn.forward(th, x)
+    z = np.exp(logits - logits.max(axis=1, keepdims=True))
+    return z / z.sum(axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("B", [1, 5, 333, 700])
+def test_tensor_core_inference_matches_oracle(B):
+    """pond_cnn_forward runs the convolutions as implicit GEMMs on the tensor
+    cores (several samples per CTA when the batch exceeds two CTAs per SM):
+    probabilities against the FP64 oracle on the same BF16 weights and inputs,
+    for batches of one sample, a few, and more than the grid."""
+    theta, xt, y, yt = setup(B, 7 + B)
+    net = pond.Classifier(theta, max_batch=B)
+    prob = net.forward(xt).cpu().numpy()
+    net.close()
+    xo = xt.float().cpu().numpy().astype(np.float64)
+    th = gpu_weights_view(theta)
+    po = np.concatenate([oracle_prob(th, xo[i:i + 1]) for i in range(0, B, max(1, B // 40))])
+    pg = prob[::max(1, B // 40)]
+    assert np.all(np.isfinite(prob)) and np.allclose(prob.sum(1), 1.0, atol=1e-5)
+    assert np.max(np.abs(pg - po)) < 1e-2, np.max(np.abs(pg - po))
+
+
+def test_tensor_core_inference_follows_training():
+    """After Adam steps the inference kernel uses the updated weights: its
+    probabilities agree with the oracle's forward of the trained parameters."""
+    theta, xt, y, yt = setup(16, 21)
+    net = pond.Classifier(theta, max_batch=16)
+    for _ in range(5):
+        net.train_step(xt, yt, 1e-2)
+    th_new = net.params()
+    prob = net.forward(xt).cpu().numpy()
+    net.close()
+    xo = xt.float().cpu().numpy().astype(np.float64)
+    po = oracle_prob(gpu_weights_view(th_new), xo)
+    assert np.max(np.abs(prob - po)) < 1e-2, np.max(np.abs(prob - po))
