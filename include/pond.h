@@ -203,6 +203,8 @@ typedef struct {
                                      multiply (Eq. 4), 4 per detected channel sample
                                      (|v|^2 and the sub-channel sum), 1 per sample for the
                                      in-phase sum of two halves, fold and decimation */
+  double push_enqueue_ms;   /* host time of the last pond_push spent enqueueing copies and passes */
+  double push_wait_ms;      /* host time of the last pond_push spent waiting for its last copy */
 } pond_stats_t;
 
 /*

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -64,6 +65,7 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr double K_DM = 1.0 / 2.41e-4;          // s MHz^2 (Eq. 1 constant)
 constexpr long long STAGE_BYTES = 128ll << 20;  // host-push staging chunk
+constexpr int NSTAGE = 2;                        // staging buffers: copies run up to one piece ahead
 constexpr long long FIRST_STAGE_BYTES = 32ll << 20;  // first piece of a stream's host push
 constexpr long long TS_RING_SINGLE = 1ll << 22; // time-series samples held on the device (one trial)
 constexpr long long TS_RING_MULTI = 1ll << 19;  // ... per trial of a batched plan
@@ -180,10 +182,10 @@ struct pond_s {
   cudaStream_t sx[NSLOT] = {};
   cudaEvent_t ev_in = nullptr, ev_join[NSLOT] = {};
   cudaEvent_t ev_done = nullptr, ev_caller = nullptr;
-  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  cudaEvent_t ev_copied[NSTAGE] = {}, ev_used[NSTAGE] = {};
   // side-stream work of the last two ingests (carry reuse) and of the segments
   // that read each staging buffer (staging reuse)
-  cudaEvent_t ev_side[2][NSLOT] = {}, ev_used_x[2][NSLOT] = {};
+  cudaEvent_t ev_side[2][NSLOT] = {}, ev_used_x[NSTAGE][NSLOT] = {};
   int ingest_par = 0;
   // single-DM plans fold on their own stream: a segment's fold waits for its
   // detection (ev_pready), the next detection into the same P for the fold
@@ -200,7 +202,7 @@ struct pond_s {
   float* ts = nullptr;
   int* ts_cnt = nullptr;
   // host-push staging
-  int8_t* stage[2] = {nullptr, nullptr};
+  int8_t* stage[NSTAGE] = {};
   int stage_next = 0;
   // voltages (single-DM plans, tests)
   float2* vbuf = nullptr;
@@ -226,6 +228,7 @@ struct pond_s {
   double stage_ms[POND_NSTAGE] = {0};
   long long stage_launches[POND_NSTAGE] = {0};
   long long launches = 0;
+  double push_enqueue_ms = 0, push_wait_ms = 0;   // host times of the last pond_push
   // split-BF16 tensor-core stages: product terms (0 = FP32), W16 parts, MMA wait flag
   int tc_terms = 0;
   uint4* wdft = nullptr;
@@ -762,14 +765,16 @@ int ingest_device(pond_t h, const int8_t* d, long long n) {
     Lane& ln = h->lanes[li];
     // keep [seg_start, end) for the lane's next segment
     int8_t* dst = ln.carry[1 - ln.carry_cur];
+    // the carry is rewritten by a kernel, not a copy engine, so the copy engines
+    // carry only the host pushes' pieces
     if (ln.seg_start < h->total_in) {
       const long long old = h->total_in - ln.seg_start;
-      CK(cudaMemcpyAsync(dst, ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos) * ch, old * ch,
-                         cudaMemcpyDeviceToDevice, h->st));
-      if (n > 0) CK(cudaMemcpyAsync(dst + old * ch, d, n * ch, cudaMemcpyDeviceToDevice, h->st));
+      CK(launch_copy_bytes(dst, ln.carry[ln.carry_cur] + (ln.seg_start - ln.carry_pos) * ch, old * ch, h->st));
+      if (n > 0) CK(launch_copy_bytes(dst + old * ch, d, n * ch, h->st));
+      h->launches += 1 + (n > 0 && old > 0);
     } else if (end > ln.seg_start) {
-      CK(cudaMemcpyAsync(dst, d + (ln.seg_start - h->total_in) * ch, (end - ln.seg_start) * ch,
-                         cudaMemcpyDeviceToDevice, h->st));
+      CK(launch_copy_bytes(dst, d + (ln.seg_start - h->total_in) * ch, (end - ln.seg_start) * ch, h->st));
+      h->launches += 1;
     }
     ln.carry_cur = 1 - ln.carry_cur;
     ln.carry_pos = ln.seg_start;
@@ -808,8 +813,7 @@ void destroy_all(pond_t h) {
   cudaFree(h->ts);
   cudaFree(h->ts_cnt);
   if (h->ts_pin) cudaFreeHost(h->ts_pin);
-  cudaFree(h->stage[0]);
-  cudaFree(h->stage[1]);
+  for (int i = 0; i < NSTAGE; ++i) cudaFree(h->stage[i]);
   cudaFree(h->vbuf);
   cudaFree(h->wdft);
   cudaFree(h->tc_err);
@@ -818,7 +822,7 @@ void destroy_all(pond_t h) {
     for (int i = 0; i <= ST_COUNT; ++i)
       if (se.e[i]) cudaEventDestroy(se.e[i]);
   for (auto e : h->ev_pool) cudaEventDestroy(e);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < NSTAGE; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
   }
@@ -834,10 +838,10 @@ void destroy_all(pond_t h) {
   if (h->st) cudaStreamDestroy(h->st);
   for (int k = 1; k < NSLOT; ++k) {
     if (h->ev_join[k]) cudaEventDestroy(h->ev_join[k]);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 2; ++i)
       if (h->ev_side[i][k]) cudaEventDestroy(h->ev_side[i][k]);
+    for (int i = 0; i < NSTAGE; ++i)
       if (h->ev_used_x[i][k]) cudaEventDestroy(h->ev_used_x[i][k]);
-    }
     if (h->sx[k]) cudaStreamDestroy(h->sx[k]);
   }
   if (h->cst) cudaStreamDestroy(h->cst);
@@ -1293,10 +1297,8 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   for (int k = 1; k < NSLOT; ++k) {
     CKD(cudaStreamCreateWithFlags(&h->sx[k], cudaStreamNonBlocking));
     CKD(cudaEventCreateWithFlags(&h->ev_join[k], cudaEventDisableTiming));
-    for (int i = 0; i < 2; ++i) {
-      CKD(cudaEventCreateWithFlags(&h->ev_side[i][k], cudaEventDisableTiming));
-      CKD(cudaEventCreateWithFlags(&h->ev_used_x[i][k], cudaEventDisableTiming));
-    }
+    for (int i = 0; i < 2; ++i) CKD(cudaEventCreateWithFlags(&h->ev_side[i][k], cudaEventDisableTiming));
+    for (int i = 0; i < NSTAGE; ++i) CKD(cudaEventCreateWithFlags(&h->ev_used_x[i][k], cudaEventDisableTiming));
   }
   CKD(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
   CKD(cudaStreamCreateWithFlags(&h->sf, cudaStreamNonBlocking));
@@ -1307,7 +1309,7 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   }
   CKD(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
   CKD(cudaEventCreateWithFlags(&h->ev_caller, cudaEventDisableTiming));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < NSTAGE; ++i) {
     CKD(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
     CKD(cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming));
   }
@@ -1447,18 +1449,20 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
   if (n % h->ch) return fail(POND_E_ARG, "push of %zu bytes splits an N / S sample pair", n);
   CK(cudaSetDevice(h->device));
   if (!h->stage[0]) {
-    CK(cudaMalloc(&h->stage[0], STAGE_BYTES));
-    CK(cudaMalloc(&h->stage[1], STAGE_BYTES));
-    CK(cudaEventRecord(h->ev_used[0], h->st));
-    CK(cudaEventRecord(h->ev_used[1], h->st));
+    for (int i = 0; i < NSTAGE; ++i) {
+      CK(cudaMalloc(&h->stage[i], STAGE_BYTES));
+      CK(cudaEventRecord(h->ev_used[i], h->st));
+      for (int k = 1; k < NSLOT; ++k) CK(cudaEventRecord(h->ev_used_x[i][k], h->sx[k]));
+    }
   }
   cudaEvent_t last = nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
   for (size_t off = 0; off < n;) {
     // a short first piece of a stream lets the passes start while the rest is copied
     const long long cap = (h->total_in == 0 && off == 0) ? FIRST_STAGE_BYTES : STAGE_BYTES;
     const long long len = std::min<long long>(cap, (long long)(n - off));
     const int i = h->stage_next;
-    h->stage_next ^= 1;
+    h->stage_next = (h->stage_next + 1) % NSTAGE;
     CK(cudaStreamWaitEvent(h->cst, h->ev_used[i], 0));
     for (int k = 1; k < NSLOT; ++k) CK(cudaStreamWaitEvent(h->cst, h->ev_used_x[i][k], 0));
     CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
@@ -1471,7 +1475,11 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     off += (size_t)len;
   }
   // the caller's buffer is free once the copies have landed
+  const auto t_enq = std::chrono::steady_clock::now();
   if (last) CK(cudaEventSynchronize(last));
+  const auto t_end = std::chrono::steady_clock::now();
+  h->push_enqueue_ms = std::chrono::duration<double, std::milli>(t_enq - t_start).count();
+  h->push_wait_ms = std::chrono::duration<double, std::milli>(t_end - t_enq).count();
   return POND_OK;
 }
 
@@ -1809,6 +1817,8 @@ int pond_stats(pond_t h, pond_stats_t* s) {
   s->algo_flops[ST_IC] = 5 * L * g.logR2 + detect;
   s->algo_flops[ST_FOLD] = nv;
   s->algo_flops[ST_DEC] = nv;
+  s->push_enqueue_ms = h->push_enqueue_ms;
+  s->push_wait_ms = h->push_wait_ms;
   for (int i = 0; i < POND_NSTAGE; ++i) {
     s->stage_ms[i] = h->stage_ms[i];
     s->stage_launches[i] = h->stage_launches[i];

@@ -504,9 +504,32 @@ __global__ void k_make_chirp_c64(float2* tab, int logR1, int logR2, double du, d
   tab[i] = make_float2((float)cs, (float)-sn);
 }
 
+// Byte copy between device buffers (any alignment): 16-byte words where both
+// sides allow, single bytes otherwise.
+__global__ void k_copy_bytes(int8_t* __restrict__ dst, const int8_t* __restrict__ src, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const long long n16 = n >> 4;
+    for (long long i = i0; i < n16; i += stride)
+      reinterpret_cast<uint4*>(dst)[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+    for (long long i = (n16 << 4) + i0; i < n; i += stride) dst[i] = src[i];
+  } else {
+    for (long long i = i0; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_copy_bytes(int8_t* dst, const int8_t* src, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long words = std::max(1ll, n >> 4);
+  const unsigned blocks = (unsigned)std::min<long long>((words + 255) / 256, 2048);
+  k_copy_bytes<<<blocks, 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_chirp_c64(float2* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
                              cudaStream_t st) {

@@ -341,16 +341,21 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det_tc(const float2* __restr
     tc::tmem_dealloc(tmem, TMEM_COLS);
   }
   if (logG == 0) return;
-  __threadfence();
+  // release: the barrier orders every thread's partials before thread 0's fence
+  // and ticket; acquire: the last group's thread 0 fences after its ticket and
+  // the barrier orders the CTA's L2 loads of the other groups' partials after it
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const int t = atomicAdd(cnt + m1, 1);
     s_last = t == (1 << logG) - 1;
-    if (s_last) cnt[m1] = 0;   // every group has taken its ticket
+    if (s_last) {
+      cnt[m1] = 0;   // every group has taken its ticket
+      __threadfence();
+    }
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // the G partials of an output are loaded together, then added in group order
   constexpr int GMAX = 16;
   constexpr int MPT = IC_R2 / NT;

@@ -111,7 +111,8 @@ class pond_stats_t(ctypes.Structure):
                 ("stage_launches", ctypes.c_int64 * POND_NSTAGE),
                 ("pass_bytes", ctypes.c_double * POND_NSTAGE),
                 ("stage_name", ctypes.c_char_p * POND_NSTAGE),
-                ("algo_flops", ctypes.c_double * POND_NSTAGE)]
+                ("algo_flops", ctypes.c_double * POND_NSTAGE), ("push_enqueue_ms", ctypes.c_double),
+                ("push_wait_ms", ctypes.c_double)]
 
 
 _lib = None

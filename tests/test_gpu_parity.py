@@ -132,8 +132,9 @@ def test_three_pass_schedule(cfg):
     else:
         x = _stream(p, seed=nfft + 3, extra=29)
     r = pcd.run(p, x, want_voltages=True)
-    three = run_engine(x, p, chunks=[len(x) // 3, len(x) - len(x) // 3])
-    four = run_engine(x, p, schedule=pond.POND_SCHEDULE_FOUR_PASS)
+    chunks = [len(x) // 3, len(x) - len(x) // 3]
+    three = run_engine(x, p, chunks=chunks)
+    four = run_engine(x, p, chunks=chunks, schedule=pond.POND_SCHEDULE_FOUR_PASS)
     check(three, r)
     check(four, r)
     # the fused row pass with its chirp read from the per-bin table instead of the anchors
@@ -141,7 +142,8 @@ def test_three_pass_schedule(cfg):
     check(run_engine(x, p, chirp=pond.POND_CHIRP_ANCHORS), r)
     segs = three["stats"]["segments"]
     assert segs == four["stats"]["segments"] and segs >= 2
-    assert three["stats"]["kernel_launches"] * 5 == four["stats"]["kernel_launches"] * 4
+    # one pass fewer per segment (the pushes' carry copies are the same in both)
+    assert four["stats"]["kernel_launches"] - three["stats"]["kernel_launches"] == segs
 
 
 @pytest.mark.parametrize("cfg", [(1 << 16, 16, 0.3, 16.0, 128, 0.033), (1 << 18, 8, 1.0, 16.0, 128, 0.03),
