@@ -71,11 +71,13 @@ __device__ __forceinline__ void load_real4(const FbArgs& a, long long q, float (
   }
 }
 
-// One CTA per SM: with the pass loop around the stages, their per-thread
-// indices stay live across passes and need more than the 64 registers that two
-// 512-thread CTAs per SM allow (at 64 the kernel spills).
-template <int R>
-__global__ void __launch_bounds__(NT, 1) k_fb_power(FbArgs a, const float2* __restrict__ tw) {
+// ONE = false: one CTA per SM: with the pass loop around the stages, their
+// per-thread indices stay live across passes and need more than the 64
+// registers that two 512-thread CTAs per SM allow (at 64 the kernel spills).
+// ONE = true (a CTA's spectra fit one tile pass, as with nint = 1): no pass
+// loop and no running sums across passes, two CTAs per SM.
+template <int R, bool ONE>
+__global__ void __launch_bounds__(NT, ONE ? 2 : 1) k_fb_power(FbArgs a, const float2* __restrict__ tw) {
   constexpr int NCH = R / 2;
   constexpr int NL = TILE / R;                 // lines per pass
   constexpr int LSTR = line_stride(R);
@@ -92,7 +94,8 @@ __global__ void __launch_bounds__(NT, 1) k_fb_power(FbArgs a, const float2* __re
   const int spl = a.form == FB_CID ? 1 : 2;    // spectra per line
   const long long s0 = (long long)blockIdx.x * a.s_cta;
   const int len = (int)min(a.s_cta, a.n_spec - s0);   // spectra of this CTA
-  for (int k = threadIdx.x; k < NCH; k += NT) acc[k] = 0.f;
+  if (!ONE)
+    for (int k = threadIdx.x; k < NCH; k += NT) acc[k] = 0.f;
   for (int p = 0; p < len; p += spl * NL) {
     // load: line l holds spectra s0 + p + spl l (+ 1)
 #pragma unroll
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) k_fb_power(FbArgs a, const float2* __re
     for (int u = 0; u < KPT; ++u) {
       const int k = (int)threadIdx.x + u * NT;
       if (k < NCH) {
-        float s = acc[k];
+        float s = ONE ? 0.f : acc[k];
         for (int l = 0; l < NL; ++l) {
           const int r = p + spl * l;
           if (r >= len) break;
@@ -153,9 +156,10 @@ __global__ void __launch_bounds__(NT, 1) k_fb_power(FbArgs a, const float2* __re
             }
           }
         }
-        acc[k] = s;
+        if (!ONE) acc[k] = s;
       }
     }
+    if (ONE) break;    // the CTA's spectra fit one pass
     __syncthreads();   // the next pass's loads overwrite the tile
   }
 }
@@ -333,14 +337,22 @@ double rounded(double x) {
 
 template <int R>
 cudaError_t fb_attr() {
-  return cudaFuncSetAttribute(pond::k_fb_power<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)pond::fb_smem_bytes<R>());
+  cudaError_t e = cudaFuncSetAttribute(pond::k_fb_power<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pond::fb_smem_bytes<R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pond::k_fb_power<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pond::fb_smem_bytes<R>());
+  return e;
 }
 
 template <int R>
 cudaError_t fb_launch(const FbArgs& a, const float2* tw, cudaStream_t st) {
   const long long blocks = (a.n_spec + a.s_cta - 1) / a.s_cta;
-  pond::k_fb_power<R><<<(unsigned)blocks, pond::NT, pond::fb_smem_bytes<R>(), st>>>(a, tw);
+  const long long per_pass = (long long)(a.form == pond::FB_CID ? 1 : 2) * (pond::TILE / R);
+  if (a.s_cta <= per_pass)
+    pond::k_fb_power<R, true><<<(unsigned)blocks, pond::NT, pond::fb_smem_bytes<R>(), st>>>(a, tw);
+  else
+    pond::k_fb_power<R, false><<<(unsigned)blocks, pond::NT, pond::fb_smem_bytes<R>(), st>>>(a, tw);
   return cudaGetLastError();
 }
 
