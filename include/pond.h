@@ -233,7 +233,10 @@ int pond_plan_ex(pond_t* out, const pond_opts* opts);
  *   the input of the paper's GPU flow (Sec. 3.7, Fig. "gpuflow": the digitised
  *   voltages held on the host are sent to the device's global memory; Sec. 3.1:
  *   the ADC delivers 8-bit real samples of each half of the band).  The data
- *   are copied to the device before the call returns (pinned memory copies
+ *   move to the device in pieces of 128 MiB through two staging buffers while
+ *   the passes run: page-locked (pinned, device-mapped) memory by a copy kernel
+ *   on 8 CTAs that reads it over the host link, pageable memory by the copy
+ *   engines.  The data are copied to the device before the call returns (pinned memory copies
  *   asynchronously, pageable memory through the driver's staging), so x may be
  *   reused at once; processing of complete segments continues asynchronously.
  *   Errors: POND_E_ARG (x NULL with n > 0), POND_E_STATE (after pond_flush),

@@ -1457,6 +1457,18 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
   }
   cudaEvent_t last = nullptr;
   const auto t_start = std::chrono::steady_clock::now();
+  // Pinned host memory is addressable from the device: a copy kernel on a few
+  // CTAs moves each piece into its staging buffer.  Copy-engine transfers that
+  // overlap the passes were seen to stall now and then for tens of ms (the
+  // same copies alone do not); the kernel copy, at a small cost in SMs, does not.
+  const int8_t* xdev = nullptr;
+  {
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, x) == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer)
+      xdev = static_cast<const int8_t*>(attr.devicePointer);
+    else
+      cudaGetLastError();
+  }
   for (size_t off = 0; off < n;) {
     // a short first piece of a stream lets the passes start while the rest is copied
     const long long cap = (h->total_in == 0 && off == 0) ? FIRST_STAGE_BYTES : STAGE_BYTES;
@@ -1465,7 +1477,12 @@ int pond_push(pond_t h, const int8_t* x, size_t n) {
     h->stage_next = (h->stage_next + 1) % NSTAGE;
     CK(cudaStreamWaitEvent(h->cst, h->ev_used[i], 0));
     for (int k = 1; k < NSLOT; ++k) CK(cudaStreamWaitEvent(h->cst, h->ev_used_x[i][k], 0));
-    CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
+    if (xdev) {
+      CK(launch_copy_host(h->stage[i], xdev + off, len, 8, h->cst));
+      h->launches += 1;
+    } else {
+      CK(cudaMemcpyAsync(h->stage[i], x + off, len, cudaMemcpyHostToDevice, h->cst));
+    }
     CK(cudaEventRecord(h->ev_copied[i], h->cst));
     CK(cudaStreamWaitEvent(h->st, h->ev_copied[i], 0));
     RC(ingest_device(h, h->stage[i], len / h->ch));

@@ -523,6 +523,31 @@ __global__ void k_copy_bytes(int8_t* __restrict__ dst, const int8_t* __restrict_
 // Host launchers
 // ---------------------------------------------------------------------------
 
+// Host (mapped, pinned) -> device copy by a few CTAs: each thread keeps four
+// 16-byte loads in flight, so 32 CTAs stream host memory at the rate the passes
+// consume it while leaving the other SMs to them.  Both pointers 16-byte aligned.
+__global__ void __launch_bounds__(512) k_copy_host(uint4* __restrict__ dst, const uint4* __restrict__ src,
+                                                    long long n16) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n16; i += 4 * stride) {
+    const uint4 a = __ldcs(src + i), b = __ldcs(src + i + stride), c = __ldcs(src + i + 2 * stride),
+                d = __ldcs(src + i + 3 * stride);
+    dst[i] = a;
+    dst[i + stride] = b;
+    dst[i + 2 * stride] = c;
+    dst[i + 3 * stride] = d;
+  }
+  for (; i < n16; i += stride) dst[i] = __ldcs(src + i);
+}
+
+cudaError_t launch_copy_host(int8_t* dst, const int8_t* src, long long n, int blocks, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (((((uintptr_t)dst | (uintptr_t)src) & 15) != 0) || (n & 15)) return launch_copy_bytes(dst, src, n, st);
+  k_copy_host<<<blocks, 512, 0, st>>>(reinterpret_cast<uint4*>(dst), reinterpret_cast<const uint4*>(src), n >> 4);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copy_bytes(int8_t* dst, const int8_t* src, long long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const long long words = std::max(1ll, n >> 4);

@@ -149,6 +149,8 @@ void build_ic_tc_ops(unsigned char* out);
 int ic_tc_ops_bytes();
 // Device-to-device byte copy as a kernel (the carry rewrite between pushes).
 cudaError_t launch_copy_bytes(int8_t* dst, const int8_t* src, long long n, cudaStream_t st);
+// Host-to-device copy from mapped pinned memory by `blocks` CTAs (the copy engines are not used).
+cudaError_t launch_copy_host(int8_t* dst, const int8_t* src, long long n, int blocks, cudaStream_t st);
 cudaError_t launch_chirp_table(unsigned* tab, const Geom& g, double du, double half, double f0, double alpha, int sgn,
                                cudaStream_t st);
 cudaError_t launch_decimate_multi(const float* P, long long pstride, long long n, long long g0, long long num,
