@@ -30,13 +30,27 @@ __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c
 __host__ __device__ constexpr int line_stride(int R) { return R + R / 16 + 1; }
 __device__ __forceinline__ int pidx(int line, int e, int lstr) { return line * lstr + e + (e >> 4); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex arithmetic on a (re, im) pair.  Component-wise sums, differences and
+// real scalings are packed FP32x2 instructions (sm_100 and later: one issue
+// for both components, each rounded as the scalar form).  The product stays
+// scalar: its packed form needs the operands' components broadcast and swapped
+// and issued no fewer instructions.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pd;}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (forward transform) or +i (inverse)
 template <bool INV> __device__ __forceinline__ float2 rot90(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
@@ -57,14 +71,20 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
   b = csub(t, b);
 }
 
+// The odd outputs d02 +- rot90(d13) mix components, so they stay scalar.
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-  float2 s13 = cadd(a1, a3), d13 = rot90<INV>(csub(a1, a3));
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const float2 s13 = cadd(a1, a3), d13 = csub(a1, a3);
   a0 = cadd(s02, s13);
   a2 = csub(s02, s13);
-  a1 = cadd(d02, d13);
-  a3 = csub(d02, d13);
+  if (INV) {   // rot90 = (-y, x)
+    a1 = make_float2(d02.x - d13.y, d02.y + d13.x);
+    a3 = make_float2(d02.x + d13.y, d02.y - d13.x);
+  } else {     // rot90 = (y, -x)
+    a1 = make_float2(d02.x + d13.y, d02.y - d13.x);
+    a3 = make_float2(d02.x - d13.y, d02.y + d13.x);
+  }
 }
 
 // r-point DFT of x (natural order in and out).
