@@ -131,7 +131,17 @@ typedef struct {
                                 (1 .. 128); 0 = chosen as for trial_mode (default 32) */
   int32_t chirp;        /* single-DM three-pass plans: where the forward row pass takes Eq. 4's
                            inverse filter from (POND_CHIRP_*) */
-  int32_t reserved[2];
+  int32_t inv_split;    /* log2 Q1 of the four-pass inverse, M = Q1 Q2 (M = nfft / (2 nchan)): I1
+                           transforms columns of Q2 = M / Q1 bins of each sub-channel, I2 rows of
+                           Q1 (the tile shape of the per-sub-channel inverse).  Used where the plan
+                           runs the four-pass inverse: single-DM plans on the four-pass schedule
+                           and batched lanes running POND_TRIALS_FOUR_PASS.  0 = the default split
+                           (batched plans with autotune: the tuner times the admissible splits).
+                           Admissible: 2 <= q <= 12, q <= 13 - log2 nchan, q <= log2 R2 (the
+                           forward column length) and 2 <= log2 M - q <= 12, for every FFT length
+                           the plan uses; else POND_E_ARG (with nfft_choices, lengths where the
+                           split is not admissible are not candidates) */
+  int32_t reserved[1];
 } pond_opts;
 
 /* Chirp source of a single-DM plan's fused forward row pass. */
@@ -155,6 +165,12 @@ typedef struct {
                                       dDM (e.g. a uniform grid from 0), the table holds the
                                       phase of dDM mod 1 in Q0.32 and trial d's phase is
                                       n_d times it mod 2^32 (exact integer product) */
+#define POND_TRIALS_FOUR_PASS 4    /* three launches per trial: I1 (the trial's chirp applied as the
+                                      shared spectrum's columns are loaded, inverse columns of Q2),
+                                      I2 (inverse rows of Q1, detection, sum over sub-channels) and
+                                      the decimation; the split M = Q1 Q2 is opts.inv_split, the
+                                      default or the tuner's.  Lanes without the three-pass geometry
+                                      (M = 64 R2) always run this form */
 
 /* Fold metadata returned with a profile snapshot. */
 typedef struct {
@@ -306,22 +322,29 @@ int pond_trials(pond_t h, double* dm, int64_t* nfft, int32_t cap, int32_t* ntria
  * pond_tuning: how each lane of a batched plan runs its trials (the
  *   autotuner's choices).  Lanes in increasing FFT length; out holds cap
  *   entries and *nlanes receives the number of lanes.  With autotune, each
- *   lane's candidates (per-trial launches, and the multi-trial forms with 8 or
- *   32 trials per launch, anchors or table) were timed on the lane's own
- *   buffers with CUDA events, and the fastest per trial is the one used; the
- *   choice is cached per (nfft, nchan, device, trial count).  A single-DM plan
- *   has one lane with mode POND_TRIALS_PER_TRIAL.
+ *   lane's candidates were timed on the lane's own buffers with CUDA events
+ *   and the fastest per trial is the one used: in lanes with the three-pass
+ *   geometry the per-trial launches and the multi-trial forms (8 or 32 trials
+ *   per launch, anchors or table), in every lane the four-pass form at up to
+ *   four admissible inverse splits (the default and its nearest neighbours;
+ *   only opts.inv_split when it is set).  The choice is cached per (nfft,
+ *   nchan, device, trial count, inv_split).  A single-DM plan has one lane:
+ *   mode POND_TRIALS_PER_TRIAL, or POND_TRIALS_FOUR_PASS on the four-pass
+ *   schedule.
  */
-#define POND_TUNE_MAXCAND 8
+#define POND_TUNE_MAXCAND 12
 typedef struct {
   int64_t nfft;
   int32_t ntrials;
-  int32_t mode;               /* POND_TRIALS_PER_TRIAL, _MULTI_ANCHOR or _MULTI_TABLE */
+  int32_t mode;               /* POND_TRIALS_PER_TRIAL, _MULTI_ANCHOR, _MULTI_TABLE or _FOUR_PASS */
   int32_t trials_per_launch;
   int32_t ncand;              /* candidates timed (0 without autotune) */
+  int32_t inv_split;          /* log2 Q1 of the lane's four-pass inverse (used by mode _FOUR_PASS) */
+  int32_t reserved;
   double dm_step;             /* the table form's dDM (0 when the DMs allow no table) */
   int32_t cand_mode[POND_TUNE_MAXCAND];
   int32_t cand_kt[POND_TUNE_MAXCAND];
+  int32_t cand_split[POND_TUNE_MAXCAND];   /* log2 Q1 of a _FOUR_PASS candidate, else 0 */
   double cand_us[POND_TUNE_MAXCAND];   /* device time per trial and segment, us */
 } pond_lane_info;
 int pond_tuning(pond_t h, pond_lane_info* out, int32_t cap, int32_t* nlanes);

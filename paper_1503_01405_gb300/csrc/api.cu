@@ -150,7 +150,9 @@ struct Lane {
   int* d_rows = nullptr;                    // per lane trial: its series row (the caller's trial index)
   double dm_step = 0;                       // table form's DM step (0: no table)
   std::vector<int> cand_mode, cand_kt;      // autotuner candidates and their time per trial
+  std::vector<int> cand_split;              // log2 Q1 of a four-pass candidate, else 0
   std::vector<double> cand_us;
+  float2* stwq = nullptr;                   // Q1 and Q2 tables of a tuned split other than the built one
 };
 
 }  // namespace
@@ -266,7 +268,7 @@ int validate(const pond_opts* o) {
   }
   if (o->precision != POND_FP32 && o->precision != POND_SPLIT_BF16 && o->precision != POND_SPLIT_BF16_5T)
     return fail(POND_E_ARG, "precision must be POND_FP32, POND_SPLIT_BF16 or POND_SPLIT_BF16_5T");
-  if (o->trial_mode < POND_TRIALS_AUTO || o->trial_mode > POND_TRIALS_MULTI_TABLE)
+  if (o->trial_mode < POND_TRIALS_AUTO || o->trial_mode > POND_TRIALS_FOUR_PASS)
     return fail(POND_E_ARG, "trial_mode %d is not a POND_TRIALS_* value", o->trial_mode);
   if (o->trials_per_launch < 0 || o->trials_per_launch > 128)
     return fail(POND_E_ARG, "trials_per_launch must be in 0 .. 128");
@@ -276,7 +278,15 @@ int validate(const pond_opts* o) {
     return fail(POND_E_ARG, "schedule must be POND_SCHEDULE_AUTO or POND_SCHEDULE_FOUR_PASS");
   if (o->input_channels < 0 || o->input_channels > 2)
     return fail(POND_E_ARG, "input_channels must be 0 or 1 (one int8 stream) or 2 (N / S pairs added in phase)");
+  if (o->inv_split < 0 || o->inv_split > 12) return fail(POND_E_ARG, "inv_split must be 0 (default) or 2 .. 12");
   return POND_OK;
+}
+
+// An inverse split M = Q1 Q2 (q = log2 Q1) the four-pass kernels take: I2's
+// CTA holds Q1-point rows of every sub-channel (nchan Q1 <= TILE), I1's bins
+// lie in runs of M / R2 columns (Q1 <= R2), and both lengths are 4 .. 4096.
+bool split_ok(const Geom& g, int lognch, int q) {
+  return q >= 2 && q <= 12 && q <= 13 - lognch && q <= g.logR2 && g.logM - q >= 2 && g.logM - q <= 12;
 }
 
 // Overlap-save geometry of an FFT length at the largest DM it must carry.
@@ -315,6 +325,13 @@ int geometry(const pond_opts* o, long long nfft, double dm, Geom* g) {
   if (g->logR2 < 2 || g->logR2 > g->logM || g->logQ1 < 2 || g->logQ2 < 2 || g->logQ2 > 12)
     return fail(POND_E_NCHAN, "unsupported nchan %d for nfft %lld (need M >= 16 and nchan*4 <= 8192)",
                 o->nchan, nfft);
+  if (o->inv_split) {
+    if (!split_ok(*g, lognch, o->inv_split))
+      return fail(POND_E_ARG, "inv_split %d is not admissible for nfft %lld, nchan %d (M = 2^%d, R2 = 2^%d)",
+                  o->inv_split, nfft, o->nchan, g->logM, g->logR2);
+    g->logQ1 = o->inv_split;
+    g->logQ2 = g->logM - g->logQ1;
+  }
   return POND_OK;
 }
 
@@ -427,6 +444,7 @@ void free_lane(Lane* ln) {
   cudaFree(ln->d_clog);
   cudaFree(ln->d_rows);
   cudaFree(ln->stw);
+  cudaFree(ln->stwq);
   cudaFree(ln->tw2buf);
   cudaFree(ln->carry[0]);
   cudaFree(ln->carry[1]);
@@ -650,7 +668,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
     CK(launch_fwd_rows(g, bufA, bufB, ln.tw3L, ln.tw2L, ln.stwR1, cs));
     RC(record(h, 1 + ST_F2, cs));
     h->launches += 2;
-    if (ln.mode != POND_TRIALS_PER_TRIAL) {
+    if (ln.mode == POND_TRIALS_MULTI_ANCHOR || ln.mode == POND_TRIALS_MULTI_TABLE) {
       // kt trials per launch: the row pass with each trial's chirp, the column
       // pass with detection, then the decimation of every trial's series row
       const int ntr = (int)ln.trials.size();
@@ -686,7 +704,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
       for (size_t q = 0; q < ln.trials.size(); ++q) {
         const int d = ln.trials[q];
         const Trial& t = h->trials[d];
-        if (ln.fused_multi) {
+        if (ln.mode == POND_TRIALS_PER_TRIAL) {
           // the trial's chirp and the first inverse factor as Ir loads the shared spectrum's rows
           CK(launch_inv_rows_chirp(g, bufB, bufA, ln.tw3L, ln.stwJ, t.anc, t.clog, cs));
           if (q == 0) RC(record(h, 1 + ST_IR, cs));
@@ -694,7 +712,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
                        (int)m_hi, cs));
           if (q == 0) RC(record(h, 1 + ST_IC, cs));
         } else {
-          // every trial's chirp is applied as I1 loads the shared forward spectrum
+          // four passes: every trial's chirp is applied as I1 loads the shared forward spectrum
           CK(launch_inv_cols(g, bufB, bufA, t.anc, t.clog, ln.stwQ2, cs));
           if (q == 0) RC(record(h, 1 + ST_I1, cs));
           CK(launch_inv_rows(g, bufA, P, vout, h->v_cap, h->v_len, (int)m_lo, (int)m_hi, ln.tw3M, ln.stwQ1, cs));
@@ -855,10 +873,10 @@ void destroy_all(pond_t h) {
 // ---------------------------------------------------------------------------
 
 std::mutex g_tune_mu;
-std::map<std::tuple<long long, int, int, int>, std::pair<double, double>> g_tune_cache;
+std::map<std::tuple<long long, int, int, int, int>, std::pair<double, double>> g_tune_cache;
 
 int measure_lane(pond_t h, const pond_opts* o, long long nfft, double* t_fwd, double* t_inv) {
-  const auto key = std::make_tuple(nfft, o->nchan, o->device, o->schedule);
+  const auto key = std::make_tuple(nfft, o->nchan, o->device, o->schedule, o->inv_split);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -1051,18 +1069,44 @@ int alloc_multi(Lane* ln, int kt) {
 // lane in the given mode (row pass, column pass, decimation), on slot 0, by
 // CUDA events over three launches after a warm-up.  The series rows it adds to
 // are cleared by the caller afterwards.
-int time_trials(pond_t h, Lane* ln, int mode, int kt, double* us) {
+int time_trials(pond_t h, Lane* ln, int mode, int kt, int split, double* us) {
   const Geom& g = ln->g;
   const int nq = std::min(kt, (int)ln->trials.size());
   const long long m_lo = g.n_past, m_hi = g.M - g.n_fut, g0 = m_lo, nv = m_hi - m_lo;
   const long long j_lo = (g0 * h->dec_den) / h->dec_num, j_hi = ((g0 + nv - 1) * h->dec_den) / h->dec_num;
+  // the four-pass form at this split: its own Q1 / Q2 tables
+  Geom gq = g;
+  float2* tq = nullptr;
+  const float2 *tq1 = nullptr, *tq2 = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t ce = cudaEventCreate(&e0);
+  cudaError_t ce = cudaSuccess;
+  if (mode == POND_TRIALS_FOUR_PASS) {
+    gq.logQ1 = split;
+    gq.logQ2 = g.logM - split;
+    const int n1 = stage_tw_entries(1 << gq.logQ1), n2 = stage_tw_entries(1 << gq.logQ2);
+    ce = cudaMalloc(&tq, (size_t)std::max(1, n1 + n2) * sizeof(float2));
+    tq1 = tq;
+    tq2 = tq + n1;
+    if (ce == cudaSuccess) ce = launch_stage_tw(tq, 1 << gq.logQ1, h->st);
+    if (ce == cudaSuccess) ce = launch_stage_tw(tq + n1, 1 << gq.logQ2, h->st);
+  }
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   const int reps = 3;
   for (int it = 0; it <= reps && ce == cudaSuccess; ++it) {
     if (it == 1) ce = cudaEventRecord(e0, h->st);
-    if (mode == POND_TRIALS_PER_TRIAL) {
+    if (mode == POND_TRIALS_FOUR_PASS) {
+      for (int q = 0; q < nq && ce == cudaSuccess; ++q) {
+        const Trial& t = h->trials[ln->trials[q]];
+        ce = launch_inv_cols(gq, ln->bufB[0], ln->bufA[0], t.anc, t.clog, tq2, h->st);
+        if (ce == cudaSuccess)
+          ce = launch_inv_rows(gq, ln->bufA[0], ln->P[0], nullptr, 0, 0, (int)m_lo, (int)m_hi, ln->tw3M, tq1, h->st);
+        if (ce == cudaSuccess)
+          ce = launch_decimate(ln->P[0], nv, g0, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+                               h->ts + (size_t)ln->trials[q] * h->ring, h->ts_cnt + (size_t)ln->trials[q] * h->ring,
+                               h->ring, h->st);
+      }
+    } else if (mode == POND_TRIALS_PER_TRIAL) {
       for (int q = 0; q < nq && ce == cudaSuccess; ++q) {
         const Trial& t = h->trials[ln->trials[q]];
         ce = launch_inv_rows_chirp(g, ln->bufB[0], ln->bufA[0], ln->tw3L, ln->stwJ, t.anc, t.clog, h->st);
@@ -1092,113 +1136,180 @@ int time_trials(pond_t h, Lane* ln, int mode, int kt, double* us) {
   if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
+  if (tq) {
+    cudaStreamSynchronize(h->st);
+    cudaFree(tq);
+  }
   if (ce != cudaSuccess) return fail(POND_E_CUDA, "trial autotune: %s", cudaGetErrorString(ce));
   *us = 1e3 * ms / reps / nq;
   return POND_OK;
 }
 
-std::map<std::tuple<long long, int, int, int, bool, int, int>, std::tuple<int, int, std::vector<int>, std::vector<int>,
-                                                                        std::vector<double>>>
-    g_trial_tune;
+// Run the lane's four-pass inverse at split q: its Q1 / Q2 tables are built
+// here unless q is the split the lane was built with.
+int use_split(pond_t h, Lane* ln, int q) {
+  Geom& g = ln->g;
+  if (q == g.logQ1) return POND_OK;
+  g.logQ1 = q;
+  g.logQ2 = g.logM - q;
+  const int n1 = stage_tw_entries(1 << g.logQ1), n2 = stage_tw_entries(1 << g.logQ2);
+  cudaFree(ln->stwq);
+  ln->stwq = nullptr;
+  CK(cudaMalloc(&ln->stwq, (size_t)std::max(1, n1 + n2) * sizeof(float2)));
+  ln->stwQ1 = ln->stwq;
+  ln->stwQ2 = ln->stwq + n1;
+  CK(launch_stage_tw(ln->stwq, 1 << g.logQ1, h->st));
+  CK(launch_stage_tw(ln->stwq + n1, 1 << g.logQ2, h->st));
+  return POND_OK;
+}
+
+// Inverse splits the tuner times: the lane's own split and the admissible ones
+// nearest to it, at most four (only opts.inv_split when it is set).
+std::vector<int> split_candidates(const pond_opts* o, const Geom& g) {
+  if (o->inv_split) return {g.logQ1};
+  const int lognch = ilog2ll(g.nchan);
+  std::vector<int> v{g.logQ1};
+  for (int d = 1; d <= 12 && v.size() < 4; ++d)
+    for (int q : {g.logQ1 - d, g.logQ1 + d})
+      if (v.size() < 4 && split_ok(g, lognch, q)) v.push_back(q);
+  return v;
+}
+
+// A tuned lane: mode, trials per launch, split, and every candidate (mode, kt, split, us).
+struct TrialTune {
+  int mode = 0, kt = 1, split = 0;
+  std::vector<int> cmode, ckt, csplit;
+  std::vector<double> cus;
+};
+std::map<std::tuple<long long, int, int, int, bool, int, int, int>, TrialTune> g_trial_tune;
+
+void free_multi(Lane* ln) {
+  for (int k = 0; k < NSLOT; ++k) {
+    cudaFree(ln->bufT[k]);
+    cudaFree(ln->Pm[k]);
+    cudaFree(ln->partm[k]);
+    cudaFree(ln->cntm[k]);
+    ln->bufT[k] = nullptr;
+    ln->Pm[k] = ln->partm[k] = nullptr;
+    ln->cntm[k] = nullptr;
+  }
+  ln->kt = 1;
+}
+
+// Put the lane into a tuned (or cached) form.
+int apply_tune(pond_t h, Lane* ln, const TrialTune& t) {
+  ln->mode = t.mode;
+  ln->cand_mode = t.cmode;
+  ln->cand_kt = t.ckt;
+  ln->cand_split = t.csplit;
+  ln->cand_us = t.cus;
+  if (t.mode == POND_TRIALS_FOUR_PASS) RC(use_split(h, ln, t.split));
+  if (t.mode == POND_TRIALS_PER_TRIAL || t.mode == POND_TRIALS_FOUR_PASS) {
+    free_multi(ln);
+    return POND_OK;
+  }
+  return t.kt != ln->kt || !ln->bufT[0] ? alloc_multi(ln, t.kt) : POND_OK;
+}
 
 // Choose how the lane runs its trials (after its trials' anchors exist and the
 // series rings are allocated; the rings are cleared afterwards by the caller).
+// Lanes with the three-pass geometry (M = 64 R2) run the per-trial row and
+// column passes, the multi-trial forms or the four-pass form; the others run
+// the four-pass form, at the split opts.inv_split, the default or the tuner's.
 int setup_trials(pond_t h, const pond_opts* o, Lane* ln) {
   const Geom& g = ln->g;
   const int ntr = (int)ln->trials.size();
-  ln->mode = POND_TRIALS_PER_TRIAL;
-  ln->kt = 1;
   const int req = o->trial_mode;
+  ln->kt = 1;
+  ln->mode = ln->fused_multi ? POND_TRIALS_PER_TRIAL : POND_TRIALS_FOUR_PASS;
+  if (!h->multi) return POND_OK;
+  if (req == POND_TRIALS_FOUR_PASS) ln->mode = POND_TRIALS_FOUR_PASS;
+  const bool tune = req == POND_TRIALS_AUTO && o->autotune;
   // several trials per launch need the three-pass lane geometry and two or more trials
-  if (!h->multi || !ln->fused_multi || ntr < 2 || req == POND_TRIALS_PER_TRIAL)
-    return POND_OK;
-  std::vector<int> rows(ntr), clogs(ntr);
-  std::vector<const ChirpAnchor*> ancs(ntr);
-  std::vector<double> dms(ntr);
-  for (int q = 0; q < ntr; ++q) {
-    const Trial& t = h->trials[ln->trials[q]];
-    rows[q] = ln->trials[q];
-    ancs[q] = t.anc;
-    clogs[q] = t.clog;
-    dms[q] = t.dm;
-  }
-  CK(cudaMalloc(&ln->d_rows, ntr * sizeof(int)));
-  CK(cudaMalloc(&ln->d_clog, ntr * sizeof(int)));
-  CK(cudaMalloc(&ln->d_anc, ntr * sizeof(ChirpAnchor*)));
-  CK(cudaMemcpy(ln->d_rows, rows.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ln->d_clog, clogs.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ln->d_anc, ancs.data(), ntr * sizeof(ChirpAnchor*), cudaMemcpyHostToDevice));
-  double step = 0;
-  std::vector<unsigned> nm;
-  if (dm_steps(dms, &step, &nm)) {
-    ln->dm_step = step;
-    CK(cudaMalloc(&ln->d_nmul, ntr * sizeof(unsigned)));
-    CK(cudaMemcpy(ln->d_nmul, nm.data(), ntr * sizeof(unsigned), cudaMemcpyHostToDevice));
-    CK(cudaMalloc(&ln->atab, (size_t)g.L * sizeof(unsigned)));
-    const double alpha = K_DM * 1e6 * step / (o->f0_mhz * o->f0_mhz);
-    CK(launch_chirp_table(ln->atab, g, o->fs_hz / (double)g.N * 1e-6, std::fabs(o->bw_mhz) / 2.0, o->f0_mhz, alpha,
-                          h->sgn, h->st));
+  const bool multi_ok = ln->fused_multi && ntr >= 2 && (req == POND_TRIALS_AUTO || req == POND_TRIALS_MULTI_ANCHOR ||
+                                                       req == POND_TRIALS_MULTI_TABLE);
+  if (multi_ok) {
+    std::vector<int> rows(ntr), clogs(ntr);
+    std::vector<const ChirpAnchor*> ancs(ntr);
+    std::vector<double> dms(ntr);
+    for (int q = 0; q < ntr; ++q) {
+      const Trial& t = h->trials[ln->trials[q]];
+      rows[q] = ln->trials[q];
+      ancs[q] = t.anc;
+      clogs[q] = t.clog;
+      dms[q] = t.dm;
+    }
+    CK(cudaMalloc(&ln->d_rows, ntr * sizeof(int)));
+    CK(cudaMalloc(&ln->d_clog, ntr * sizeof(int)));
+    CK(cudaMalloc(&ln->d_anc, ntr * sizeof(ChirpAnchor*)));
+    CK(cudaMemcpy(ln->d_rows, rows.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ln->d_clog, clogs.data(), ntr * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ln->d_anc, ancs.data(), ntr * sizeof(ChirpAnchor*), cudaMemcpyHostToDevice));
+    double step = 0;
+    std::vector<unsigned> nm;
+    if (dm_steps(dms, &step, &nm)) {
+      ln->dm_step = step;
+      CK(cudaMalloc(&ln->d_nmul, ntr * sizeof(unsigned)));
+      CK(cudaMemcpy(ln->d_nmul, nm.data(), ntr * sizeof(unsigned), cudaMemcpyHostToDevice));
+      CK(cudaMalloc(&ln->atab, (size_t)g.L * sizeof(unsigned)));
+      const double alpha = K_DM * 1e6 * step / (o->f0_mhz * o->f0_mhz);
+      CK(launch_chirp_table(ln->atab, g, o->fs_hz / (double)g.N * 1e-6, std::fabs(o->bw_mhz) / 2.0, o->f0_mhz, alpha,
+                            h->sgn, h->st));
+    }
   }
   const int best_multi = ln->dm_step > 0 ? POND_TRIALS_MULTI_TABLE : POND_TRIALS_MULTI_ANCHOR;
   const int kt_req = o->trials_per_launch ? std::min(o->trials_per_launch, ntr) : 0;
-  if (req != POND_TRIALS_AUTO || !o->autotune) {
+  if (!tune) {
     // the requested form (the table form only where the DMs allow it), else the table form where possible
+    if (!multi_ok) return POND_OK;
     ln->mode = (req == POND_TRIALS_MULTI_ANCHOR) ? POND_TRIALS_MULTI_ANCHOR : best_multi;
     return alloc_multi(ln, kt_req ? kt_req : std::min(32, ntr));
   }
   // autotune: time every candidate on this lane, keep the fastest per trial
-  std::vector<std::pair<int, int>> cands{{POND_TRIALS_PER_TRIAL, 1}};
+  struct Cand {
+    int mode, kt, split;
+  };
+  std::vector<Cand> cands;
   std::vector<int> kts;
-  if (kt_req) kts.push_back(kt_req);
-  else kts = {std::min(8, ntr), std::min(32, ntr)};
-  kts.erase(std::unique(kts.begin(), kts.end()), kts.end());
-  for (int kt : kts) {
-    cands.push_back({POND_TRIALS_MULTI_ANCHOR, kt});
-    if (ln->dm_step > 0) cands.push_back({POND_TRIALS_MULTI_TABLE, kt});
+  if (ln->fused_multi) cands.push_back({POND_TRIALS_PER_TRIAL, 1, 0});
+  if (multi_ok) {
+    if (kt_req) kts.push_back(kt_req);
+    else kts = {std::min(8, ntr), std::min(32, ntr)};
+    kts.erase(std::unique(kts.begin(), kts.end()), kts.end());
+    for (int kt : kts) {
+      cands.push_back({POND_TRIALS_MULTI_ANCHOR, kt, 0});
+      if (ln->dm_step > 0) cands.push_back({POND_TRIALS_MULTI_TABLE, kt, 0});
+    }
   }
-  const auto key = std::make_tuple(g.N, g.nchan, o->device, ntr, ln->dm_step > 0, kt_req, (int)(h->dec_num / h->dec_den));
+  for (int q : split_candidates(o, g)) cands.push_back({POND_TRIALS_FOUR_PASS, 1, q});
+  const auto key = std::make_tuple(g.N, g.nchan, o->device, ntr, ln->dm_step > 0, kt_req,
+                                   (int)(h->dec_num / h->dec_den), o->inv_split);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_trial_tune.find(key);
-    if (it != g_trial_tune.end()) {
-      ln->mode = std::get<0>(it->second);
-      ln->cand_mode = std::get<2>(it->second);
-      ln->cand_kt = std::get<3>(it->second);
-      ln->cand_us = std::get<4>(it->second);
-      return ln->mode == POND_TRIALS_PER_TRIAL ? POND_OK : alloc_multi(ln, std::get<1>(it->second));
-    }
+    if (it != g_trial_tune.end()) return apply_tune(h, ln, it->second);
   }
-  RC(alloc_multi(ln, *std::max_element(kts.begin(), kts.end())));
+  if (!kts.empty()) RC(alloc_multi(ln, *std::max_element(kts.begin(), kts.end())));
   CK(cudaMemsetAsync(ln->bufB[0], 0, (size_t)g.L * sizeof(float2), h->st));
+  TrialTune t;
   size_t best = 0;
   for (size_t c = 0; c < cands.size(); ++c) {
     double us = 0;
-    RC(time_trials(h, ln, cands[c].first, cands[c].second, &us));
-    ln->cand_mode.push_back(cands[c].first);
-    ln->cand_kt.push_back(cands[c].second);
-    ln->cand_us.push_back(us);
-    if (us < ln->cand_us[best]) best = c;
+    RC(time_trials(h, ln, cands[c].mode, cands[c].kt, cands[c].split, &us));
+    t.cmode.push_back(cands[c].mode);
+    t.ckt.push_back(cands[c].kt);
+    t.csplit.push_back(cands[c].split);
+    t.cus.push_back(us);
+    if (us < t.cus[best]) best = c;
   }
-  ln->mode = cands[best].first;
+  t.mode = cands[best].mode;
+  t.kt = cands[best].kt;
+  t.split = cands[best].split;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_trial_tune[key] = std::make_tuple(ln->mode, cands[best].second, ln->cand_mode, ln->cand_kt, ln->cand_us);
+    g_trial_tune[key] = t;
   }
-  if (ln->mode == POND_TRIALS_PER_TRIAL) {
-    for (int k = 0; k < NSLOT; ++k) {
-      cudaFree(ln->bufT[k]);
-      cudaFree(ln->Pm[k]);
-      cudaFree(ln->partm[k]);
-      cudaFree(ln->cntm[k]);
-      ln->bufT[k] = nullptr;
-      ln->Pm[k] = ln->partm[k] = nullptr;
-      ln->cntm[k] = nullptr;
-    }
-    ln->kt = 1;
-    return POND_OK;
-  }
-  if (cands[best].second != ln->kt) RC(alloc_multi(ln, cands[best].second));
-  return POND_OK;
+  return apply_tune(h, ln, t);
 }
 
 int plan_impl(pond_t* out, const pond_opts* o) {
@@ -1675,11 +1786,13 @@ int pond_tuning(pond_t h, pond_lane_info* out, int32_t cap, int32_t* nlanes) {
     r.ntrials = (int32_t)ln.trials.size();
     r.mode = ln.mode;
     r.trials_per_launch = ln.kt;
+    r.inv_split = ln.g.logQ1;
     r.dm_step = ln.dm_step;
     r.ncand = (int32_t)std::min<size_t>(ln.cand_us.size(), POND_TUNE_MAXCAND);
     for (int c = 0; c < r.ncand; ++c) {
       r.cand_mode[c] = ln.cand_mode[c];
       r.cand_kt[c] = ln.cand_kt[c];
+      r.cand_split[c] = ln.cand_split[c];
       r.cand_us[c] = ln.cand_us[c];
     }
   }

@@ -35,8 +35,9 @@ POND_TRIALS_AUTO = 0
 POND_TRIALS_PER_TRIAL = 1
 POND_TRIALS_MULTI_ANCHOR = 2
 POND_TRIALS_MULTI_TABLE = 3
+POND_TRIALS_FOUR_PASS = 4
 TRIAL_MODE_NAMES = {POND_TRIALS_PER_TRIAL: "per-trial", POND_TRIALS_MULTI_ANCHOR: "multi-anchor",
-                    POND_TRIALS_MULTI_TABLE: "multi-table"}
+                    POND_TRIALS_MULTI_TABLE: "multi-table", POND_TRIALS_FOUR_PASS: "four-pass"}
 POND_NSTAGE = 9
 POND_NOALLOC_MAX_NBINS = 1024
 POND_STACK_ROTATION = 0
@@ -78,17 +79,18 @@ class pond_opts(ctypes.Structure):
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("input_channels", ctypes.c_int32),
                 ("trial_mode", ctypes.c_int32), ("trials_per_launch", ctypes.c_int32),
-                ("chirp", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("chirp", ctypes.c_int32), ("inv_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
-POND_TUNE_MAXCAND = 8
+POND_TUNE_MAXCAND = 12
 
 
 class pond_lane_info(ctypes.Structure):
     _fields_ = [("nfft", ctypes.c_int64), ("ntrials", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("trials_per_launch", ctypes.c_int32), ("ncand", ctypes.c_int32), ("dm_step", ctypes.c_double),
+                ("trials_per_launch", ctypes.c_int32), ("ncand", ctypes.c_int32), ("inv_split", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dm_step", ctypes.c_double),
                 ("cand_mode", ctypes.c_int32 * POND_TUNE_MAXCAND), ("cand_kt", ctypes.c_int32 * POND_TUNE_MAXCAND),
-                ("cand_us", ctypes.c_double * POND_TUNE_MAXCAND)]
+                ("cand_split", ctypes.c_int32 * POND_TUNE_MAXCAND), ("cand_us", ctypes.c_double * POND_TUNE_MAXCAND)]
 
 
 class pond_meta(ctypes.Structure):
@@ -248,7 +250,7 @@ class Engine:
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
                  precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
                  schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1, trial_mode: int = POND_TRIALS_AUTO,
-                 trials_per_launch: int = 0, chirp: int = POND_CHIRP_AUTO):
+                 trials_per_launch: int = 0, chirp: int = POND_CHIRP_AUTO, inv_split: int = 0):
         """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
@@ -264,6 +266,7 @@ class Engine:
         o.trial_mode = trial_mode
         o.trials_per_launch = trials_per_launch
         o.chirp = chirp
+        o.inv_split = inv_split
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])
@@ -368,7 +371,8 @@ class Engine:
 
     def tuning(self) -> list:
         """How each lane runs its trials: FFT length, trials, mode, trials per
-        launch, DM step of the table form, and the autotuner's timed candidates."""
+        launch, the four-pass inverse split (log2 Q1), DM step of the table form,
+        and the autotuner's timed candidates."""
         n = ctypes.c_int32()
         _check(lib().pond_tuning(self._h, None, 0, ctypes.byref(n)))
         arr = (pond_lane_info * max(1, n.value))()
@@ -376,10 +380,12 @@ class Engine:
         out = []
         for r in arr[:n.value]:
             out.append({"nfft": r.nfft, "ntrials": r.ntrials, "mode": TRIAL_MODE_NAMES.get(r.mode, r.mode),
-                        "trials_per_launch": r.trials_per_launch, "dm_step": r.dm_step,
+                        "trials_per_launch": r.trials_per_launch, "inv_split": r.inv_split,
+                        "dm_step": r.dm_step,
                         "candidates_us_per_trial": [
                             {"mode": TRIAL_MODE_NAMES.get(r.cand_mode[c], r.cand_mode[c]),
-                             "trials_per_launch": r.cand_kt[c], "us": r.cand_us[c]} for c in range(r.ncand)]})
+                             "trials_per_launch": r.cand_kt[c], "inv_split": r.cand_split[c],
+                             "us": r.cand_us[c]} for c in range(r.ncand)]})
         return out
 
     def voltages(self, cap: int = 1 << 22):

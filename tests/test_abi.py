@@ -114,10 +114,24 @@ def test_batched_plan_validation():
     with pytest.raises(pond.PondError) as e:        # the fixed nfft cannot carry DM 30
         pond.Engine(**base, dms=[0.1, 30.0])
     assert e.value.name == "NFFT"
-    for kw in (dict(trial_mode=4), dict(trial_mode=-1), dict(trials_per_launch=129), dict(trials_per_launch=-2)):
+    for kw in (dict(trial_mode=5), dict(trial_mode=-1), dict(trials_per_launch=129), dict(trials_per_launch=-2),
+               dict(inv_split=-1), dict(inv_split=13), dict(inv_split=1), dict(inv_split=8), dict(inv_split=12)):
         with pytest.raises(pond.PondError) as e:
             pond.Engine(**base, dms=[0.1, 0.2], **kw)
         assert e.value.name == "ARG", kw
+
+
+@pytest.mark.parametrize("nfft,nchan,bad", [(1 << 16, 4, (1, 8, 11)),      # M 2^13, R2 2^7: q in 2..7
+                                            (1 << 21, 16, (3, 10)),        # M 2^16, R2 2^10: q in 4..9
+                                            (1 << 24, 64, (4, 8))])        # M 2^17: q in 5..7 (nchan Q1 <= 8192)
+def test_inverse_split_admissibility(nfft, nchan, bad):
+    """Inverse splits outside the kernels' tile limits are refused on the host
+    (single-DM four-pass plans here), before any CUDA call."""
+    for q in bad:
+        with pytest.raises(pond.PondError) as e:
+            pond.Engine(326.5, 16.0, 32e6, 0.1, nfft, nchan, 64, 0.1, schedule=pond.POND_SCHEDULE_FOUR_PASS,
+                        inv_split=q)
+        assert e.value.name == "ARG", q
 
 
 INCOH_CASES = [  # (options changed from a valid incoherent plan, expected code)

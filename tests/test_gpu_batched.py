@@ -218,16 +218,55 @@ def test_table_form_falls_back_to_anchors_off_grid():
 
 def test_trial_autotuner_times_every_form(grid_case):
     """With autotune the lane's forms (per-trial launches; anchors and table at 8
-    and 32 trials per launch, clipped to the trial count) are timed, the fastest
-    per trial runs, and the result still matches the oracle."""
+    and 32 trials per launch, clipped to the trial count; the four-pass form at
+    the default inverse split 2^8 x 2^8 and its nearest admissible neighbours)
+    are timed, the fastest per trial runs, and the result still matches the
+    oracle."""
     x, nfft, nchan, t_dec, res = grid_case
     info = tuned(GRID, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
     c = info[0]["candidates_us_per_trial"]
-    assert {k["mode"] for k in c} == {"per-trial", "multi-anchor", "multi-table"}
+    assert {k["mode"] for k in c} == {"per-trial", "multi-anchor", "multi-table", "four-pass"}
+    assert sorted(k["inv_split"] for k in c if k["mode"] == "four-pass") == [6, 7, 8, 9]
+    assert all(k["inv_split"] == 0 for k in c if k["mode"] != "four-pass")
     assert all(k["us"] > 0 for k in c)
     best = min(c, key=lambda k: k["us"])
     assert info[0]["mode"] == best["mode"]
+    if best["mode"] == "four-pass":
+        assert info[0]["inv_split"] == best["inv_split"]
     T, C, j0, nf = run_engine(x, GRID, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
+
+
+@pytest.mark.parametrize("q", [4, 6, 8, 9])
+def test_four_pass_trials_at_each_split_match_oracle(grid_case, q):
+    """Every trial through I1 + I2 at inverse split 2^q x 2^(16-q) (the tile
+    shape of the per-sub-channel inverse) against the oracle."""
+    x, nfft, nchan, t_dec, res = grid_case
+    T, C, j0, nf = run_engine(x, GRID, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_FOUR_PASS, inv_split=q)
+    info = tuned(GRID, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_FOUR_PASS, inv_split=q)
+    assert info[0]["mode"] == "four-pass" and info[0]["inv_split"] == q and info[0]["trials_per_launch"] == 1
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (q, d, rel(T[d], r.ts))
+
+
+def test_autotuned_split_outside_the_three_pass_geometry():
+    """A lane without the three-pass geometry (nfft 2^16, 16 sub-channels: M 2^11,
+    R2 2^7) runs the four-pass form; with autotune its inverse split is timed
+    (default 2^6 and neighbours 5, 7, 4) and the chosen one matches the oracle."""
+    dms = [0.0, 0.05, 0.3, 0.15, 0.25]
+    nfft, nchan, t_dec = 1 << 16, 16, 8e-6
+    x = stream(7 * (1 << 16) + 12345, seed=31)
+    info = tuned(dms, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
+    c = info[0]["candidates_us_per_trial"]
+    assert [k["mode"] for k in c] == ["four-pass"] * 4
+    assert [k["inv_split"] for k in c] == [6, 5, 7, 4]
+    best = min(c, key=lambda k: k["us"])
+    assert info[0]["mode"] == "four-pass" and info[0]["inv_split"] == best["inv_split"]
+    T, C, j0, nf = run_engine(x, dms, nfft, nchan, t_dec, autotune=True, nfft_choices=(nfft,))
+    res = oracle_batched(x, dms, nf, nchan, t_dec)
     for d, r in enumerate(res):
         assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
         assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))

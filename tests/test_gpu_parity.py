@@ -33,10 +33,11 @@ def rel(a, b):
 
 
 def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6,
-               schedule=pond.POND_SCHEDULE_AUTO, input_channels=1, chirp=pond.POND_CHIRP_AUTO, pinned=False):
+               schedule=pond.POND_SCHEDULE_AUTO, input_channels=1, chirp=pond.POND_CHIRP_AUTO, pinned=False,
+               inv_split=0):
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
                      want_voltages=want_voltages, schedule=schedule, input_channels=input_channels,
-                     chirp=chirp) as e:
+                     chirp=chirp, inv_split=inv_split) as e:
         if pinned:
             # page-locked host memory: the pieces reach the device by the copy kernel
             import torch
@@ -154,6 +155,29 @@ def test_three_pass_schedule(cfg):
     assert segs == four["stats"]["segments"] and segs >= 2
     # one pass fewer per segment (the pushes' carry copies are the same in both)
     assert four["stats"]["kernel_launches"] - three["stats"]["kernel_launches"] == segs
+
+
+# Four-pass inverse splits M = Q1 Q2 (log2 Q1 = q) other than the default: I1's
+# column tiles of Q2 and I2's rows of Q1 cover the same sub-channel inverses.
+SPLITS = [((1 << 16, 16, 0.3, 16.0, 128, 0.033), (2, 3, 4, 5, 7)),       # M 2^11, R2 2^7; default 6
+          ((1 << 18, 8, 1.0, -16.0, 128, 0.03), (2, 5, 8)),              # M 2^14, R2 2^8; default 7
+          ((1 << 21, 16, 3.0, 16.0, 256, 0.07), (4, 9))]                  # M 2^16, R2 2^10; default 8
+
+
+@pytest.mark.parametrize("cfg,splits", SPLITS, ids=[f"N{c[0]}_c{c[1]}" for c, _ in SPLITS])
+def test_inverse_splits_match_oracle(cfg, splits):
+    """The four-pass schedule at every listed split against the oracle (voltages,
+    profile, series), with the same launches per segment as the default split."""
+    nfft, nchan, dm, bw, nbins, period = cfg
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
+    x = _stream(p, seed=nfft + 11, extra=5)
+    r = pcd.run(p, x, want_voltages=True)
+    base = run_engine(x, p, schedule=pond.POND_SCHEDULE_FOUR_PASS)
+    check(base, r)
+    for q in splits:
+        out = run_engine(x, p, schedule=pond.POND_SCHEDULE_FOUR_PASS, inv_split=q)
+        check(out, r)
+        assert out["stats"]["kernel_launches"] == base["stats"]["kernel_launches"], q
 
 
 @pytest.mark.parametrize("cfg", [(1 << 16, 16, 0.3, 16.0, 128, 0.033), (1 << 18, 8, 1.0, 16.0, 128, 0.03),
