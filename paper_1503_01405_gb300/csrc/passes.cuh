@@ -126,6 +126,18 @@ __device__ __forceinline__ float2 tw3(const float2* t, unsigned e) {
 }
 
 
+// The passes' CTAs start in launch order as earlier ones end (two resident per
+// SM); CTA b asks L2 for the tile of CTA b + PF_DIST, which starts a fraction
+// of a CTA lifetime later.  Measured on the full-rate plan (Msamples/s, two
+// segment streams): none 104.1k; distance 1: 109.0k, 8: 109.9k, 16: 110.5k,
+// 38: 111.2k, 76: 111.1k, 152: 110.2k, 304: 108.8k, 608: 105.6k.
+constexpr int PF_DIST = 38;
+// Ask L2 to fetch [p, p + bytes) (16-byte aligned, bytes a multiple of 16):
+// no registers, no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Offsets into the segment buffers are 32-bit: every buffer holds L <= 2^24
 // elements (nfft <= 2^25).
 
@@ -516,6 +528,10 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
   if constexpr (TC) tc::setup(tcc, sm, tile_f2<R1, TC>(nl), tca);
   const int q0 = blockIdx.x * np;
   if constexpr (!TC && R1 >= 256) {
+    if (threadIdx.x < 2 && np == 1 && blockIdx.x + PF_DIST < gridDim.x) {
+      const int q = q0 + PF_DIST, row = threadIdx.x == 0 ? q : R2 - q;   // as in k_fwd_rows_inv
+      prefetch_l2(in + ((size_t)row << LOGR1), R1 * (unsigned)sizeof(float2));
+    }
     f2_stage1<R1, LSTR>(in, sm, st3, q0, np, R2, nl);
     __syncthreads();
     Stages<R1, 16, false, LSTR>::run(sm, nl, stw);        // the stages after the first
@@ -620,6 +636,11 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   load_twiddles<R1>(stw, tw);
   load_twiddles<J>(stwj, twJ);
   const int q0 = blockIdx.x * np;
+  if (threadIdx.x < 2 && np == 1 && blockIdx.x + PF_DIST < gridDim.x) {
+    // the two rows of CTA blockIdx.x + PF_DIST (q and its mirror R2 - q)
+    const int q = q0 + PF_DIST, row = threadIdx.x == 0 ? q : R2 - q;
+    prefetch_l2(in + ((size_t)row << LOGR1), R1 * (unsigned)sizeof(float2));
+  }
   f2_stage1<R1, LSTR>(in, sm, st3, q0, np, R2, nl);
   // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L
   for (int i = threadIdx.x; i < nl * J; i += NT) {
@@ -736,6 +757,16 @@ __global__ void __launch_bounds__(NT, 2) k_inv_rows_chirp_multi(const float2* __
   const int t = blockIdx.x;
   const int r0 = blockIdx.y * nl;
   const int tot = nl * R1;
+  if (t == 0 && threadIdx.x < 2) {
+    // trials run fastest in launch order: the first trial's CTA of a row tile
+    // warms L2 with the rows (and table words) of a later tile
+    const unsigned rn = blockIdx.y + max(1u, (unsigned)PF_DIST / gridDim.x);
+    if (rn < gridDim.y) {
+      const size_t e0 = ((size_t)rn * nl) << LOGR1;
+      if (threadIdx.x == 0) prefetch_l2(in + e0, (unsigned)tot * (unsigned)sizeof(float2));
+      else if (TABLE) prefetch_l2(mc.atab + e0, (unsigned)tot * (unsigned)sizeof(unsigned));
+    }
+  }
   load_tw3(st3, tw3L);
   load_twiddles<J>(stwj, twJ);
   // rows r0 .. r0 + nl - 1 are contiguous: 16-byte loads of columns k1, k1 + 1
@@ -1023,6 +1054,17 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det(const float2* __restrict
   load_twiddles<R2>(stw, tw);
   const int m1 = blockIdx.x >> logG, gi = blockIdx.x & ((1 << logG) - 1);
   const float2* blk = in + (size_t)blockIdx.x * tot;   // block m1 G + g
+  if (threadIdx.x < 4) {
+    // the block of CTA blockIdx.x + PF_DIST (in launch order, the next trial's
+    // blocks after this trial's last), in four quarters
+    const unsigned nx = gridDim.x, lin = blockIdx.y * nx + blockIdx.x + PF_DIST;
+    if (lin < nx * gridDim.y) {
+      const float2* nb = in - blockIdx.y * ts.in + (size_t)(lin / nx) * ts.in + (size_t)(lin % nx) * tot;
+      const unsigned qb = (unsigned)tot * (unsigned)sizeof(float2) / 4;
+      if (ts.in != 0 || lin / nx == blockIdx.y)
+        prefetch_l2(reinterpret_cast<const char*>(nb) + threadIdx.x * qb, qb);
+    }
+  }
   {
     // The first radix-16 stage straight from global memory: butterfly t of line
     // ci (sub-channels fastest, so consecutive lanes read consecutive elements)

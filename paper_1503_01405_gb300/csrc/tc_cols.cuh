@@ -213,6 +213,15 @@ __global__ void __launch_bounds__(NT, 2) k_inv_cols_det_tc(const float2* __restr
   const int logG = lognch - 2;
   const int m1 = blockIdx.x >> logG, gi = blockIdx.x & ((1 << logG) - 1);
   const float2* blk = in + (size_t)blockIdx.x * (IC_R2 * NL);
+  if (threadIdx.x < 4) {
+    // the block of CTA blockIdx.x + PF_DIST in launch order, as the FP32 column pass does
+    const unsigned nx = gridDim.x, lin = blockIdx.y * nx + blockIdx.x + PF_DIST;
+    if (lin < nx * gridDim.y && (ts.in != 0 || lin / nx == blockIdx.y)) {
+      const float2* nb = in - blockIdx.y * ts.in + (size_t)(lin / nx) * ts.in + (size_t)(lin % nx) * (IC_R2 * NL);
+      constexpr unsigned QB = IC_R2 * NL * (unsigned)sizeof(float2) / 4;
+      prefetch_l2(reinterpret_cast<const char*>(nb) + threadIdx.x * QB, QB);
+    }
+  }
   const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
   const int L = warp & 3, Q = warp >> 2;
   const int row = 32 * L + lane;                   // this thread's MMA row and TMEM lane
