@@ -138,6 +138,17 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Ask L2 for the whole 16-byte words of bytes [lo, hi) of p, in pieces of at
+// most 64 KiB (rounded inward: nothing outside the range is touched).
+__device__ __forceinline__ void prefetch_range(const int8_t* p, long long lo, long long hi) {
+  uintptr_t s = ((uintptr_t)(p + lo) + 15) & ~(uintptr_t)15;
+  const uintptr_t e = (uintptr_t)(p + hi) & ~(uintptr_t)15;
+  for (; s < e; s += 65536) {
+    const uintptr_t n = e - s < 65536 ? e - s : 65536;
+    prefetch_l2(reinterpret_cast<const void*>(s), (unsigned)n);
+  }
+}
+
 // Offsets into the segment buffers are 32-bit: every buffer holds L <= 2^24
 // elements (nfft <= 2^25).
 
@@ -226,6 +237,16 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(SegIn in, float2* __restrict
   if constexpr (TC) tc::setup(tcc, sm, tile_f2<R2, TC, LSTR>(nl), tca);
   const int tile = blockIdx.x;
   const int n1_0 = tile * nl;
+  // every CTA reads a column slice of every row, so the first F1PF_CTAS CTAs
+  // ask L2 for the whole segment (its carried and new runs), a 1/F1PF_CTAS
+  // share each, before the strided loads of the first wave arrive (full rate:
+  // 111.2k -> 112.8k Msamples/s)
+  constexpr int F1PF_CTAS = 64;
+  if (threadIdx.x == 0 && tile < F1PF_CTAS && gridDim.x >= F1PF_CTAS) {
+    const long long pa = (in.a_len + F1PF_CTAS - 1) / F1PF_CTAS, pb = (in.b_len + F1PF_CTAS - 1) / F1PF_CTAS;
+    if (in.a_len > 0) prefetch_range(in.a, min(in.a_len, tile * pa), min(in.a_len, (tile + 1) * pa));
+    if (in.b_len > 0) prefetch_range(in.b, min(in.b_len, tile * pb), min(in.b_len, (tile + 1) * pb));
+  }
   // FP32 form, R2 >= 512, aligned runs: the first radix-16 stage takes its inputs
   // straight from global memory (butterfly t of column b, columns fastest: a warp
   // reads the nl columns of 8 rows per load) and the stages after it start from
