@@ -841,29 +841,29 @@ def run_precision(args, rank, ws, dist):
         print(json.dumps(line), flush=True)
 
 
-def run_learned(args, rank):
+LEARNED_WORKLOAD = ("learned: DM-time patches (32 trials x 256 samples of 32 us) from the batched engine on "
+                    "labelled 8 s chunks; pulse / DM-0 burst / narrowband / noise")
+
+
+def learned_core(chunks: int, shifts: int, epochs: int) -> dict:
     """Classifier on DM-time patches: training chunks and disjoint held-out
     chunks (different seeds) through the batched engine; recall and false
-    positive rate of the classifier and of the boxcar detector; inference rate."""
-    if rank != 0:
-        return
-    import numpy as np
+    positive rate of the classifier and of the boxcar detector, the boxcar with
+    the network's veto; inference rate."""
     import torch
 
-    from paper_1503_01405_gb300 import build as pbuild
-    from paper_1503_01405_gb300 import learn, pond, synth
+    from paper_1503_01405_gb300 import learn, pond
 
-    pbuild.build()
     t0 = time.perf_counter()
-    Xtr, Ytr, Ftr = learn.build_dataset(args.chunks, seed=1000, shifts=args.shifts)
-    Xte, Yte, Fte = learn.build_dataset(max(2, args.chunks // 5), seed=2000, shifts=args.shifts)
-    Xva, Yva, Fva = learn.build_dataset(max(2, args.chunks // 8), seed=3000, shifts=args.shifts)
+    Xtr, Ytr, Ftr = learn.build_dataset(chunks, seed=1000, shifts=shifts)
+    Xte, Yte, Fte = learn.build_dataset(max(2, chunks // 5), seed=2000, shifts=shifts)
+    Xva, Yva, Fva = learn.build_dataset(max(2, chunks // 8), seed=3000, shifts=shifts)
     gen_s = time.perf_counter() - t0
     theta = learn.init_params(99)
     clf = pond.Classifier(theta, max_batch=512)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = learn.train(clf, Xtr, Ytr, epochs=args.epochs, batch=256, lr=2e-3, seed=3)
+    hist = learn.train(clf, Xtr, Ytr, epochs=epochs, batch=256, lr=2e-3, seed=3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
     pte = learn.predict(clf, Xte)
@@ -878,18 +878,27 @@ def run_learned(args, rank):
     rate_big = learn.inference_rate(clf_big, Xte, batch=8192, reps=10)
     clf_big.close()
     clf.close()
-    line = {"metric": "single-pulse candidates classified per second (CNN inference)", "value": rate,
-            "unit": "candidates/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "learned: DM-time patches (32 trials x 256 samples of 32 us) from the batched "
-                                   "engine on labelled 8 s chunks; pulse / DM-0 burst / narrowband / noise",
-                       "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)), "epochs": args.epochs,
-                       "shifts_per_event": args.shifts, "train_chunks": args.chunks,
-                       "batch": 256, "lr": 2e-3},
+    return {"value": rate, "unit": "candidates/s",
+            "config": {"workload": LEARNED_WORKLOAD, "train_patches": int(len(Ytr)), "test_patches": int(len(Yte)),
+                       "epochs": epochs, "shifts_per_event": shifts, "train_chunks": chunks, "batch": 256,
+                       "lr": 2e-3},
             "inference_batch": 512, "value_batch_8192": rate_big,
             "inference_kernel": "k_cnn_infer_tc (tcgen05 implicit-GEMM convolutions, BF16, FP32 accumulators)",
             "evaluation": res, "boxcar_with_network_veto": veto, "validation_patches": int(len(Yva)),
-            "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s,
-            "dataset_s": gen_s}
+            "train_loss_first_last": [hist[0], hist[-1]], "train_s": train_s, "dataset_s": gen_s}
+
+
+def run_learned(args, rank):
+    if rank != 0:
+        return
+    from paper_1503_01405_gb300 import build as pbuild
+
+    pbuild.build()
+    r = learned_core(args.chunks, args.shifts, args.epochs)
+    line = {"metric": "single-pulse candidates classified per second (CNN inference)", "value": r.pop("value"),
+            "unit": r.pop("unit"), "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": r.pop("config")}
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 
@@ -1187,6 +1196,11 @@ def main():
                             "trial_samples_per_s": bval * 1e6 * 128, "nfft_groups": b["groups"],
                             "plan_s_incl_autotune": b["plan_s"], "tuning": b["tuning"],
                             "gpu_launches_per_step": b["launches_per_step"], "clocks": b["clocks"]}
+        # the learned form at the default scale (40 training chunks, 16 shifts per event)
+        torch.cuda.empty_cache()
+        lr_ = learned_core(40, 16, 20)
+        lr_["metric"] = "single-pulse candidates classified per second (CNN inference)"
+        extra["learned"] = lr_
     clocks = clk.summary()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
