@@ -126,29 +126,6 @@ __device__ __forceinline__ float2 tw3(const float2* t, unsigned e) {
 }
 
 
-// The passes' CTAs start in launch order as earlier ones end (two resident per
-// SM); CTA b asks L2 for the tile of CTA b + PF_DIST, which starts a fraction
-// of a CTA lifetime later.  Measured on the full-rate plan (Msamples/s, two
-// segment streams): none 104.1k; distance 1: 109.0k, 8: 109.9k, 16: 110.5k,
-// 38: 111.2k, 76: 111.1k, 152: 110.2k, 304: 108.8k, 608: 105.6k.
-constexpr int PF_DIST = 38;
-// Ask L2 to fetch [p, p + bytes) (16-byte aligned, bytes a multiple of 16):
-// no registers, no completion to wait for.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Ask L2 for the whole 16-byte words of bytes [lo, hi) of p, in pieces of at
-// most 64 KiB (rounded inward: nothing outside the range is touched).
-__device__ __forceinline__ void prefetch_range(const int8_t* p, long long lo, long long hi) {
-  uintptr_t s = ((uintptr_t)(p + lo) + 15) & ~(uintptr_t)15;
-  const uintptr_t e = (uintptr_t)(p + hi) & ~(uintptr_t)15;
-  for (; s < e; s += 65536) {
-    const uintptr_t n = e - s < 65536 ? e - s : 65536;
-    prefetch_l2(reinterpret_cast<const void*>(s), (unsigned)n);
-  }
-}
-
 // Offsets into the segment buffers are 32-bit: every buffer holds L <= 2^24
 // elements (nfft <= 2^25).
 
