@@ -362,6 +362,9 @@ int pond_tuning(pond_t h, pond_lane_info* out, int32_t cap, int32_t* nlanes);
  *   out[0] (both required).  A batched plan writes trial d's samples at
  *   out[d * cap + i] (out holds ndm * cap floats); counts are common to all trials.  Samples are complete once every g they cover has
  *   been processed; after pond_flush all remaining samples are complete.
+ *   When out (or counts) is page-locked host memory (cudaMallocHost,
+ *   cudaHostRegister) the device's rows are copied into it directly; other
+ *   host memory receives them through the handle's pinned row buffer.
  */
 int pond_timeseries(pond_t h, float* out, int32_t* counts, size_t cap, size_t* n_out,
                     int64_t* first_index);

@@ -508,29 +508,41 @@ int collect_timing(pond_t h) {
   return POND_OK;
 }
 
-// Move completed time-series samples of every trial from the device rings to the host.
+// True when p is page-locked host memory (cudaMallocHost / cudaHostRegister):
+// device-to-host copies can land there directly.
+bool pinned_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 // Move n completed series samples, from ts_drained on, out of the device ring
 // into row d of dst (dst(d) returns its first element) and the counts into
-// cnt, through the pinned row buffer (device-to-pageable copies are several
-// times slower), and clear the ring slots they held.
+// cnt, and clear the ring slots they held.  Rows that are page-locked host
+// memory receive the device-to-host copies directly; others go through the
+// pinned row buffer (device-to-pageable copies are several times slower).
 template <class DstRow>
 int drain_ts(pond_t h, long long n, DstRow dst, int32_t* cnt) {
   const int ntr = (int)h->trials.size();
-  if (!h->ts_pin) CK(cudaMallocHost(&h->ts_pin, (size_t)h->ring * sizeof(float)));
   const long long slot0 = h->ts_drained % h->ring;
   auto row = [&](auto* dev_row, auto* out) -> int {
     using T = typename std::remove_pointer<decltype(out)>::type;
     static_assert(sizeof(T) == sizeof(float), "4-byte ring rows");
+    const bool direct = out && pinned_host(out);
+    if (out && !direct && !h->ts_pin) CK(cudaMallocHost(&h->ts_pin, (size_t)h->ring * sizeof(float)));
+    T* land = direct ? out : static_cast<T*>(h->ts_pin);
     long long done = 0, slot = slot0;
     while (done < n) {
       const long long run = std::min(n - done, h->ring - slot);
-      if (out) CK(cudaMemcpyAsync(static_cast<T*>(h->ts_pin) + done, dev_row + slot, run * sizeof(T),
-                                  cudaMemcpyDeviceToHost, h->st));
+      if (out) CK(cudaMemcpyAsync(land + done, dev_row + slot, run * sizeof(T), cudaMemcpyDeviceToHost, h->st));
       CK(cudaMemsetAsync(dev_row + slot, 0, run * sizeof(T), h->st));
       done += run;
       slot = 0;
     }
-    if (out) {
+    if (out && !direct) {
       CK(cudaStreamSynchronize(h->st));
       memcpy(out, h->ts_pin, n * sizeof(T));
     }

@@ -348,6 +348,20 @@ class Engine:
             C = np.concatenate(cparts) if cparts else np.zeros(0, np.int32)
         return (T if self.ndm else T[0]), C, first
 
+    def timeseries_into(self, T: np.ndarray, C: np.ndarray) -> tuple[int, int]:
+        """Drain completed series samples into caller arrays: T float32 ([ndm, cap]
+        for a batched plan, [cap] otherwise), C int32 [cap].  Returns (samples
+        written, index of the first).  Arrays in page-locked memory (e.g. a
+        pinned torch tensor's numpy view) receive the device's rows directly."""
+        rows = max(1, self.ndm)
+        cap = C.shape[0]
+        assert T.dtype == np.float32 and C.dtype == np.int32 and T.size == rows * cap
+        assert T.flags.c_contiguous and C.flags.c_contiguous
+        n = ctypes.c_size_t()
+        j0 = ctypes.c_int64()
+        _check(lib().pond_timeseries(self._h, _ptr(T), _ptr(C), cap, ctypes.byref(n), ctypes.byref(j0)))
+        return n.value, j0.value
+
     def candidates(self, threshold: float = 6.0, cap: int = 1 << 16, classifier=None):
         """Boxcar candidates over the completed, undrained series: list of dicts.
         With ``classifier`` (a Classifier on the same device) each candidate's

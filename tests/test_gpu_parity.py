@@ -251,6 +251,28 @@ def test_pinned_host_push_matches_oracle():
     check(got, pcd.run(p, x, want_voltages=True))
 
 
+def test_series_into_pinned_arrays():
+    """pond_timeseries into page-locked caller arrays (copied there directly)
+    returns what the default drain returns, bit for bit, and pageable arrays
+    work the same way; a second drain is empty."""
+    import torch
+    nfft, nchan, dm, bw, nbins, period = CONFIGS[3]
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period)
+    x = _stream(p, seed=91, extra=3)
+    ref = run_engine(x, p, want_voltages=False)
+    cap = len(ref["T"]) + 100
+    for pinned in (True, False):
+        T = torch.zeros(cap, dtype=torch.float32, pin_memory=pinned).numpy()
+        C = torch.zeros(cap, dtype=torch.int32, pin_memory=pinned).numpy()
+        with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period) as e:
+            e.push(x)
+            e.flush()
+            n, j0 = e.timeseries_into(T, C)
+            assert e.timeseries_into(T[:10].copy(), C[:10].copy())[0] == 0
+        assert n == len(ref["T"]) and j0 == ref["j0"]
+        assert np.array_equal(T[:n], ref["T"]) and np.array_equal(C[:n], ref["C"])
+
+
 def test_repeatable_bitwise():
     p = pcd.make_plan(326.5, 16.0, 32e6, 1.0, 1 << 17, 64, 256, 0.05)
     x = _stream(p, seed=9, extra=3)
