@@ -799,9 +799,16 @@ cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double in
                             long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
                             double* psum, long long* phits, cudaStream_t st) {
   if (n <= 0 || nj <= 0) return cudaSuccess;
-  // whole series samples per CTA: at least 256 channel samples each, at most MAX_FOLD_PARTS CTAs
+  // whole series samples per CTA: at least FOLD_MIN_SAMPLES channel samples
+  // each, at most MAX_FOLD_PARTS CTAs.  The fold runs beside the passes of the
+  // next segments, and each resident fold CTA holds registers a pass CTA would
+  // use: a few long-lived CTAs displace less than many short ones (full rate,
+  // 105k samples per segment, CTAs: 304: 112.5k, 152: 113.9k, 76: 114.8k,
+  // 38: 114.8k, 19: 114.0k Msamples/s), while segments of a million samples
+  // (one sub-channel) still spread over every SM.
+  constexpr long long FOLD_MIN_SAMPLES = 1400;
   const long long per_j = std::max(1ll, num / den);
-  long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (256 + per_j - 1) / per_j);
+  long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (FOLD_MIN_SAMPLES + per_j - 1) / per_j);
   jpc = std::min(jpc, nj);
   const unsigned parts = (unsigned)((nj + jpc - 1) / jpc);
   k_fold_dec<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, num, den, j_lo, nj, jpc, T,
