@@ -74,6 +74,10 @@ class Plan:
     S: int = 0         # segment step in real samples
     inc: float = 0.0   # fold phase increment per channel sample
     dec: Fraction = Fraction(1)   # channel samples per time-series sample
+    # optional polynomial phase model of the fold (replaces the constant period):
+    # phi(g) = sum_i phase_coef[i] tau^i, tau = g dtc - phase_tref (seconds from the first sample)
+    phase_coef: tuple = ()
+    phase_tref: float = 0.0
 
 
 def adding_in_phase(raw: np.ndarray) -> np.ndarray:
@@ -101,8 +105,10 @@ def overlap(f0: float, bw: float, dm: float, dtc: float) -> tuple[int, int]:
 
 
 def make_plan(f0: float, bw: float, fs: float, dm: float, nfft: int, nchan: int,
-              nbins: int, period: float, t_dec_s: float = 61.44e-6) -> Plan:
-    """Validate a plan and derive the overlap-save geometry."""
+              nbins: int, period: float, t_dec_s: float = 61.44e-6, phase=None) -> Plan:
+    """Validate a plan and derive the overlap-save geometry.  ``phase`` =
+    (t_ref, coefficients) folds with that polynomial phase model instead of the
+    constant period (1 .. 8 coefficients, cycles per second^i)."""
     if not (f0 > 0 and bw != 0 and abs(bw) < 2 * f0 and fs > 0):
         raise PlanError("ARG", "bad band")
     if abs(fs - 2.0 * abs(bw) * 1e6) > 1e-6 * fs:
@@ -131,7 +137,12 @@ def make_plan(f0: float, bw: float, fs: float, dm: float, nfft: int, nchan: int,
         raise PlanError("ARG", "t_dec must be >= 1 ns")
     dec = Fraction(t_dec_ns) * Fraction(int(fs)) / (Fraction(10 ** 9) * 2 * nchan)
     inc = dtc / period
-    return Plan(f0, bw, fs, dm, nfft, nchan, nbins, period, t_dec_ns,
+    pc, pt = (), 0.0
+    if phase is not None:
+        pt, pc = float(phase[0]), tuple(float(c) for c in phase[1])
+        if not 1 <= len(pc) <= 8 or not all(math.isfinite(c) for c in pc + (pt,)):
+            raise PlanError("ARG", "phase model: 1 .. 8 finite coefficients and a finite t_ref")
+    return Plan(f0, bw, fs, dm, nfft, nchan, nbins, period, t_dec_ns, phase_coef=pc, phase_tref=pt,
                 L=L, M=M, dtc=dtc, n_past=n_past, n_fut=n_fut, S_c=S_c,
                 S=2 * nchan * S_c, inc=inc, dec=dec)
 
@@ -200,11 +211,20 @@ def fold(p: Plan, power: np.ndarray, g0: int) -> tuple[np.ndarray, np.ndarray]:
     """Fold P[g], g = g0.., at the period (FP64 phase, epoch at g = 0).
 
     bin(g) = min(floor(frac(g * inc) * nbins), nbins - 1), inc = (2 nchan / fs) / P.
+    With a phase model the phase is phi(g) of that polynomial at t = g dtc
+    (Horner's rule, each FP64 operation rounded on its own; the reading of the
+    TEMPO2 predictors of Sec. 3.4 used by the pulse stacks), and
+    bin(g) = min(floor((phi - floor(phi)) nbins), nbins - 1).
     """
-    g = np.arange(g0, g0 + len(power), dtype=np.float64)
-    x = g * p.inc
-    phi = x - np.floor(x)
-    b = np.minimum((phi * p.nbins).astype(np.int64), p.nbins - 1)
+    if p.phase_coef:
+        from oracle import stack
+        b = stack.rotation_and_bin(p.phase_coef, p.phase_tref,
+                                   np.arange(g0, g0 + len(power), dtype=np.int64), p.dtc, p.nbins)[1]
+    else:
+        g = np.arange(g0, g0 + len(power), dtype=np.float64)
+        x = g * p.inc
+        phi = x - np.floor(x)
+        b = np.minimum((phi * p.nbins).astype(np.int64), p.nbins - 1)
     s = np.bincount(b, weights=power, minlength=p.nbins).astype(np.float64)
     h = np.bincount(b, minlength=p.nbins).astype(np.int64)
     return s, h

@@ -343,6 +343,60 @@ def test_pulsar_recovered_small_workload():
     assert 40 < snr < 60, snr
 
 
+# --- the fold with a polynomial phase model (replacing the constant period) -------
+
+def test_phase_model_fold_is_the_constant_period_off_bin_edges():
+    """A model phi = tau / P (t_ref 0) bins every sample as the constant-period
+    rule does, except samples within 1e-9 of a bin edge (the two phases round
+    differently: (g dtc)(1/P) against g (dtc/P)), which move by one bin; the
+    fold's histogram is that of the model's bins."""
+    from oracle import stack
+    P = 0.0123457
+    p0 = pcd.make_plan(**ORT, dm=0.0, nfft=1 << 12, nchan=4, nbins=64, period=P)
+    p1 = pcd.make_plan(**ORT, dm=0.0, nfft=1 << 12, nchan=4, nbins=64, period=P, phase=(0.0, [0.0, 1.0 / P]))
+    g0 = 12345
+    g = np.arange(g0, g0 + 400_000, dtype=np.int64)
+    x = g.astype(np.float64) * p0.inc
+    fr = (x - np.floor(x)) * 64
+    b0 = np.minimum(fr.astype(np.int64), 63)
+    b1 = stack.rotation_and_bin(p1.phase_coef, 0.0, g, p1.dtc, 64)[1]
+    edge = np.abs(fr - np.round(fr)) < 1e-6
+    assert np.array_equal(b0[~edge], b1[~edge])
+    assert np.all(np.abs((b0 - b1 + 32) % 64 - 32)[edge] <= 1)
+    w = np.random.default_rng(4).random(len(g))
+    s, h = pcd.fold(p1, w, g0)
+    assert np.array_equal(h, np.bincount(b1, minlength=64))
+    assert np.allclose(s, np.bincount(b1, weights=w, minlength=64), rtol=1e-12)
+
+
+def test_phase_model_fold_aligns_a_spinning_down_train():
+    """Unit pulses at the closed-form times where a spinning-down pulsar's phase
+    t / P - Pdot t^2 / (2 P^2) reaches n + 17/32 (the middle of bin 8 of 16,
+    rounded to the nearest 62.5 ns sample: within 3e-5 cycles) fold into that
+    bin with the model, and smear over many bins at the constant period."""
+    from oracle import stack
+    P, Pdot, nb = 1e-3, 1e-4, 16
+    t_ref, c = stack.spin_model(P, Pdot)
+    p_model = pcd.make_plan(**ORT, dm=0.0, nfft=1 << 10, nchan=1, nbins=nb, period=P, phase=(t_ref, c))
+    p_const = pcd.make_plan(**ORT, dm=0.0, nfft=1 << 10, nchan=1, nbins=nb, period=P)
+    dtc = p_model.dtc
+    n = np.arange(200)
+    t = P * (1.0 - np.sqrt(1.0 - 2.0 * Pdot * (n + 17 / 32))) / Pdot
+    gi = np.rint(t / dtc).astype(np.int64)
+    power = np.zeros(int(gi[-1]) + 10)
+    power[gi] = 1.0
+    s, h = pcd.fold(p_model, power, 0)
+    assert s[nb // 2] == len(n) and s.sum() == len(n)
+    s2, _ = pcd.fold(p_const, power, 0)
+    assert np.count_nonzero(s2) >= nb // 2
+
+
+def test_phase_model_plan_errors():
+    for bad in ((0.0, []), (0.0, [0.0] * 9), (float("nan"), [0.0, 1.0]), (0.0, [0.0, float("inf")])):
+        with pytest.raises(pcd.PlanError):
+            pcd.make_plan(**ORT, dm=0.0, nfft=1 << 10, nchan=1, nbins=16, period=1e-3, phase=bad)
+
+
 # --- the batched form (many DM trials on shared segments) ---------------------------
 
 def test_batched_trial_with_own_geometry_is_single_dm_run():
