@@ -141,7 +141,18 @@ typedef struct {
                            forward column length) and 2 <= log2 M - q <= 12, for every FFT length
                            the plan uses; else POND_E_ARG (with nfft_choices, lengths where the
                            split is not admissible are not candidates) */
-  int32_t reserved[1];
+  int32_t phase_ncoef;  /* single-DM plans: 0 = fold at the constant period_s; 1 .. 8 = fold with
+                           the polynomial phase model below instead (Sec. 3.4: the fold period
+                           comes from the TEMPO2 predictors): phi(g) = sum_i phase_coef[i] tau^i
+                           cycles, tau = g dt_c - phase_tref_s seconds from the first stream
+                           sample (dt_c = 2 nchan / fs), by Horner's rule with every FP64 multiply
+                           and add rounded on its own; bin = min(floor((phi - floor(phi)) nbins),
+                           nbins - 1).  A spin-down model (P, Pdot, epoch t_e) is {phi_0, 1/P,
+                           -Pdot / (2 P^2)} about t_e.  period_s is still required (> 0) and is
+                           what pond_meta reports.  POND_E_ARG: more than 8 coefficients,
+                           non-finite values, or a batched plan */
+  double phase_tref_s;
+  double phase_coef[8];
 } pond_opts;
 
 /* Chirp source of a single-DM plan's fused forward row pass. */

@@ -171,6 +171,7 @@ struct pond_s {
   int schedule = POND_SCHEDULE_AUTO;
   int ch = 1;                               // bytes per real sample (2: N / S added in phase)
   double dtc = 0, inc = 0;
+  FoldPhase fold_rule;                      // the fold's phase: constant period or a phase model
   long long dec_num = 1, dec_den = 1;
   int sgn = 1;
   // lanes and trials (trials in the caller's order)
@@ -279,6 +280,13 @@ int validate(const pond_opts* o) {
   if (o->input_channels < 0 || o->input_channels > 2)
     return fail(POND_E_ARG, "input_channels must be 0 or 1 (one int8 stream) or 2 (N / S pairs added in phase)");
   if (o->inv_split < 0 || o->inv_split > 12) return fail(POND_E_ARG, "inv_split must be 0 (default) or 2 .. 12");
+  if (o->phase_ncoef < 0 || o->phase_ncoef > 8) return fail(POND_E_ARG, "phase_ncoef must be 0 .. 8");
+  if (o->phase_ncoef > 0) {
+    if (o->ndm > 0) return fail(POND_E_ARG, "a phase model folds single-DM plans only");
+    if (!std::isfinite(o->phase_tref_s)) return fail(POND_E_ARG, "phase_tref_s must be finite");
+    for (int i = 0; i < o->phase_ncoef; ++i)
+      if (!std::isfinite(o->phase_coef[i])) return fail(POND_E_ARG, "phase_coef[%d] must be finite", i);
+  }
   return POND_OK;
 }
 
@@ -669,7 +677,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
       CK(cudaEventRecord(h->ev_pready[slot], cs));
       CK(cudaStreamWaitEvent(fs, h->ev_pready[slot], 0));
     }
-    CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+    CK(launch_fold_dec(P, nv, g0, h->fold_rule, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
                        h->ts + (size_t)ln.trials[0] * h->ring, h->ts_cnt + (size_t)ln.trials[0] * h->ring, h->ring,
                        h->psum, h->phits, fs));
     RC(record(h, 1 + ST_FOLD, fs));
@@ -734,7 +742,7 @@ int run_segment(pond_t h, int li, SegIn in, long long s, long long g_end) {
         CK(cudaStreamWaitEvent(cs, ln.ev_chain[(slot + NSLOT - 1) % NSLOT][q], 0));
         if (!h->multi) {
           // fold and decimation in one launch; the profile is merged when read
-          CK(launch_fold_dec(P, nv, g0, h->inc, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
+          CK(launch_fold_dec(P, nv, g0, h->fold_rule, h->nbins, h->dec_num, h->dec_den, j_lo, j_hi - j_lo + 1,
                              h->ts + (size_t)d * h->ring, h->ts_cnt + (size_t)d * h->ring, h->ring, h->psum,
                              h->phits, cs));
           RC(record(h, 1 + ST_FOLD, cs));
@@ -1355,6 +1363,11 @@ int plan_impl(pond_t* out, const pond_opts* o) {
   h->ch = o->input_channels == 2 ? 2 : 1;
   h->dtc = 2.0 * o->nchan / o->fs_hz;
   h->inc = multi ? 0.0 : h->dtc / o->period_s;
+  h->fold_rule.inc = h->inc;
+  h->fold_rule.nc = o->phase_ncoef;
+  h->fold_rule.dt = h->dtc;
+  h->fold_rule.t_ref = o->phase_tref_s;
+  for (int i = 0; i < o->phase_ncoef; ++i) h->fold_rule.c[i] = o->phase_coef[i];
   const double tdec = o->t_dec_s > 0 ? o->t_dec_s : 61.44e-6;
   h->t_dec_ns = (long long)std::llround(tdec * 1e9);
   auto bail = [&](int rc) {

@@ -139,13 +139,26 @@ __device__ __forceinline__ int fold_bin(long long g, double inc, int nbins) {
   return b < nbins - 1 ? b : nbins - 1;
 }
 
+// The bin of g under the fold's phase rule: the constant period, or the
+// polynomial phase model (Horner's rule, each FP64 multiply and add rounded
+// on its own; bin = min(floor((phi - floor(phi)) nbins), nbins - 1)).
+__device__ __forceinline__ int fold_bin(long long g, const FoldPhase& r, int nbins) {
+  if (r.nc == 0) return fold_bin(g, r.inc, nbins);
+  const double tau = __dsub_rn(__dmul_rn((double)g, r.dt), r.t_ref);
+  double x = r.c[r.nc - 1];
+  for (int k = r.nc - 2; k >= 0; --k) x = __dadd_rn(__dmul_rn(x, tau), r.c[k]);
+  const int b = (int)__dmul_rn(__dsub_rn(x, floor(x)), (double)nbins);
+  return b < nbins - 1 ? b : nbins - 1;
+}
+
 // Fold channel samples [c0, c1) of P (global index g0 + c) into this warp's
 // histogram (FOLD_WARPS warps share the chunk: warp w takes groups of
 // 32 * FOLD_U samples w, w + FOLD_WARPS, ...).  Bin b is kept at entry
 // (b - b0) mod nbins, so a chunk that spans a short cyclic run of bins starting
 // at b0 needs only that run's entries.
+template <class Rule>
 __device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long long c0, long long c1, long long g0,
-                                           double inc, int nbins, int b0, double* myh, int* myc, float* mybuf) {
+                                           const Rule& rule, int nbins, int b0, double* myh, int* myc, float* mybuf) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // FOLD_U groups of 32 samples per warp and iteration: their loads and FP64
   // bin computations are all in flight before the groups are scanned in order
@@ -159,7 +172,7 @@ __device__ __forceinline__ void fold_chunk(const float* __restrict__ P, long lon
       bv[u] = -1;
       if (i < c1) {
         pv[u] = __ldg(P + i);
-        bv[u] = fold_bin(g0 + i, inc, nbins);
+        bv[u] = fold_bin(g0 + i, rule, nbins);
       }
     }
 #pragma unroll
@@ -265,8 +278,9 @@ constexpr int DEC_SPAN = 16;
 // merged when the profile is read) and then sums each of its series samples
 // (one thread per j for spans under 64 channel samples, else one warp per j
 // with four partial sums).  Every j belongs to one CTA, so no atomics.
+template <bool MODEL>
 __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_dec(const float* __restrict__ P, long long n,
-                                                              long long g0, double inc, int nbins,
+                                                              long long g0, FoldPhase rule, int nbins,
                                                               long long num, long long den, long long j_lo,
                                                               long long nj, long long jpc,
                                                               float* __restrict__ T, int* __restrict__ C,
@@ -278,16 +292,21 @@ __global__ void __launch_bounds__(FOLD_WARPS * 32) k_fold_dec(const float* __res
   const long long jb = min(j_lo + nj, ja + jpc);
   const long long ga = max(ceil_div_ll(ja * num, den), g0);
   const long long gb = min(ceil_div_ll(jb * num, den), g0 + n);
-  // the phase grows with g, so a chunk shorter than one period (with a margin
-  // of two bins) covers the cyclic run of bins fold_bin(ga) .. fold_bin(gb - 1)
+  // at the constant period the phase grows with g, so a chunk shorter than one
+  // period (with a margin of two bins) covers the cyclic run of bins
+  // fold_bin(ga) .. fold_bin(gb - 1); a phase model keeps every bin
   int b0 = 0, used = nbins;
-  if (gb > ga && (double)(gb - 1 - ga) * inc < 1.0 - 2.0 / nbins) {
-    b0 = fold_bin(ga, inc, nbins);
-    const int b1 = fold_bin(gb - 1, inc, nbins);
+  if (!MODEL && gb > ga && (double)(gb - 1 - ga) * rule.inc < 1.0 - 2.0 / nbins) {
+    b0 = fold_bin(ga, rule.inc, nbins);
+    const int b1 = fold_bin(gb - 1, rule.inc, nbins);
     used = (b1 >= b0 ? b1 - b0 : b1 - b0 + nbins) + 1;
   }
   const FoldSmem f = fold_smem_init(fsm, nbins, used);
-  fold_chunk(P, ga - g0, gb - g0, g0, inc, nbins, b0, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
+  if constexpr (MODEL)
+    fold_chunk(P, ga - g0, gb - g0, g0, rule, nbins, b0, f.hsum + w * nbins, f.hcnt + w * nbins, f.pbuf + w * 32);
+  else
+    fold_chunk(P, ga - g0, gb - g0, g0, rule.inc, nbins, b0, f.hsum + w * nbins, f.hcnt + w * nbins,
+               f.pbuf + w * 32);
   __syncthreads();
   for (int e = threadIdx.x; e < used; e += blockDim.x) {
     double s = 0.0;
@@ -748,7 +767,9 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fold_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fold_dec, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
+    e = cudaFuncSetAttribute(k_fold_dec<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fold_dec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fold_smem_bytes(MAX_NBINS));
   return e;
 }
 
@@ -798,7 +819,7 @@ cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double inc, int nbins, long long num,
+cudaError_t launch_fold_dec(const float* P, long long n, long long g0, const FoldPhase& ph, int nbins, long long num,
                             long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
                             double* psum, long long* phits, cudaStream_t st) {
   if (n <= 0 || nj <= 0) return cudaSuccess;
@@ -814,8 +835,12 @@ cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double in
   long long jpc = std::max((nj + MAX_FOLD_PARTS - 1) / MAX_FOLD_PARTS, (FOLD_MIN_SAMPLES + per_j - 1) / per_j);
   jpc = std::min(jpc, nj);
   const unsigned parts = (unsigned)((nj + jpc - 1) / jpc);
-  k_fold_dec<<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, inc, nbins, num, den, j_lo, nj, jpc, T,
-                                                                     C, ring, psum, phits);
+  if (ph.nc > 0)
+    k_fold_dec<true><<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, ph, nbins, num, den, j_lo, nj,
+                                                                           jpc, T, C, ring, psum, phits);
+  else
+    k_fold_dec<false><<<parts, FOLD_WARPS * 32, fold_smem_bytes(nbins), st>>>(P, n, g0, ph, nbins, num, den, j_lo, nj,
+                                                                            jpc, T, C, ring, psum, phits);
   return cudaGetLastError();
 }
 

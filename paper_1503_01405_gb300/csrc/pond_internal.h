@@ -160,10 +160,19 @@ size_t fold_smem_bytes(int nbins);
 int fold_parts(long long n, long long* chunk);
 cudaError_t launch_fold(const float* P, long long n, long long g0, double inc, int nbins, double* psum,
                         int* phits, double* prof_sum, long long* prof_hits, cudaStream_t st);
+// The fold's phase rule: nc = 0 folds at the constant period (phase g inc);
+// 1 <= nc <= 8 evaluates the polynomial phi = sum_i c[i] tau^i, tau = g dt - t_ref
+// (Horner's rule, every FP64 operation rounded on its own).
+struct FoldPhase {
+  double inc = 0;
+  int nc = 0;
+  double dt = 0, t_ref = 0;
+  double c[8] = {};
+};
 // Fold + decimation of one segment (single-DM plans): the fold adds to
 // per-CTA partial rows [MAX_FOLD_PARTS][nbins] that accumulate over the
 // stream; launch_fold_snapshot merges them into the profile (replacing it).
-cudaError_t launch_fold_dec(const float* P, long long n, long long g0, double inc, int nbins, long long num,
+cudaError_t launch_fold_dec(const float* P, long long n, long long g0, const FoldPhase& ph, int nbins, long long num,
                             long long den, long long j_lo, long long nj, float* T, int* C, long long ring,
                             double* psum, long long* phits, cudaStream_t st);
 cudaError_t launch_fold_snapshot(const double* psum, const long long* phits, int nbins, double* prof_sum,

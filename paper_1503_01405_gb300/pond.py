@@ -79,7 +79,8 @@ class pond_opts(ctypes.Structure):
                 ("nfft_choices", ctypes.c_int64 * 4), ("autotune", ctypes.c_int32),
                 ("schedule", ctypes.c_int32), ("input_channels", ctypes.c_int32),
                 ("trial_mode", ctypes.c_int32), ("trials_per_launch", ctypes.c_int32),
-                ("chirp", ctypes.c_int32), ("inv_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("chirp", ctypes.c_int32), ("inv_split", ctypes.c_int32), ("phase_ncoef", ctypes.c_int32),
+                ("phase_tref_s", ctypes.c_double), ("phase_coef", ctypes.c_double * 8)]
 
 
 POND_TUNE_MAXCAND = 12
@@ -250,8 +251,11 @@ class Engine:
                  timing: bool = False, device: int = 0, epoch_mjd: tuple[int, float] = (0, 0.0),
                  precision: int = POND_FP32, dms=None, nfft_choices=(), autotune: bool = False,
                  schedule: int = POND_SCHEDULE_AUTO, input_channels: int = 1, trial_mode: int = POND_TRIALS_AUTO,
-                 trials_per_launch: int = 0, chirp: int = POND_CHIRP_AUTO, inv_split: int = 0):
-        """A single-DM plan, or with ``dms`` a batched plan over those DM trials."""
+                 trials_per_launch: int = 0, chirp: int = POND_CHIRP_AUTO, inv_split: int = 0,
+                 phase_model=None):
+        """A single-DM plan, or with ``dms`` a batched plan over those DM trials.
+        ``phase_model`` = (t_ref seconds, coefficients): fold with that polynomial
+        phase instead of the constant period (single-DM plans)."""
         o = pond_opts()
         o.f0_mhz, o.bw_mhz, o.fs_hz, o.dm = f0, bw, fs, dm
         o.nfft, o.nchan, o.nbins, o.period_s = nfft, nchan, nbins, period
@@ -267,6 +271,13 @@ class Engine:
         o.trials_per_launch = trials_per_launch
         o.chirp = chirp
         o.inv_split = inv_split
+        if phase_model is not None:
+            t_ref, coef = phase_model
+            coef = [float(c) for c in coef]
+            o.phase_ncoef = len(coef)
+            o.phase_tref_s = float(t_ref)
+            for i, c in enumerate(coef[:8]):
+                o.phase_coef[i] = c
         self._dms = None
         if dms is not None:
             self._dms = (ctypes.c_double * len(dms))(*[float(d) for d in dms])

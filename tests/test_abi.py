@@ -121,6 +121,19 @@ def test_batched_plan_validation():
         assert e.value.name == "ARG", kw
 
 
+def test_phase_model_errors():
+    """A fold phase model is checked on the host: at most 8 finite coefficients,
+    a finite reference time, single-DM plans only."""
+    base = dict(f0=326.5, bw=16.0, fs=32e6, dm=0.1, nfft=1 << 16, nchan=4, nbins=64, period=0.1)
+    for pm in ((0.0, [0.0] * 9), (float("nan"), [0.0, 10.0]), (0.0, [0.0, float("inf")])):
+        with pytest.raises(pond.PondError) as e:
+            pond.Engine(**base, phase_model=pm)
+        assert e.value.name == "ARG", pm
+    with pytest.raises(pond.PondError) as e:
+        pond.Engine(326.5, 16.0, 32e6, 0.0, 1 << 16, 4, 1, 1.0, dms=[0.1, 0.2], phase_model=(0.0, [0.0, 10.0]))
+    assert e.value.name == "ARG"
+
+
 @pytest.mark.parametrize("nfft,nchan,bad", [(1 << 16, 4, (1, 8, 11)),      # M 2^13, R2 2^7: q in 2..7
                                             (1 << 21, 16, (3, 10)),        # M 2^16, R2 2^10: q in 4..9
                                             (1 << 24, 64, (4, 8))])        # M 2^17: q in 5..7 (nchan Q1 <= 8192)

@@ -35,9 +35,10 @@ def rel(a, b):
 def run_engine(x, p, chunks=None, want_voltages=True, device_push=False, t_dec=61.44e-6,
                schedule=pond.POND_SCHEDULE_AUTO, input_channels=1, chirp=pond.POND_CHIRP_AUTO, pinned=False,
                inv_split=0):
+    pm = (p.phase_tref, list(p.phase_coef)) if p.phase_coef else None
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=t_dec,
                      want_voltages=want_voltages, schedule=schedule, input_channels=input_channels,
-                     chirp=chirp, inv_split=inv_split) as e:
+                     chirp=chirp, inv_split=inv_split, phase_model=pm) as e:
         if pinned:
             # page-locked host memory: the pieces reach the device by the copy kernel
             import torch
@@ -249,6 +250,41 @@ def test_pinned_host_push_matches_oracle():
     for k in ("s", "h", "T", "C", "V"):
         assert np.array_equal(got[k], ref[k]), k
     check(got, pcd.run(p, x, want_voltages=True))
+
+
+# The fold with a polynomial phase model in place of the constant period: a
+# spinning-down pulsar (P, Pdot about an epoch inside the stream) and a cubic
+# model with a negative reference time, on both schedules.
+PHASE_CASES = [
+    ((1 << 18, 8, 1.0, 16.0, 128, 0.03), "spin"),
+    ((1 << 16, 16, 0.3, -16.0, 64, 0.033), "cubic"),
+]
+
+
+@pytest.mark.parametrize("cfg,kind", PHASE_CASES, ids=[k for _, k in PHASE_CASES])
+def test_phase_model_fold_matches_oracle(cfg, kind):
+    """Hits exact, sums and the series (unchanged by the model) within the FP32
+    tolerance of the oracle; two push splits give the same profile bit for bit."""
+    from oracle import stack
+    nfft, nchan, dm, bw, nbins, period = cfg
+    if kind == "spin":
+        model = stack.spin_model(period, 3e-4, 0.0123, 0.25)
+    else:
+        model = (-0.5, [0.1, 1.0 / period, 2e-3, -7e-4])
+    p = pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period, phase=model)
+    x = _stream(p, seed=nfft + 17, extra=9)
+    r = pcd.run(p, x)
+    scheds = (pond.POND_SCHEDULE_AUTO, pond.POND_SCHEDULE_FOUR_PASS)
+    outs = []
+    for sched in scheds:
+        out = run_engine(x, p, want_voltages=False, schedule=sched)
+        check(out, r, voltages=False)
+        outs.append(out)
+    cut = run_engine(x, p, want_voltages=False, chunks=[len(x) // 3, len(x) - len(x) // 3])
+    assert np.array_equal(cut["s"], outs[0]["s"]) and np.array_equal(cut["h"], outs[0]["h"])
+    # the model moves samples between bins: the constant-period profile differs
+    const = pcd.fold(pcd.make_plan(326.5, bw, 32e6, dm, nfft, nchan, nbins, period), r.power, r.first_g)[1]
+    assert not np.array_equal(const, r.prof_hits)
 
 
 def test_series_into_pinned_arrays():
