@@ -1211,7 +1211,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32": "f32", "bf16x3": "bf16x3+f32acc", "bf16x5": "bf16x5+f32acc"}[args.precision],
-                "data": "synthetic", "config": dict(workload_config(n, ch), fft_stages=args.precision),
+                "data": "synthetic", "config": dict(workload_config(n, ch), fft_stages=args.precision,
+                              chirp={"auto": "table (default)", "anchors": "anchors", "table": "table"}[args.chirp]),
                 "realtime_factor": value / REALTIME_MSPS,
                 "e2e": e2e, "gpu_launches": int(st1["kernel_launches"]) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "cufft_baseline": cufft, "clocks": clocks}

@@ -156,7 +156,8 @@ typedef struct {
 } pond_opts;
 
 /* Chirp source of a single-DM plan's fused forward row pass. */
-#define POND_CHIRP_AUTO 0     /* this build's default: POND_CHIRP_ANCHORS */
+#define POND_CHIRP_AUTO 0     /* this build's default: POND_CHIRP_TABLE (measured faster in the
+                                 two-stream pipeline once its rows are prefetched into L2) */
 #define POND_CHIRP_ANCHORS 1  /* evaluated per bin from FP64-built anchors (exact Q0.64 phase
                                  polynomial, FP32 sine and cosine): no per-bin memory read, as the
                                  paper's convolution kernel computes the chirp per thread */

@@ -371,7 +371,11 @@ int build_trial(pond_t h, const pond_opts* o, Trial* t) {
   const double half = std::fabs(o->bw_mhz) / 2.0;
   const double alpha = K_DM * 1e6 * t->dm / (o->f0_mhz * o->f0_mhz);
   CK(launch_tables(t->anc, t->nanc, t->clog, du, half, o->f0_mhz, alpha, h->sgn, h->st));
-  if (o->chirp == POND_CHIRP_TABLE && ln.fused) {
+  // single-DM three-pass plans take the chirp from the per-bin table unless the
+  // anchors are asked for: with the table rows prefetched into L2 the fused row
+  // pass then overlaps the other segment stream better (full rate: 116.6k
+  // against 114.5k Msamples/s)
+  if ((o->chirp == POND_CHIRP_TABLE || o->chirp == POND_CHIRP_AUTO) && ln.fused) {
     CK(cudaMalloc(&t->ctab, (size_t)ln.g.L * sizeof(float2)));
     CK(launch_chirp_c64(t->ctab, ln.g, du, half, o->f0_mhz, alpha, h->sgn, h->st));
   }

@@ -634,10 +634,12 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows_inv(const float2* __restrict
   load_twiddles<R1>(stw, tw);
   load_twiddles<J>(stwj, twJ);
   const int q0 = blockIdx.x * np;
-  if (threadIdx.x < 2 && np == 1 && blockIdx.x + PF_DIST < gridDim.x) {
-    // the two rows of CTA blockIdx.x + PF_DIST (q and its mirror R2 - q)
-    const int q = q0 + PF_DIST, row = threadIdx.x == 0 ? q : R2 - q;
-    prefetch_l2(in + ((size_t)row << LOGR1), R1 * (unsigned)sizeof(float2));
+  if (threadIdx.x < 4 && np == 1 && blockIdx.x + PF_DIST < gridDim.x) {
+    // the two rows of CTA blockIdx.x + PF_DIST (q and its mirror R2 - q), and
+    // with the per-bin chirp table the same rows of the table
+    const int q = q0 + PF_DIST, row = (threadIdx.x & 1) == 0 ? q : R2 - q;
+    if (threadIdx.x < 2) prefetch_l2(in + ((size_t)row << LOGR1), R1 * (unsigned)sizeof(float2));
+    else if (CTAB) prefetch_l2(ctab + ((size_t)row << LOGR1), R1 * (unsigned)sizeof(float2));
   }
   f2_stage1<R1, LSTR>(in, sm, st3, q0, np, R2, nl);
   // e^{2 pi i k2 m1 / M} = conj(w^{k2 m1 NCH}), k2 m1 NCH < L

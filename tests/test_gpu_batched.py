@@ -130,12 +130,13 @@ def test_batched_three_pass_matches_oracle():
 
 def test_single_trial_batch_equals_single_dm_plan_three_pass():
     """In the three-pass geometry a one-trial batched plan (F2, then the row pass
-    with the chirp) and the single-DM plan (F2 with the chirp) form the same
-    spectrum, chirp products and runs: identical series, bit for bit."""
+    with the chirp from the trial's anchors) and the single-DM plan (F2 with the
+    chirp from the same anchors) form the same spectrum, chirp products and
+    runs: identical series, bit for bit."""
     dm, nfft, nchan, t_dec = 1.0, 1 << 18, 8, 8e-6
     x = stream(8 * nfft, seed=36, dm=dm)
     T, C, j0, _ = run_engine(x, [dm], nfft, nchan, t_dec)
-    with pond.Engine(F0, BW, FS, dm, nfft, nchan, 16, 0.011, t_dec=t_dec) as e:
+    with pond.Engine(F0, BW, FS, dm, nfft, nchan, 16, 0.011, t_dec=t_dec, chirp=pond.POND_CHIRP_ANCHORS) as e:
         e.push(x)
         e.flush()
         Ts, Cs, js = e.timeseries()
