@@ -1,13 +1,15 @@
-"""The full-rate workload at its full size, in the launch configuration the
-benchmark times, against the oracle on sampled outputs and on properties that
-hold at any size.
+"""The full-rate and batched workloads at their full sizes, in the launch
+configurations the benchmark times, against the oracle on sampled outputs and
+on properties that hold at any size.
 
 The 60 s stream (1.92e9 int8 samples, 326.5 MHz / 16 MHz, DM 26.8, nfft 2^24,
 64 sub-channels, 1024 bins, 61.44 us series) goes through the engine as one
 device push on two segment streams.  The oracle (FP64) then recomputes three
 sampled stretches of the series (the first segment, one in the middle, the last
 emitted samples) from the same input bytes, and the whole fold's hit counts
-from its bin rule over every emitted channel sample.
+from its bin rule over every emitted channel sample.  The batched chunk (8 s,
+128 DM trials 0..60, FFT lengths chosen by the autotuner) is checked on three
+trials over a stretch of one segment.
 """
 import numpy as np
 import pytest
@@ -97,3 +99,49 @@ def test_fold_hits_and_conservation(full_run):
     assert abs(r["s"].sum() - r["T"].astype(np.float64).sum()) <= 1e-5 * r["s"].sum()
     prof = r["s"] / np.maximum(r["h"], 1)
     assert abs(int(np.argmax(prof)) - p.nbins // 2) <= 20
+
+
+# --- the batched workload at its full size: one 8 s chunk, 128 DM trials 0..60 ---
+
+@pytest.fixture(scope="module")
+def batched_run():
+    import torch
+    dev = torch.device("cuda", 0)
+    spec = synth.BATCH_CHUNK
+    pulses = synth.draw_pulses(spec.seed, 10, spec.n / spec.fs)
+    x_dev = synth.make_chunk_torch(spec, pulses, dev)
+    with pond.Engine(PLAN["f0"], PLAN["bw"], PLAN["fs"], 0.0, 1 << 24, 64, 1, 1.0, t_dec=32e-6,
+                     dms=synth.BATCH_DMS, nfft_choices=(1 << 22, 1 << 23, 1 << 24), autotune=True) as e:
+        e.push_tensor(x_dev)
+        e.flush()
+        T, C, j0 = e.timeseries(cap=1 << 19)
+        dms, nf = e.trials()
+    x = x_dev.cpu().numpy()
+    del x_dev
+    torch.cuda.empty_cache()
+    return dict(x=x, T=T, C=C, j0=j0, dms=dms, nf=nf)
+
+
+@pytest.mark.parametrize("d", [0, 64, 127])
+def test_batched_chunk_sampled_trials_match_oracle(batched_run, d):
+    """Trial d of the autotuned 128-trial chunk on a stretch of one segment in
+    the middle of the chunk: the oracle runs the single-DM path at DM_d on the
+    trial's group segmentation (its FFT length, the group's largest DM) over
+    the stretch; complete series samples match (counts exact, FP32 tolerance)."""
+    r = batched_run
+    nf = r["nf"]
+    dm = float(r["dms"][d])
+    gmax = max(float(r["dms"][i]) for i in range(len(nf)) if nf[i] == nf[d])
+    base = pcd.make_plan(PLAN["f0"], PLAN["bw"], PLAN["fs"], 0.0, int(nf[d]), 64, 1, 1.0, 32e-6)
+    q = pcd.trial_plan(base, dm, gmax)
+    g_lo, g_hi = pcd.batched_range(base, max(float(v) for v in r["dms"]), len(r["x"]))
+    ga = (g_lo + g_hi) // 2
+    gb = min(ga + q.S_c, g_hi)
+    o = pcd.run(q, r["x"], g_range=(ga, gb))
+    num, den = q.dec.numerator, q.dec.denominator
+    j_lo, j_hi = -(-ga * den // num), (gb * den) // num
+    assert j_hi - j_lo > 1000
+    eo = slice(j_lo - o.ts_first, j_hi - o.ts_first)
+    ee = slice(j_lo - r["j0"], j_hi - r["j0"])
+    assert np.array_equal(o.ts_counts[eo], r["C"][ee])
+    assert rel(r["T"][d][ee], o.ts[eo]) <= TOL_P, (d, rel(r["T"][d][ee], o.ts[eo]))
