@@ -271,3 +271,20 @@ def test_autotuned_split_outside_the_three_pass_geometry():
     for d, r in enumerate(res):
         assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
         assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
+
+
+def test_batched_series_into_pinned_arrays(grid_case):
+    """pond_timeseries of a batched plan into page-locked [ndm, cap] arrays (rows
+    copied there directly) returns the default drain's rows bit for bit."""
+    import torch
+    x, nfft, nchan, t_dec, _ = grid_case
+    T, C, j0, _ = run_engine(x, GRID, nfft, nchan, t_dec)
+    cap = T.shape[1] + 64
+    Tp = torch.zeros((len(GRID), cap), dtype=torch.float32, pin_memory=True).numpy()
+    Cp = torch.zeros(cap, dtype=torch.int32, pin_memory=True).numpy()
+    with pond.Engine(F0, BW, FS, 0.0, nfft, nchan, 1, 1.0, t_dec=t_dec, dms=GRID) as e:
+        e.push(x)
+        e.flush()
+        n, j = e.timeseries_into(Tp, Cp)
+    assert n == T.shape[1] and j == j0
+    assert np.array_equal(Tp[:, :n], T) and np.array_equal(Cp[:n], C)

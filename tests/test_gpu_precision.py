@@ -39,9 +39,9 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
 
 
-def run_engine(x, p, precision, want_voltages=True, chunks=None):
+def run_engine(x, p, precision, want_voltages=True, chunks=None, **kw):
     with pond.Engine(p.f0, p.bw, p.fs, p.dm, p.nfft, p.nchan, p.nbins, p.period, t_dec=p.t_dec_ns * 1e-9,
-                     want_voltages=want_voltages, precision=precision) as e:
+                     want_voltages=want_voltages, precision=precision, **kw) as e:
         pos = 0
         for c in (chunks or [len(x)]):
             e.push(x[pos:pos + c])
@@ -99,6 +99,18 @@ def test_precision_matches_oracle(cfg, prec):
         x = _stream(p, seed=nfft + nchan, extra=17)
     r = pcd.run(p, x, want_voltages=True)
     check(run_engine(x, p, prec), r)
+
+
+@pytest.mark.parametrize("prec", PRECISIONS, ids=lambda v: PNAME[v])
+def test_precision_at_other_inverse_splits(prec):
+    """The four-pass tensor-core inverse at splits other than the default (I1's
+    columns of Q2 and I2's rows of Q1 as DFT-matrix stages of other lengths)
+    against the oracle: nfft 2^16, 16 sub-channels (M 2^11, default split 2^6)."""
+    p = pcd.make_plan(326.5, 16.0, 32e6, 0.3, 1 << 16, 16, 128, 0.033)
+    x = _stream(p, seed=77, extra=3)
+    r = pcd.run(p, x, want_voltages=True)
+    for q in (3, 5, 7):
+        check(run_engine(x, p, prec, schedule=pond.POND_SCHEDULE_FOUR_PASS, inv_split=q), r)
 
 
 @pytest.mark.parametrize("prec", PRECISIONS, ids=lambda v: PNAME[v])
