@@ -675,10 +675,10 @@ size_t smem_inv_rows_chirp(int R1, int nl) {
   return ((size_t)TW3_SN + stage_table_size(FUSED_J) + (size_t)nl * FUSED_J + (size_t)nl * (R1 + R1 / 16)) *
          sizeof(float2);
 }
-// k_inv_rows_chirp_multi: the row pass's tables and tile plus the resident rows
-// (8 bytes per bin) and, with the table chirp, their table words (4 bytes per bin)
-size_t smem_inv_rows_multi(int R1, int nl, bool table) {
-  return smem_inv_rows_chirp(R1, nl) + (size_t)nl * R1 * (sizeof(float2) + (table ? sizeof(unsigned) : 0));
+// k_inv_rows_chirp_res: the row pass's tables and tile plus the resident rows
+// (8 bytes per bin) and their table words (4 bytes per bin)
+size_t smem_inv_rows_res(int R1, int nl) {
+  return smem_inv_rows_chirp(R1, nl) + (size_t)nl * R1 * (sizeof(float2) + sizeof(unsigned));
 }
 }  // namespace
 
@@ -701,16 +701,18 @@ cudaError_t launch_inv_rows_chirp_multi(const Geom& g, const float2* in, float2*
   const int R2 = 1 << g.logR2, R1 = 1 << g.logR1;
   const int nl = std::min(TILE / R1, R2);
   if (ntr < 1) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)(R2 / nl);
+  // table form: one CTA per row tile runs every trial; anchor form: one CTA
+  // per (trial, row tile)
+  const unsigned tiles = (unsigned)(R2 / nl);
   switch (R1) {
 #define CASE(R)                                                                                             \
   case R:                                                                                                   \
     if (table)                                                                                              \
-      k_inv_rows_chirp_multi<R, FUSED_J, true><<<grid, NT, smem_inv_rows_multi(R, nl, true), st>>>(         \
-          in, out, g.L, g.logR2, tw3L, twJ, mc, ntr);                                                       \
+      k_inv_rows_chirp_res<R, FUSED_J><<<tiles, NT, smem_inv_rows_res(R, nl), st>>>(in, out, g.L, g.logR2,  \
+                                                                                    tw3L, twJ, mc, ntr);    \
     else                                                                                                    \
-      k_inv_rows_chirp_multi<R, FUSED_J, false><<<grid, NT, smem_inv_rows_multi(R, nl, false), st>>>(       \
-          in, out, g.L, g.logR2, tw3L, twJ, mc, ntr);                                                       \
+      k_inv_rows_chirp_multi<R, FUSED_J><<<dim3((unsigned)ntr, tiles), NT, smem_inv_rows_chirp(R, nl), st>>>( \
+          in, out, g.L, g.logR2, tw3L, twJ, mc);                                                            \
     break;
     POND_FUSED_R1(CASE)
 #undef CASE
@@ -757,13 +759,11 @@ cudaError_t set_kernel_attributes() {
 #undef SET_I
 #define SET_M(R)                                                                                       \
   if (e == cudaSuccess)                                                                                \
-    e = cudaFuncSetAttribute(k_inv_rows_chirp_multi<R, FUSED_J, true>,                                 \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                                 \
-                             (int)smem_inv_rows_multi(R, TILE / R, true));                                \
+    e = cudaFuncSetAttribute(k_inv_rows_chirp_res<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem_inv_rows_res(R, TILE / R));                                        \
   if (e == cudaSuccess)                                                                                \
-    e = cudaFuncSetAttribute(k_inv_rows_chirp_multi<R, FUSED_J, false>,                                \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,                                 \
-                             (int)smem_inv_rows_multi(R, TILE / R, false));
+    e = cudaFuncSetAttribute(k_inv_rows_chirp_multi<R, FUSED_J>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)smem_inv_rows_chirp(R, TILE / R));
   POND_FUSED_R1(SET_M)
 #undef SET_M
 #define SET_C(R) \

@@ -732,21 +732,21 @@ __device__ __forceinline__ float2 chirp_q32(unsigned u) {
   return make_float2(c, -s);
 }
 
-// IrK: Ir for the ntr trials of one batched launch with the rows resident.
-// CTA y (one per SM, R2 / nl of them) loads its nl rows of the shared spectrum
-// (and, in the table form, their table words, stored in the spectrum's row
-// layout) into shared memory once, then runs every trial of the launch on
-// them: the trial's chirp, F2f's length-64 runs and the blocked store for the
-// column pass, to out + t out_tstride.  The rows are read from L2 or HBM once
-// per launch instead of once per trial (per trial and segment 51.3 -> 46.5 us
-// with 32 trials per launch; one trial per CTA at two CTAs per SM waited on
-// those reads).
-template <int R1, int J, bool TABLE>
-__global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_multi(const float2* __restrict__ in,
-                                                                float2* __restrict__ out, long long out_tstride,
-                                                                int logR2, const float2* __restrict__ tw3L,
-                                                                const float2* __restrict__ twJ, MultiChirp mc,
-                                                                int ntr) {
+// IrK, table form: Ir for the ntr trials of one batched launch with the rows
+// resident.  CTA b (one per SM, R2 / nl of them) loads its nl rows of the
+// shared spectrum and their table words (stored in the spectrum's row layout)
+// into shared memory once, then runs every trial of the launch on them: the
+// trial's chirp, F2f's length-64 runs and the blocked store for the column
+// pass, to out + t out_tstride.  The rows are read from L2 or HBM once per
+// launch instead of once per trial (per trial and segment, passes and
+// decimation: 51.3 -> 48.2 us with 32 trials per launch; one trial per CTA at
+// two CTAs per SM waited on those reads).
+template <int R1, int J>
+__global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_res(const float2* __restrict__ in,
+                                                              float2* __restrict__ out, long long out_tstride,
+                                                              int logR2, const float2* __restrict__ tw3L,
+                                                              const float2* __restrict__ twJ, MultiChirp mc,
+                                                              int ntr) {
   static_assert(J == 64 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
   constexpr int NCH = R1 / J;
   constexpr int LSTR = R1 + R1 / 16;
@@ -759,8 +759,8 @@ __global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_multi(const float2* __
   const int nl = min(TILE / R1, R2);
   const int tot = nl * R1;
   float4* raw = reinterpret_cast<float4*>(twk + nl * J);          // the rows, two bins per entry
-  uint2* tabw = reinterpret_cast<uint2*>(raw + tot / 2);          // their table words (TABLE)
-  float2* sm = TABLE ? reinterpret_cast<float2*>(tabw + tot / 2) : reinterpret_cast<float2*>(tabw);
+  uint2* tabw = reinterpret_cast<uint2*>(raw + tot / 2);          // their table words
+  float2* sm = reinterpret_cast<float2*>(tabw + tot / 2);
   const int r0 = blockIdx.x * nl;
   load_tw3(st3, tw3L);
   load_twiddles<J>(stwj, twJ);
@@ -768,7 +768,7 @@ __global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_multi(const float2* __
   const uint2* a2 = reinterpret_cast<const uint2*>(mc.atab) + ((size_t)r0 << (LOGR1 - 1));
   for (int i = threadIdx.x; i < tot / 2; i += NT) {
     raw[i] = __ldg(in4 + i);
-    if (TABLE) tabw[i] = __ldg(a2 + i);
+    tabw[i] = __ldg(a2 + i);
   }
   __syncthreads();   // st3 and the rows
   for (int i = threadIdx.x; i < nl * J; i += NT) {
@@ -776,33 +776,87 @@ __global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_multi(const float2* __
     twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
   }
   for (int t = 0; t < ntr; ++t) {
-    if constexpr (TABLE) {
-      const unsigned nm = __ldg(mc.nmul + t);
-      for (int i = threadIdx.x; i < tot / 2; i += NT) {
-        const int idx = 2 * i, slot = idx >> LOGR1, k1 = idx & (R1 - 1);
-        const float4 rv = raw[i];
-        const uint2 w = tabw[i];
-        float2* p = sm + pidx(slot, k1, LSTR);
-        p[0] = cmul(make_float2(rv.x, rv.y), chirp_q32(nm * w.x));
-        p[1] = cmul(make_float2(rv.z, rv.w), chirp_q32(nm * w.y));
-      }
-    } else {
-      const ChirpAnchor* anc = mc.anc[t];
-      const int clog = __ldg(mc.clog + t);
-      for (int i = threadIdx.x; i < tot / 2; i += NT) {
-        const int idx = 2 * i, slot = idx >> LOGR1, k1 = idx & (R1 - 1);
-        const float4 rv = raw[i];
-        const unsigned ka = (unsigned)(r0 + slot) + ((unsigned)k1 << logR2), kb = ka + (1u << logR2);
-        const ChirpAnchor a = anc[ka >> clog], b = anc[kb >> clog];
-        float2* p = sm + pidx(slot, k1, LSTR);
-        p[0] = cmul(make_float2(rv.x, rv.y), chirp_from(a, clog, ka));
-        p[1] = cmul(make_float2(rv.z, rv.w), chirp_from(b, clog, kb));
-      }
+    const unsigned nm = __ldg(mc.nmul + t);
+    for (int i = threadIdx.x; i < tot / 2; i += NT) {
+      const int idx = 2 * i, slot = idx >> LOGR1, k1 = idx & (R1 - 1);
+      const float4 rv = raw[i];
+      const uint2 w = tabw[i];
+      float2* p = sm + pidx(slot, k1, LSTR);        // k1 even: no pad between the two
+      p[0] = cmul(make_float2(rv.x, rv.y), chirp_q32(nm * w.x));
+      p[1] = cmul(make_float2(rv.z, rv.w), chirp_q32(nm * w.y));
     }
     __syncthreads();   // the chirped tile (and twk, before the first trial)
     j_runs<R1, J>(sm, stwj, twk, out + (size_t)t * out_tstride, nl, logR2, [&](int slot) { return r0 + slot; });
     __syncthreads();   // the tile is free for the next trial
   }
+}
+
+// IrK, anchor form: Ir for the ntr trials of one batched launch, one trial per
+// CTA.  blockIdx.y is the row tile (nl rows of the shared spectrum) and
+// blockIdx.x the trial, so the CTAs that read the same rows are adjacent in
+// launch order and find them in L2 after the first.  Trial t's output (the
+// blocked layout of F2f) goes to out + t out_tstride.  The anchor chirp costs
+// about 20 more instructions per bin than the table's, and two CTAs per SM
+// hide them better than the rows-resident form's one (per trial and segment,
+// 32 trials per launch: 55.1 us here, 57.8 with the rows and each trial's
+// anchors resident).
+template <int R1, int J>
+__global__ void __launch_bounds__(NT, 2) k_inv_rows_chirp_multi(const float2* __restrict__ in,
+                                                                float2* __restrict__ out, long long out_tstride,
+                                                                int logR2, const float2* __restrict__ tw3L,
+                                                                const float2* __restrict__ twJ, MultiChirp mc) {
+  static_assert(J == 64 && R1 % (4 * J) == 0 && R1 >= NT, "row layout of the fused pass");
+  constexpr int NCH = R1 / J;
+  constexpr int LSTR = R1 + R1 / 16;
+  constexpr int LOGJ = ilog2c(J), LOGNCH = ilog2c(NCH), LOGR1 = ilog2c(R1);
+  extern __shared__ float2 smem[];
+  float2* st3 = smem;                              // [TW3_SN], w = exp(-2 pi i / L)
+  float2* stwj = st3 + TW3_SN;
+  float2* twk = stwj + stage_table_size(J);        // [nl][J]: e^{2 pi i k2 m1 / M}
+  const int R2 = 1 << logR2;
+  const int nl = min(TILE / R1, R2);
+  float2* sm = twk + nl * J;
+  const int t = blockIdx.x;
+  const int r0 = blockIdx.y * nl;
+  const int tot = nl * R1;
+  if (t == 0 && threadIdx.x == 0) {
+    // trials run fastest in launch order: the first trial's CTA of a row tile
+    // warms L2 with the rows of a later tile
+    const unsigned rn = blockIdx.y + max(1u, (unsigned)PF_DIST / gridDim.x);
+    if (rn < gridDim.y) prefetch_l2(in + (((size_t)rn * nl) << LOGR1), (unsigned)tot * (unsigned)sizeof(float2));
+  }
+  load_tw3(st3, tw3L);
+  load_twiddles<J>(stwj, twJ);
+  // rows r0 .. r0 + nl - 1 are contiguous: 16-byte loads of columns k1, k1 + 1
+  const float4* in4 = reinterpret_cast<const float4*>(in) + ((size_t)r0 << (LOGR1 - 1));
+  constexpr int H = EPT / 2;
+  float4 r[H];
+#pragma unroll
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * ((int)threadIdx.x + u * NT);
+    if (idx < tot) r[u] = __ldg(in4 + (idx >> 1));
+  }
+  const ChirpAnchor* anc = mc.anc[t];
+  const int clog = __ldg(mc.clog + t);
+#pragma unroll
+  for (int u = 0; u < H; ++u) {
+    const int idx = 2 * ((int)threadIdx.x + u * NT);
+    if (idx < tot) {
+      const int slot = idx >> LOGR1, k1 = idx & (R1 - 1);
+      const unsigned ka = (unsigned)(r0 + slot) + ((unsigned)k1 << logR2), kb = ka + (1u << logR2);
+      const ChirpAnchor a = anc[ka >> clog], b = anc[kb >> clog];
+      float2* p = sm + pidx(slot, k1, LSTR);
+      p[0] = cmul(make_float2(r[u].x, r[u].y), chirp_from(a, clog, ka));
+      p[1] = cmul(make_float2(r[u].z, r[u].w), chirp_from(b, clog, kb));
+    }
+  }
+  __syncthreads();   // st3 and the tile
+  for (int i = threadIdx.x; i < nl * J; i += NT) {
+    const unsigned k2 = (unsigned)(r0 + (i >> LOGJ)), m1 = (unsigned)(i & (J - 1));
+    twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
+  }
+  __syncthreads();
+  j_runs<R1, J>(sm, stwj, twk, out + (size_t)t * out_tstride, nl, logR2, [&](int slot) { return r0 + slot; });
 }
 
 // ---------------------------------------------------------------------------

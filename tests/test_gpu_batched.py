@@ -217,6 +217,39 @@ def test_table_form_falls_back_to_anchors_off_grid():
         assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
 
 
+def test_multi_anchor_form_in_a_wide_low_band():
+    """A wide low band (150 MHz, 100 MHz wide, 200 MHz sampling, nfft 2^21):
+    the chirp's curvature asks for 32 to 4096 anchors per trial (2^15 down to
+    2^8 bins per anchor) within one launch.  The multi-trial anchor form gives
+    the per-trial launches' series bit for bit, and the oracle's."""
+    f0, bw, fs = 150.0, 100.0, 200e6
+    dms = [0.0, 0.004, 0.008, 0.012, 0.016]
+    nfft, nchan, t_dec = 1 << 21, 16, 16e-6
+    p = pcd.make_plan(f0, bw, fs, max(dms), nfft, nchan, 1, 1.0, t_dec)
+    x = synth.make_stream(synth.StreamSpec(n=3 * p.S + nfft + 777, seed=41, fs=fs, f0=f0, bw=bw, dm=0.008,
+                                           period=0.0041, snr=80.0, duty=0.05))
+
+    def run(mode, kt):
+        with pond.Engine(f0, bw, fs, 0.0, nfft, nchan, 1, 1.0, t_dec=t_dec, dms=dms, trial_mode=mode,
+                         trials_per_launch=kt) as e:
+            e.push(x)
+            e.flush()
+            T, C, j0 = e.timeseries()
+            info = e.tuning()
+        return T, C, j0, info
+
+    a = run(pond.POND_TRIALS_PER_TRIAL, 0)
+    for kt in (0, 3):
+        b = run(pond.POND_TRIALS_MULTI_ANCHOR, kt)
+        assert b[3][0]["mode"] == "multi-anchor"
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2], kt
+    base = pcd.make_plan(f0, bw, fs, 0.0, nfft, nchan, 1, 1.0, t_dec)
+    res = pcd.run_batched(base, [(dm, nfft, max(dms)) for dm in dms], x)
+    for d, r in enumerate(res):
+        assert a[2] == r.ts_first and np.array_equal(a[1], r.ts_counts)
+        assert rel(a[0][d], r.ts) <= TOL, (d, rel(a[0][d], r.ts))
+
+
 def test_trial_autotuner_times_every_form(grid_case):
     """With autotune the lane's forms (per-trial launches; anchors and table at 8
     and 32 trials per launch, clipped to the trial count; the four-pass form at
