@@ -676,9 +676,9 @@ size_t smem_inv_rows_chirp(int R1, int nl) {
          sizeof(float2);
 }
 // k_inv_rows_chirp_res: the row pass's tables and tile plus the resident rows
-// (8 bytes per bin) and their table words (4 bytes per bin)
+// (8 bytes per bin) and their table words (4 bytes per bin), in the tile's layout
 size_t smem_inv_rows_res(int R1, int nl) {
-  return smem_inv_rows_chirp(R1, nl) + (size_t)nl * R1 * (sizeof(float2) + sizeof(unsigned));
+  return smem_inv_rows_chirp(R1, nl) + (size_t)nl * (R1 + R1 / 16) * (sizeof(float2) + sizeof(unsigned));
 }
 }  // namespace
 

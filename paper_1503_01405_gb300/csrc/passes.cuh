@@ -552,9 +552,11 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_rows(const float2* __restrict__ i
 // to t' + 16 j), then twk[slot][m1] = e^{2 pi i k2 m1 / M} and the store of
 // element (k2 = row_of(slot), m1, c) at ((m1 G + g) R2 + k2) nl_c + ci,
 // c = g nl_c + ci, nl_c = min(8192 / R2, NCH) (the column pass's blocks).
-template <int R1, int J, class RowOf>
-__device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const float2* twk, float2* __restrict__ out,
-                                       int nl, int logR2, RowOf row_of) {
+// The run's first read takes element o of the tile (its offset in the padded
+// layout) from load(o); the runs' stores go to sm.
+template <int R1, int J, class RowOf, class Load>
+__device__ __forceinline__ void j_runs_load(float2* sm, const float2* stwj, const float2* twk,
+                                            float2* __restrict__ out, int nl, int logR2, RowOf row_of, Load load) {
   static_assert(J == 64, "radix-16 x radix-4 runs");
   constexpr int NCH = R1 / J;
   constexpr int LSTR = R1 + R1 / 16;
@@ -563,10 +565,11 @@ __device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const flo
   const int run = (int)threadIdx.x >> 2, t4 = (int)threadIdx.x & 3;
   if (run < nl * NCH) {                            // whole warps (8 runs each) in or out
     const int slot = run >> LOGNCH, c = run & (NCH - 1);
-    float2* line = sm + slot * LSTR + c * (J + J / 16);
+    const int lo = slot * LSTR + c * (J + J / 16);
+    float2* line = sm + lo;
     float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = line[pidx(0, t4 + 4 * i, 0)];
+    for (int i = 0; i < 16; ++i) v[i] = load(lo + pidx(0, t4 + 4 * i, 0));
     Dft<16, true>::run(v);
     __syncwarp();                                  // the run is read before it is overwritten
 #pragma unroll
@@ -592,6 +595,13 @@ __device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const flo
       }
     }
   }
+}
+
+// The runs of the tile held in sm.
+template <int R1, int J, class RowOf>
+__device__ __forceinline__ void j_runs(float2* sm, const float2* stwj, const float2* twk, float2* __restrict__ out,
+                                       int nl, int logR2, RowOf row_of) {
+  j_runs_load<R1, J>(sm, stwj, twk, out, nl, logR2, row_of, [&](int o) { return sm[o]; });
 }
 
 // ---------------------------------------------------------------------------
@@ -733,14 +743,16 @@ __device__ __forceinline__ float2 chirp_q32(unsigned u) {
 }
 
 // IrK, table form: Ir for the ntr trials of one batched launch with the rows
-// resident.  CTA b (one per SM, R2 / nl of them) loads its nl rows of the
+// resident.  CTA b (one per SM, R2 / nl of them) copies its nl rows of the
 // shared spectrum and their table words (stored in the spectrum's row layout)
-// into shared memory once, then runs every trial of the launch on them: the
-// trial's chirp, F2f's length-64 runs and the blocked store for the column
-// pass, to out + t out_tstride.  The rows are read from L2 or HBM once per
-// launch instead of once per trial (per trial and segment, passes and
-// decimation: 51.3 -> 48.2 us with 32 trials per launch; one trial per CTA at
-// two CTAs per SM waited on those reads).
+// into shared memory once, in the tile's padded layout, then runs every trial
+// of the launch on them: each length-64 run applies the trial's chirp as it
+// first reads its bins from those copies, and its F2f steps and blocked store
+// for the column pass go to out + t out_tstride.  A run is read and written
+// by the same four lanes, so the trials need no block barrier.  The rows are
+// read from L2 or HBM once per launch instead of once per trial (per trial and
+// segment, passes and decimation: 51.3 us one trial per CTA at two CTAs per
+// SM, 48.2 with the rows resident and a chirped tile per trial).
 template <int R1, int J>
 __global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_res(const float2* __restrict__ in,
                                                               float2* __restrict__ out, long long out_tstride,
@@ -758,36 +770,34 @@ __global__ void __launch_bounds__(NT, 1) k_inv_rows_chirp_res(const float2* __re
   const int R2 = 1 << logR2;
   const int nl = min(TILE / R1, R2);
   const int tot = nl * R1;
-  float4* raw = reinterpret_cast<float4*>(twk + nl * J);          // the rows, two bins per entry
-  uint2* tabw = reinterpret_cast<uint2*>(raw + tot / 2);          // their table words
-  float2* sm = reinterpret_cast<float2*>(tabw + tot / 2);
+  float2* rows = twk + nl * J;                     // [nl * LSTR], the tile's layout
+  float2* sm = rows + nl * LSTR;                   // [nl * LSTR], the runs' exchange
+  unsigned* tabw = reinterpret_cast<unsigned*>(sm + nl * LSTR);   // [nl * LSTR], the rows' table words
   const int r0 = blockIdx.x * nl;
   load_tw3(st3, tw3L);
   load_twiddles<J>(stwj, twJ);
   const float4* in4 = reinterpret_cast<const float4*>(in) + ((size_t)r0 << (LOGR1 - 1));
   const uint2* a2 = reinterpret_cast<const uint2*>(mc.atab) + ((size_t)r0 << (LOGR1 - 1));
   for (int i = threadIdx.x; i < tot / 2; i += NT) {
-    raw[i] = __ldg(in4 + i);
-    tabw[i] = __ldg(a2 + i);
+    const int idx = 2 * i, o = pidx(idx >> LOGR1, idx & (R1 - 1), LSTR);   // k1 even: o + 1 is k1 + 1
+    const float4 rv = __ldg(in4 + i);
+    const uint2 w = __ldg(a2 + i);
+    rows[o] = make_float2(rv.x, rv.y);
+    rows[o + 1] = make_float2(rv.z, rv.w);
+    tabw[o] = w.x;
+    tabw[o + 1] = w.y;
   }
-  __syncthreads();   // st3 and the rows
+  __syncthreads();   // st3
   for (int i = threadIdx.x; i < nl * J; i += NT) {
     const unsigned k2 = (unsigned)(r0 + (i >> LOGJ)), m1 = (unsigned)(i & (J - 1));
     twk[i] = cconj(tw3(st3, (k2 * m1) << LOGNCH));
   }
+  __syncthreads();   // twk, the rows and their table words
   for (int t = 0; t < ntr; ++t) {
     const unsigned nm = __ldg(mc.nmul + t);
-    for (int i = threadIdx.x; i < tot / 2; i += NT) {
-      const int idx = 2 * i, slot = idx >> LOGR1, k1 = idx & (R1 - 1);
-      const float4 rv = raw[i];
-      const uint2 w = tabw[i];
-      float2* p = sm + pidx(slot, k1, LSTR);        // k1 even: no pad between the two
-      p[0] = cmul(make_float2(rv.x, rv.y), chirp_q32(nm * w.x));
-      p[1] = cmul(make_float2(rv.z, rv.w), chirp_q32(nm * w.y));
-    }
-    __syncthreads();   // the chirped tile (and twk, before the first trial)
-    j_runs<R1, J>(sm, stwj, twk, out + (size_t)t * out_tstride, nl, logR2, [&](int slot) { return r0 + slot; });
-    __syncthreads();   // the tile is free for the next trial
+    j_runs_load<R1, J>(sm, stwj, twk, out + (size_t)t * out_tstride, nl, logR2, [&](int slot) { return r0 + slot; },
+                       [&](int o) { return cmul(rows[o], chirp_q32(nm * tabw[o])); });
+    __syncwarp();    // the run's last reads of sm come before the next trial's writes
   }
 }
 
