@@ -217,6 +217,29 @@ def test_table_form_falls_back_to_anchors_off_grid():
         assert rel(T[d], r.ts) <= TOL, (d, rel(T[d], r.ts))
 
 
+@pytest.mark.parametrize("nfft,nchan,grid,t_dec", [(1 << 18, 8, [0.0, 0.3, 0.6, 0.9], 8e-6),
+                                                   (1 << 22, 32, [0.0, 2.0, 4.0, 6.0], 16e-6)])
+def test_multi_trial_forms_at_other_row_lengths(nfft, nchan, grid, t_dec):
+    """The multi-trial row passes at rows of 512 bins (nfft 2^18, 8
+    sub-channels: 16 rows per CTA) and 2048 bins (nfft 2^22, 32 sub-channels:
+    4 rows per CTA), the table form with a trial block that does not divide the
+    trial count: against the oracle, and the anchor form bit for bit against
+    the per-trial launches."""
+    p = pcd.make_plan(F0, BW, FS, max(grid), nfft, nchan, 1, 1.0, t_dec)
+    x = stream(2 * p.S + nfft + 555, seed=43, dm=grid[2])
+    res = oracle_batched(x, grid, [nfft] * len(grid), nchan, t_dec)
+    T, C, j0, _ = run_engine(x, grid, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_TABLE,
+                             trials_per_launch=3)
+    info = tuned(grid, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_TABLE, trials_per_launch=3)
+    assert info[0]["mode"] == "multi-table" and info[0]["trials_per_launch"] == 3
+    for d, r in enumerate(res):
+        assert j0 == r.ts_first and np.array_equal(C, r.ts_counts)
+        assert rel(T[d], r.ts) <= TOL, (nfft, d, rel(T[d], r.ts))
+    a = run_engine(x, grid, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_PER_TRIAL)
+    b = run_engine(x, grid, nfft, nchan, t_dec, trial_mode=pond.POND_TRIALS_MULTI_ANCHOR)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
 def test_multi_anchor_form_in_a_wide_low_band():
     """A wide low band (150 MHz, 100 MHz wide, 200 MHz sampling, nfft 2^21):
     the chirp's curvature asks for 32 to 4096 anchors per trial (2^15 down to
